@@ -1,0 +1,300 @@
+"""Pins of the CPU oracle against facts fixed outside it (CPU only).
+
+Each check ties the oracle to something other than itself: hand-derived IEEE
+cases, a library routine (numpy), exact integer and rational arithmetic,
+closed forms. The mutation tests at the end show that plausible mistakes in
+the oracle (a transposed operand, a dropped term, a wrong sign, float32
+accumulation, flush to zero) fail at least one pin.
+"""
+import math
+import struct
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import model
+
+
+def f32_bits(x):
+    return np.asarray(x, dtype=np.float32).view(np.uint32)
+
+
+def from_hex(h):
+    return np.frombuffer(struct.pack("<I", int(h, 16)), dtype=np.float32)[0]
+
+
+# ---------------------------------------------------------------- generators
+
+
+def test_splitmix64_published_vectors(golden):
+    for seed, i, val in golden("splitmix64_vectors.txt"):
+        assert synth.splitmix64_scalar(int(seed), int(i)) == int(val)
+        assert int(synth.splitmix64(int(seed), 1, int(i))[0]) == int(val)
+
+
+def test_uniform_grid_and_range():
+    x = synth.uniform_pm1(7, 100000)
+    assert x.dtype == np.float32
+    assert x.min() >= -1.0 and x.max() <= 1.0 - 2.0 ** -23
+    k = (x.astype(np.float64) + 1.0) * 2.0 ** 23
+    assert np.all(k == np.round(k))  # multiples of 2^-23
+    assert abs(float(x.mean())) < 0.02
+
+
+def test_normal_moments():
+    x = synth.standard_normal(11, 200000).astype(np.float64)
+    assert abs(x.mean()) < 0.01 and abs(x.std() - 1.0) < 0.01
+
+
+def test_chunked_generation_matches_single_chunk():
+    n = synth._CHUNK + 12345
+    a = synth.uniform_pm1(3, n)
+    b = np.concatenate([synth.uniform_pm1(3, synth._CHUNK), synth.uniform_pm1(3, 12345, synth._CHUNK)])
+    assert np.array_equal(f32_bits(a), f32_bits(b))
+
+
+# ---------------------------------------------------------------- vector add
+
+
+def test_vadd_ieee_hand_cases(golden):
+    rows = golden("vadd_ieee_cases.txt")
+    a = np.array([from_hex(r[0]) for r in rows], dtype=np.float32)
+    b = np.array([from_hex(r[1]) for r in rows], dtype=np.float32)
+    want = np.array([int(r[2], 16) for r in rows], dtype=np.uint32)
+    assert np.array_equal(f32_bits(oracle.vadd(a, b)), want)
+
+
+def test_vadd_matches_numpy_float32():
+    a, b = synth.vadd_inputs(synth.task_seed(3, 5), 65536)
+    with np.errstate(all="ignore"):
+        ref = np.add(a, b, dtype=np.float32)
+    assert np.array_equal(f32_bits(oracle.vadd(a, b)), f32_bits(ref))
+
+
+def test_vadd_empty():
+    assert oracle.vadd(np.zeros(0, np.float32), np.zeros(0, np.float32)).size == 0
+
+
+# ---------------------------------------------------------------- matrix multiply
+
+
+def sgemm_pins(fn):
+    """All SGEMM pins as one predicate list; each entry is (name, passed)."""
+    out = []
+    rng = np.random.default_rng(0)
+    # 1. numpy float64 matmul (library), elementwise within the fp64 bound.
+    for (m, n, k) in [(7, 5, 3), (33, 17, 65), (64, 48, 200)]:
+        A, B = synth.sgemm_inputs(synth.task_seed(1, m), m, n, k)
+        C = fn(A, B)
+        R = A.astype(np.float64) @ B.astype(np.float64)
+        bound = 2 * k * 2.0 ** -53 * (np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64))
+        out.append((f"numpy {m}x{n}x{k}", C.shape == R.shape and bool(np.all(np.abs(C - R) <= bound))))
+    # 2. integer operands: the exact integer product.
+    for (m, n, k) in [(9, 11, 64), (16, 3, 1), (5, 31, 17)]:
+        A, B = synth.sgemm_int_inputs(99 + k, m, n, k)
+        exact = A.astype(np.int64) @ B.astype(np.int64)
+        C = fn(A, B)
+        out.append((f"integer {m}x{n}x{k}", C.shape == exact.shape and bool(np.array_equal(C, exact.astype(np.float64)))))
+    # 3. K = 1: the outer product, exact in binary64.
+    a = rng.standard_normal((6, 1)).astype(np.float32)
+    b = rng.standard_normal((1, 4)).astype(np.float32)
+    out.append(("outer", bool(np.array_equal(fn(a, b), a.astype(np.float64) * b.astype(np.float64)))))
+    # 4. B = I gives A; I on the left gives B.
+    A = rng.standard_normal((5, 8)).astype(np.float32)
+    out.append(("right identity", bool(np.array_equal(fn(A, np.eye(8, dtype=np.float32)), A.astype(np.float64)))))
+    out.append(("left identity", bool(np.array_equal(fn(np.eye(5, dtype=np.float32), A), A.astype(np.float64)))))
+    # 5. zero operand.
+    out.append(("zero", bool(np.all(fn(np.zeros((3, 4), np.float32), A[:4, :6]) == 0.0))))
+    # 6. brute force on tiny shapes: exact rationals within the ordered-sum
+    #    bound, and a Python in-order binary64 sum bit for bit.
+    ok_exact, ok_order = True, True
+    for m in (1, 2, 3, 5):
+        for n in (1, 2, 3, 5):
+            for k in (1, 2, 3, 5):
+                A, B = synth.sgemm_inputs(synth.task_seed(m, 10 * n + k), m, n, k)
+                C = fn(A, B)
+                if C.shape != (m, n):
+                    ok_exact = ok_order = False
+                    continue
+                for i in range(m):
+                    for j in range(n):
+                        terms = [Fraction(float(A[i, t])) * Fraction(float(B[t, j])) for t in range(k)]
+                        exact = sum(terms, Fraction(0))
+                        mag = sum(abs(t) for t in terms)
+                        if abs(Fraction(float(C[i, j])) - exact) > (k * Fraction(1, 2 ** 52)) * mag:
+                            ok_exact = False
+                        s = 0.0
+                        for t in range(k):
+                            s += float(A[i, t]) * float(B[t, j])
+                        if s != float(C[i, j]):
+                            ok_order = False
+    out.append(("brute force exact", ok_exact))
+    out.append(("brute force order", ok_order))
+    return out
+
+
+def test_sgemm64_pins():
+    failed = [name for name, ok in sgemm_pins(oracle.sgemm64) if not ok]
+    assert not failed, failed
+
+
+def test_sgemm64_rejects_bad_shapes():
+    with pytest.raises(ValueError):
+        oracle.sgemm64(np.zeros((2, 3), np.float32), np.zeros((4, 2), np.float32))
+
+
+def test_rel_fro_err_closed_forms():
+    A, B = synth.sgemm_int_inputs(5, 8, 8, 8)
+    R = oracle.sgemm64(A, B)
+    C = R.astype(np.float32)  # integers, exact in float32
+    assert oracle.rel_fro_err(C, R) == 0.0
+    assert oracle.rel_fro_err(np.zeros_like(C), R) == 1.0
+    scaled = (R * (1.0 + 2.0 ** -10)).astype(np.float32)  # exact: |R| small integers
+    assert abs(oracle.rel_fro_err(scaled, R) - 2.0 ** -10) < 1e-15
+    assert oracle.rel_fro_err(np.zeros(4, np.float32), np.zeros(4)) == 0.0
+    assert math.isinf(oracle.rel_fro_err(np.ones(4, np.float32), np.zeros(4)))
+
+
+# ---------------------------------------------------------------- mutations
+
+
+def _mut_transpose_b(A, B):
+    return oracle.sgemm64(A, B.T.copy()) if A.shape[1] == B.shape[1] else oracle.sgemm64(A, B).T.copy()
+
+
+def _mut_drop_last_k(A, B):
+    if A.shape[1] == 1:
+        return np.zeros((A.shape[0], B.shape[1]))
+    return oracle.sgemm64(A[:, :-1], B[:-1, :])
+
+
+def _mut_f32_accumulate(A, B):
+    C = np.zeros((A.shape[0], B.shape[1]), dtype=np.float32)
+    for t in range(A.shape[1]):
+        C += np.outer(A[:, t], B[t, :]).astype(np.float32)
+    return C.astype(np.float64)
+
+
+def _mut_sign(A, B):
+    C = oracle.sgemm64(A, B)
+    C[0, 0] = -C[0, 0]
+    return C
+
+
+def _mut_reverse_order(A, B):
+    return oracle.sgemm64(A[:, ::-1].copy(), B[::-1, :].copy())
+
+
+@pytest.mark.parametrize(
+    "mutant", [_mut_transpose_b, _mut_drop_last_k, _mut_f32_accumulate, _mut_sign, _mut_reverse_order]
+)
+def test_sgemm_pins_catch_mutants(mutant):
+    assert any(not ok for _, ok in sgemm_pins(mutant))
+
+
+def test_vadd_pins_catch_ftz_and_truncation(golden):
+    rows = golden("vadd_ieee_cases.txt")
+    a = np.array([from_hex(r[0]) for r in rows], dtype=np.float32)
+    b = np.array([from_hex(r[1]) for r in rows], dtype=np.float32)
+    want = np.array([int(r[2], 16) for r in rows], dtype=np.uint32)
+    # flush-to-zero mutant
+    def ftz(x):
+        x = x.copy()
+        x[np.abs(x) < np.float32(2.0 ** -126)] = 0.0
+        return x
+    with np.errstate(all="ignore"):
+        c_ftz = ftz(ftz(a) + ftz(b))
+        # round-toward-zero mutant: exact sum in float64, truncated to float32
+        s = a.astype(np.float64) + b.astype(np.float64)
+        c_rz = s.astype(np.float32)
+        over = np.abs(c_rz.astype(np.float64)) > np.abs(s)
+        c_rz[over] = np.nextafter(c_rz[over], np.float32(0))
+    assert not np.array_equal(f32_bits(c_ftz), want)
+    assert not np.array_equal(f32_bits(c_rz), want)
+
+
+# ---------------------------------------------------------------- execution model
+
+
+def _params(seed, count):
+    z = synth.splitmix64(seed, 5 * count)
+    u = (z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return [tuple(0.1 + 10.0 * u[5 * i : 5 * i + 5]) for i in range(count)]
+
+
+def test_model_eq7_is_eq5_and_eq6():
+    for t_init, t_in, t_comp, t_out, t_ctx in _params(1, 200):
+        for n in (1, 2, 8, 16):
+            assert math.isclose(
+                model.t_total_ioi_ps2(n, t_in, t_comp, t_out),
+                model.t_total_ioi_ps2_piecewise(n, t_in, t_comp, t_out),
+                rel_tol=1e-12,
+            )
+
+
+def test_model_single_process_cases():
+    for t_init, t_in, t_comp, t_out, t_ctx in _params(2, 100):
+        alone = t_in + t_comp + t_out
+        for f in (model.t_total_ci_ps1, model.t_total_ci_ps2, model.t_total_ioi_ps1, model.t_total_ioi_ps2):
+            assert math.isclose(f(1, t_in, t_comp, t_out), alone, rel_tol=1e-12)
+        assert math.isclose(model.t_total_no_vt(1, t_init, t_in, t_comp, t_out, t_ctx), t_init + alone, rel_tol=1e-12)
+
+
+def test_model_speedup_limits():
+    for p in _params(3, 50):
+        big = 1e9
+        assert math.isclose(model.speedup_ci(big, *p), model.speedup_max_ci(*p), rel_tol=1e-6)
+        assert math.isclose(model.speedup_ioi(big, *p), model.speedup_max_ioi(*p), rel_tol=1e-6)
+
+
+def test_model_policy_inequalities():
+    # Style 2 never loses to style 1 for I/O-intensive tasks (Eq. 7 <= Eq. 4).
+    for t_init, t_in, t_comp, t_out, t_ctx in _params(4, 200):
+        for n in (1, 2, 8):
+            assert model.t_total_ioi_ps2(n, t_in, t_comp, t_out) <= model.t_total_ioi_ps1(n, t_in, t_comp, t_out) + 1e-12
+    # Style 1 beats style 2 for compute-bound tasks when the copies of one task
+    # are shorter than its kernel (Eq. 2 < Eq. 3 iff T_in + T_out < T_comp).
+    assert model.t_total_ci_ps1(8, 1.0, 5.0, 1.0) < model.t_total_ci_ps2(8, 1.0, 5.0, 1.0)
+    assert model.t_total_ci_ps1(8, 2.0, 3.0, 2.0) > model.t_total_ci_ps2(8, 2.0, 3.0, 2.0)
+
+
+def test_model_classes():
+    assert model.classify(1, 5, 1) == model.CI
+    assert model.classify(5, 1, 6) == model.IOI
+    assert model.classify(5, 3, 1) == model.INTERMEDIATE
+    assert model.classify(3, 3, 3) == model.CI  # boundary: <= is compute-intensive
+
+
+def test_model_sequential_exceeds_shared():
+    for t_init, t_in, t_comp, t_out, t_ctx in _params(5, 100):
+        for n in (2, 4, 16):
+            seq = model.t_total_no_vt(n, t_init, t_in, t_comp, t_out, t_ctx)
+            assert seq > model.shared_time(n, t_in, t_comp, t_out)
+
+
+# ---------------------------------------------------------------- workloads
+
+
+def test_rank_runner_is_order_and_isolation():
+    w = synth.vadd_tiny(ranks=2, per_rank=3, n=1000)
+    res = oracle.run_workload(w)
+    for spec in w.tasks:
+        a, b = synth.vadd_inputs(spec.seed, spec.n)
+        assert np.array_equal(f32_bits(res[(spec.rank, spec.index)]), f32_bits(oracle.vadd(a, b)))
+
+
+def test_workload_recipes():
+    w = synth.serving_mix(ranks=16, total=4096)
+    assert len(w.tasks) == 4096
+    kinds = [t.kind for t in w.tasks]
+    assert kinds.count(synth.TASK_VADD) == 2048
+    for t in w.tasks:
+        if t.kind == synth.TASK_VADD:
+            assert 2 ** 16 <= t.n < 2 ** 24
+        else:
+            assert t.m == t.n == t.k and t.m in (256, 512, 1024, 2048)
+    g = synth.grouped_mixed(ranks=4, per_rank=8)
+    assert all(128 <= x <= 2048 and x % 64 == 0 for t in g.tasks for x in (t.m, t.n, t.k))
