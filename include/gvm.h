@@ -1,0 +1,254 @@
+/*
+ * gvm.h -- C ABI of the GB300 GPU virtualization manager.
+ *
+ * The method (Li, Narayana, El-Ghazawi, "Efficient Resource Sharing Through
+ * GPU Virtualization on Accelerated High Performance Computing Systems"):
+ * many SPMD processes share one GPU through a single virtualization manager
+ * that owns the only GPU context, gives each process a virtual GPU with its
+ * own memory objects and stream, and runs every process's task -- an input
+ * copy, a data-parallel kernel, an output copy -- concurrently with the
+ * others (Section 4.2.2, Section 5). This header is that manager's boundary.
+ *
+ * Mapping of the paper's API routines (Section 5):
+ *   REQ()          -> gvm_attach   (get a virtual GPU: ring, arena slice, streams)
+ *   SND() + STR()  -> gvm_submit   (hand over the input, start the kernel)
+ *   STP() + RCV()  -> gvm_sync     (wait for the result to be back in host memory)
+ *   RLS()          -> gvm_detach   (release the virtual GPU)
+ *   request barrier-> gvm_flush    (barrier mode: drain everything submitted so far)
+ *
+ * Conventions:
+ *   - Every entry point returns GVM_OK (0) or a negative GVM_E* code; no C++
+ *     exception crosses this boundary.
+ *   - The library owns no device memory: the caller passes device memory
+ *     (arena, control block) and stream handles; the library never calls
+ *     cudaMalloc. It allocates pinned host memory for the task rings only.
+ *   - A gvm_rank handle is used by one host thread at a time; different ranks
+ *     may be driven concurrently from different threads.
+ *   - Stream arguments are cudaStream_t values passed as void*.
+ */
+#ifndef GVM_H
+#define GVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GVM_API __attribute__((visibility("default")))
+#else
+#define GVM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define GVM_OK 0
+#define GVM_EINVAL (-1)     /* bad argument, shape or offset */
+#define GVM_EBUSY (-2)      /* rank already attached */
+#define GVM_EAGAIN (-3)     /* ring or staging space full right now; retry after gvm_sync */
+#define GVM_ENOMEM (-4)     /* the task can never fit its rank's staging space or the cap */
+#define GVM_ETIMEDOUT (-5)  /* a bounded wait ran out (host or device side) */
+#define GVM_EDEVICE (-6)    /* a CUDA call failed or the device reported an error status */
+#define GVM_ECANCELED (-7)  /* the manager shut down before the task completed */
+#define GVM_ESTATE (-8)     /* call not valid in the current state (e.g. not attached) */
+#define GVM_ENODEV (-9)     /* no usable CUDA device */
+
+/* ---- task types (Section 6, Table 2) ------------------------------------ */
+#define GVM_TASK_VADD 1   /* c[i] = a[i] + b[i], binary32, n elements */
+#define GVM_TASK_SGEMM 2  /* C = A B, binary32, row-major A (m x k), B (k x n), C (m x n) */
+
+/* ---- task flags --------------------------------------------------------- */
+#define GVM_TASK_RESIDENT 1 /* a_off/b_off/c_off address the rank's resident region;
+                               no host copies (inputs already on the device) */
+
+/* ---- SGEMM arithmetic --------------------------------------------------- */
+#define GVM_SGEMM_FMA 0    /* binary32 fused multiply-add on the CUDA cores */
+#define GVM_SGEMM_SPLIT3 1 /* A = Ah + Al, B = Bh + Bl in bf16; C = AhBh + AhBl + AlBh on
+                              tcgen05 tensor cores with binary32 accumulation in TMEM */
+
+/* ---- manager modes ------------------------------------------------------ */
+#define GVM_MODE_BARRIER 0    /* Section 5 request barrier: gvm_flush runs the scheduler
+                                 until every task submitted before it has completed */
+#define GVM_MODE_CONTINUOUS 1 /* the scheduler stays resident and takes tasks as they
+                                 arrive; it exits after idle_exit_ns without work and is
+                                 relaunched by the next gvm_submit / gvm_sync */
+
+#define GVM_MAX_RANKS 1024
+
+typedef struct gvm_config {
+  int32_t max_ranks;      /* ranks that may attach: 1 .. GVM_MAX_RANKS */
+  int32_t ring_depth;     /* task descriptors per rank; power of two, 2 .. 4096 */
+  int32_t mode;           /* GVM_MODE_BARRIER or GVM_MODE_CONTINUOUS */
+  int32_t sgemm_path;     /* GVM_SGEMM_FMA or GVM_SGEMM_SPLIT3 */
+  void* arena;            /* caller-owned device memory, 256-byte aligned. Split into
+                             max_ranks equal slices (Section 5: one memory object per
+                             process, so data of different processes coexist safely) */
+  uint64_t arena_bytes;
+  uint64_t resident_bytes; /* bytes at the start of each slice addressed by the offsets
+                              of GVM_TASK_RESIDENT tasks; the rest of the slice is the
+                              rank's staging ring (copied inputs, outputs, scratch) */
+  void* ctrl;             /* caller-owned device memory for control words and the
+                             device task table, >= gvm_ctrl_bytes(cfg), 256-aligned */
+  uint64_t ctrl_bytes;
+  void* sched_stream;     /* cudaStream_t on which the scheduler kernel is launched */
+  void* const* copy_streams; /* 2*max_ranks cudaStream_t: [2r] carries rank r's input
+                                copies, [2r+1] its output copies (Section 4.2.1: one
+                                stream per process) */
+  uint64_t admission_cap_bytes; /* cap on staging bytes held by admitted, unfinished tasks
+                                   across all ranks; 0 = only the slices bound it */
+  uint64_t wait_timeout_ns; /* bound on each device-side dependency wait and on each
+                               host wait in gvm_sync / gvm_wait_idle; 0 = 10 s */
+  uint64_t idle_exit_ns;    /* continuous mode: idle time after which the scheduler
+                               kernel exits; 0 = 1 s */
+  int32_t grid_ctas;        /* scheduler CTAs; 0 = one per SM */
+  int32_t ingest_quantum;   /* tasks taken from one rank per ingest pass; 0 = 4 */
+} gvm_config;
+
+typedef struct gvm_task {
+  int32_t type;   /* GVM_TASK_VADD or GVM_TASK_SGEMM */
+  int32_t flags;  /* 0 or GVM_TASK_RESIDENT */
+  int64_t n;      /* VADD: element count (>= 0). SGEMM: columns of B and C (>= 1) */
+  int32_t m;      /* SGEMM: rows of A and C (>= 1) */
+  int32_t k;      /* SGEMM: columns of A, rows of B (>= 1) */
+  /* host mode (flags without GVM_TASK_RESIDENT): page-locked host buffers,
+     caller-owned, valid and untouched until gvm_sync returns for this task.
+     VADD: a, b, c hold n floats. SGEMM: a = A (m*k), b = B (k*n), c = C (m*n). */
+  const void* a;
+  const void* b;
+  void* c;
+  /* resident mode: byte offsets into the rank's resident region, 16-byte aligned
+     for SGEMM and 4-byte aligned for VADD; operands must lie inside the region. */
+  uint64_t a_off;
+  uint64_t b_off;
+  uint64_t c_off;
+} gvm_task;
+
+typedef struct gvm_stats {
+  uint64_t submitted;      /* tasks accepted by gvm_submit */
+  uint64_t completed;      /* tasks observed complete by gvm_sync / gvm_poll */
+  uint64_t launches;       /* scheduler kernel launches */
+  uint64_t staged_bytes;   /* staging bytes currently held by unfinished tasks */
+  uint64_t staged_peak;    /* high-water mark of staged_bytes */
+  uint64_t h2d_bytes;      /* bytes copied host to device by the manager */
+  uint64_t d2h_bytes;      /* bytes copied device to host by the manager */
+  uint32_t device_status;  /* last error status word written by the scheduler (0 = ok) */
+  uint32_t device_where;   /* which wait or check set device_status */
+} gvm_stats;
+
+typedef struct gvm_ctx gvm_ctx;
+typedef struct gvm_rank gvm_rank;
+
+/* Device bytes the control block needs for cfg (depends on max_ranks and
+   ring_depth only). Returns 0 for an invalid cfg. */
+GVM_API uint64_t gvm_ctrl_bytes(const gvm_config* cfg);
+
+/* Creates the manager (Section 5: the GVM initialises every resource once,
+   which hides T_init, Section 4.2.3). Checks cfg, zeroes the control block on
+   sched_stream, allocates the pinned rings and, in continuous mode, launches
+   the scheduler. *out receives the handle. Errors: GVM_EINVAL (cfg),
+   GVM_ENODEV, GVM_EDEVICE, GVM_ENOMEM (host rings). */
+GVM_API int gvm_init(const gvm_config* cfg, gvm_ctx** out);
+
+/* REQ(): attaches rank 0 <= rank < max_ranks and returns its handle.
+   GVM_EBUSY if attached already, GVM_EINVAL if out of range. */
+GVM_API int gvm_attach(gvm_ctx* ctx, int32_t rank, gvm_rank** out);
+
+/* SND() + STR(): admits one task and returns at once. Host mode enqueues the
+   input copies on the rank's input stream, then a ready flag; the output copy
+   waits on the task's done flag on the rank's output stream. Resident mode
+   enqueues nothing. The task then runs when the scheduler takes it from the
+   ring. *seq_out receives its sequence number (0, 1, 2, ... per rank).
+   Errors: GVM_EINVAL (type, shape, offsets, non-pinned host buffer),
+   GVM_EAGAIN (ring slot or staging space busy: retry after gvm_sync),
+   GVM_ENOMEM (can never fit), GVM_ESTATE (detached or shut down),
+   GVM_EDEVICE (a CUDA call failed). */
+GVM_API int gvm_submit(gvm_rank* rank, const gvm_task* task, uint64_t* seq_out);
+
+/* Submits tasks[0 .. count-1] in order, as count calls of gvm_submit would,
+   stopping at the first task that cannot be admitted right now. Returns the
+   number submitted (0 .. count) and sets *first_seq to the sequence number of
+   tasks[0]; a task that is invalid or can never fit returns its error code
+   when it is the first one, else ends the batch early. */
+GVM_API int gvm_submit_many(gvm_rank* rank, const gvm_task* tasks, uint32_t count, uint64_t* first_seq);
+
+/* STP() + RCV(): blocks until every task of this rank with sequence <= seq
+   is complete and, in host mode, its output is in the host buffer. Results
+   become visible to the rank in sequence order (Section 4.2.3 keeps the
+   process order). GVM_ETIMEDOUT after wait_timeout_ns without progress,
+   GVM_EDEVICE if the scheduler reported an error, GVM_EINVAL if seq was never
+   issued. */
+GVM_API int gvm_sync(gvm_rank* rank, uint64_t seq);
+
+/* Non-blocking completion test: 1 if task seq is complete, 0 if not, or a
+   negative error code. */
+GVM_API int gvm_poll(gvm_rank* rank, uint64_t seq);
+
+/* Barrier mode: launches the scheduler on sched_stream; it drains every task
+   submitted (on any rank) before this call and then exits. Continuous mode:
+   makes sure the scheduler is running. Returns without waiting. */
+GVM_API int gvm_flush(gvm_ctx* ctx);
+
+/* Waits until the scheduler kernel and all copy streams are idle. */
+GVM_API int gvm_wait_idle(gvm_ctx* ctx);
+
+/* Copies bytes between host memory and the rank's resident region
+   (synchronously, on the rank's input stream). off + bytes must lie inside the
+   region. These place the inputs of GVM_TASK_RESIDENT tasks and read their
+   outputs back; they are not part of a task. */
+GVM_API int gvm_rank_write(gvm_rank* rank, uint64_t off, const void* src, uint64_t bytes);
+GVM_API int gvm_rank_read(gvm_rank* rank, uint64_t off, void* dst, uint64_t bytes);
+
+/* Device address of the rank's resident region (for callers that fill it
+   with their own kernels or copies), or NULL for a bad handle. */
+GVM_API void* gvm_rank_resident_ptr(gvm_rank* rank);
+
+/* RLS(): waits for the rank's tasks, then releases the rank. */
+GVM_API int gvm_detach(gvm_rank* rank);
+
+/* Stops the scheduler after in-flight work, waits for the streams, frees the
+   rings and the handle. Tasks never taken from a ring report GVM_ECANCELED
+   through gvm_sync from then on (the handle is gone, so callers must not sync
+   after shutdown). */
+GVM_API int gvm_shutdown(gvm_ctx* ctx);
+
+GVM_API int gvm_stats_get(gvm_ctx* ctx, gvm_stats* out);
+
+/* Device timestamps (globaltimer, ns) of task seq of this rank: when the
+   scheduler took it from the ring and when its last tile finished. Valid
+   once the task is complete and until its ring slot is reused. */
+GVM_API int gvm_task_times(gvm_rank* rank, uint64_t seq, uint64_t* t_ingest_ns, uint64_t* t_done_ns);
+
+GVM_API const char* gvm_strerror(int code);
+
+/* ---- the task kernels alone -------------------------------------------- */
+/* These run one task's kernel on caller-given device buffers, on the given
+   stream, without the manager: the kernels of Table 2 as the manager runs
+   them, used for unit parity checks, per-kernel measurement and the plain
+   one-context-per-process form of Section 4.1. */
+
+/* c = a + b, n binary32 elements (Table 2, VecAdd). Device pointers; any
+   alignment; n >= 0. Returns GVM_EINVAL for n < 0 or NULL with n > 0. */
+GVM_API int gvm_vadd_f32(const float* a, const float* b, float* c, int64_t n, void* stream);
+
+/* Scratch bytes gvm_sgemm_f32 needs for (m, n, k, path): 0 for the FMA path;
+   for split3 the bf16 hi/lo copies of A (m x kp) and of B transposed
+   (n x kp), kp = k rounded up to a multiple of 8. */
+GVM_API uint64_t gvm_sgemm_scratch_bytes(int32_t m, int32_t n, int32_t k, int32_t path);
+
+/* C = A B (Table 2, MM), row-major binary32 device buffers A (m x k), B (k x n),
+   C (m x n). path selects the arithmetic; scratch (device, 256-byte aligned,
+   >= gvm_sgemm_scratch_bytes) is needed by the split3 path only. Returns
+   GVM_EINVAL for bad shapes or a short scratch buffer. */
+GVM_API int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m, int32_t n, int32_t k,
+                  int32_t path, void* scratch, uint64_t scratch_bytes, void* stream);
+
+/* Reads and clears the error status of the standalone kernels: 0 when every
+   bounded wait since the last call finished in time; otherwise the low byte
+   is the status and the next byte names the wait. Synchronous. */
+GVM_API int gvm_kernel_status(uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GVM_H */

@@ -1,0 +1,208 @@
+// The task kernels on their own: gvm_vadd_f32 and gvm_sgemm_f32 run one
+// task's kernel on caller-given device buffers without the manager. They use
+// the same tile functions as the scheduler, so a task computed here and the
+// same task computed by the manager agree bit for bit.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "gvm.h"
+#include "gvm_device.cuh"
+#include "gvm_runtime.h"
+
+namespace gvm {
+
+// Last error status of a standalone kernel (0 = ok); see gvm_kernel_status.
+__device__ uint32_t g_kernel_status;
+
+__global__ void __launch_bounds__(kThreads) vadd_kernel(const float* a, const float* b, float* c, int64_t n,
+                                                        int64_t chunk) {
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  if (lo >= n) return;
+  vadd_range(a, b, c, lo, min(n, lo + chunk));
+}
+
+__global__ void __launch_bounds__(kThreads, 2) fma_sgemm_kernel(const float* A, const float* B, float* C, int m,
+                                                                 int n, int k) {
+  extern __shared__ uint8_t dyn_smem[];
+  fma_tile(A, B, C, m, n, k, blockIdx.y, blockIdx.x, reinterpret_cast<FmaSmem*>(dyn_smem));
+}
+
+__global__ void __launch_bounds__(kThreads) split_kernel(const float* A, const float* B, __nv_bfloat16* pa,
+                                                         __nv_bfloat16* pb, int m, int n, int k, int kp) {
+  const int tiles_a = (m + kSplitRows - 1) / kSplitRows;
+  const int t = blockIdx.x;
+  if (t < tiles_a) {
+    split_a_tile(A, pa, m, k, kp, t * kSplitRows);
+  } else {
+    split_b_tile(B, pb, n, k, kp, (int64_t)(t - tiles_a) * kSplitRows);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_sgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* C,
+                    int m, int n, int k, uint64_t timeout_ns) {
+  __shared__ TcShared ts;
+  __shared__ uint32_t abort_flag, fail_where;
+  extern __shared__ uint8_t dyn_smem[];
+  uint8_t* big = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    fail_where = 0;
+  }
+  tc_init(&ts);
+  uint32_t it = 0, tile_no = 0;
+  tc_tile(&tmA, &tmB, C, m, n, k, blockIdx.y, blockIdx.x, big, &ts, it, tile_no, timeout_ns, nullptr, 0,
+          &abort_flag, &fail_where, false);
+  tc_teardown(&ts);
+  if (threadIdx.x == 0 && abort_flag) atomicExch(&g_kernel_status, kStatusTimeout | (fail_where << 8));
+}
+
+// ---------------------------------------------------------------- driver API
+
+static DriverApi g_api;
+static bool g_api_ok = false;
+static std::once_flag g_api_once;
+
+const DriverApi* driver_api() {
+  std::call_once(g_api_once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    void* f3 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &f1, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return;
+    if (cudaGetDriverEntryPointByVersion("cuStreamWaitValue32", &f2, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f3, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return;
+    g_api.write_value32 = reinterpret_cast<decltype(g_api.write_value32)>(f1);
+    g_api.wait_value32 = reinterpret_cast<decltype(g_api.wait_value32)>(f2);
+    g_api.encode_tiled = reinterpret_cast<decltype(g_api.encode_tiled)>(f3);
+    g_api_ok = true;
+  });
+  return g_api_ok ? &g_api : nullptr;
+}
+
+CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUtensorMap* tmA, CUtensorMap* tmB) {
+  const DriverApi* api = driver_api();
+  if (!api) return CUDA_ERROR_NOT_INITIALIZED;
+  const uint64_t kp = split_kp(k);
+  uint8_t* pa = static_cast<uint8_t*>(scratch);
+  uint8_t* pb = pa + split_a_bytes(m, k);
+  const cuuint32_t estr[3] = {1, 1, 1};
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)m, 2};
+    const cuuint64_t strides[2] = {kp * 2, (cuuint64_t)m * kp * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcM, 1};
+    CUresult r = api->encode_tiled(tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, pa, dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return r;
+  }
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)n, 2};
+    const cuuint64_t strides[2] = {kp * 2, (cuuint64_t)n * kp * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcN, 1};
+    return api->encode_tiled(tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, pb, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+}
+
+constexpr uint64_t kStandaloneTimeoutNs = 10ull * 1000 * 1000 * 1000;
+
+static int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  }
+  return sms;
+}
+
+}  // namespace gvm
+
+using namespace gvm;
+
+extern "C" int gvm_vadd_f32(const float* a, const float* b, float* c, int64_t n, void* stream) {
+  if (n < 0) return GVM_EINVAL;
+  if (n == 0) return GVM_OK;
+  if (!a || !b || !c) return GVM_EINVAL;
+  const int sms = sm_count();
+  if (sms <= 0) return GVM_ENODEV;
+  int64_t chunk = (n + (int64_t)sms * 4 - 1) / ((int64_t)sms * 4);
+  chunk = (chunk + 1023) / 1024 * 1024;
+  if (chunk < kVaddTileMin) chunk = kVaddTileMin;
+  const int64_t grid = (n + chunk - 1) / chunk;
+  vadd_kernel<<<(unsigned)grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(a, b, c, n, chunk);
+  return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
+}
+
+extern "C" uint64_t gvm_sgemm_scratch_bytes(int32_t m, int32_t n, int32_t k, int32_t path) {
+  if (m <= 0 || n <= 0 || k <= 0) return 0;
+  return path == GVM_SGEMM_SPLIT3 ? split_scratch_bytes(m, n, k) : 0;
+}
+
+static bool fma_attr_set = false;
+static bool tc_attr_set = false;
+
+extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m, int32_t n, int32_t k,
+                             int32_t path, void* scratch, uint64_t scratch_bytes, void* stream) {
+  if (m <= 0 || n <= 0 || k <= 0 || m > 65536 || n > 65536 || k > 65536) return GVM_EINVAL;
+  if (!A || !B || !C) return GVM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (path == GVM_SGEMM_FMA) {
+    const size_t smem = sizeof(FmaSmem);
+    if (!fma_attr_set) {
+      if (cudaFuncSetAttribute(fma_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+        return GVM_EDEVICE;
+      fma_attr_set = true;
+    }
+    dim3 grid((n + kFmaTile - 1) / kFmaTile, (m + kFmaTile - 1) / kFmaTile);
+    fma_sgemm_kernel<<<grid, kThreads, smem, s>>>(A, B, C, m, n, k);
+    return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
+  }
+  if (path != GVM_SGEMM_SPLIT3) return GVM_EINVAL;
+  const uint64_t need = split_scratch_bytes(m, n, k);
+  if (!scratch || scratch_bytes < need || (reinterpret_cast<uintptr_t>(scratch) & 255)) return GVM_EINVAL;
+  CUtensorMap tmA, tmB;
+  if (encode_split_maps(scratch, m, n, k, &tmA, &tmB) != CUDA_SUCCESS) return GVM_EDEVICE;
+  const int kp = (int)split_kp(k);
+  uint8_t* pa = static_cast<uint8_t*>(scratch);
+  uint8_t* pb = pa + split_a_bytes(m, k);
+  const int nsplit = (m + kSplitRows - 1) / kSplitRows + (n + kSplitRows - 1) / kSplitRows;
+  split_kernel<<<nsplit, kThreads, 0, s>>>(A, B, reinterpret_cast<__nv_bfloat16*>(pa),
+                                           reinterpret_cast<__nv_bfloat16*>(pb), m, n, k, kp);
+  if (cudaGetLastError() != cudaSuccess) return GVM_EDEVICE;
+  const size_t smem = (size_t)kTcStages * kTcStageBytes + 1024;
+  if (!tc_attr_set) {
+    if (cudaFuncSetAttribute(tc_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return GVM_EDEVICE;
+    tc_attr_set = true;
+  }
+  dim3 grid((n + kTcN - 1) / kTcN, (m + kTcM - 1) / kTcM);
+  tc_sgemm_kernel<<<grid, kThreads, smem, s>>>(tmA, tmB, C, m, n, k, kStandaloneTimeoutNs);
+  return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
+}
+
+// Reads and clears the error status of the standalone kernels (0 = ok; else
+// low byte = status, next byte = which wait). Synchronous.
+extern "C" int gvm_kernel_status(uint32_t* out) {
+  if (!out) return GVM_EINVAL;
+  uint32_t v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_kernel_status, sizeof(v)) != cudaSuccess) return GVM_EDEVICE;
+  const uint32_t zero = 0;
+  if (cudaMemcpyToSymbol(g_kernel_status, &zero, sizeof(zero)) != cudaSuccess) return GVM_EDEVICE;
+  *out = v;
+  return GVM_OK;
+}

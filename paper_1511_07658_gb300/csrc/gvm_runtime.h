@@ -1,0 +1,35 @@
+// Internal functions shared by the host runtime translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gvm_internal.h"
+
+namespace gvm {
+
+enum : int { kPathFma = 0, kPathSplit3 = 1 };
+
+// Driver entry points, resolved once through the runtime (no link-time libcuda).
+struct DriverApi {
+  CUresult (*write_value32)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+  CUresult (*wait_value32)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+  CUresult (*encode_tiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                           const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                           CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+};
+// Returns nullptr if the driver or an entry point is unavailable.
+const DriverApi* driver_api();
+
+// Encodes the two tensor maps of a split3 task whose bf16 planes start at
+// `scratch` (A planes, then B^T planes at scratch + split_a_bytes).
+// Returns CUDA_SUCCESS or the driver's error.
+CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUtensorMap* tmA, CUtensorMap* tmB);
+
+// Scheduler kernel: occupancy-derived grid for `path`, dynamic smem bytes,
+// and an asynchronous launch on `stream`.
+cudaError_t scheduler_setup(int path, int* blocks_per_sm, size_t* smem_bytes);
+cudaError_t launch_scheduler(int path, const SchedParams& p, int grid, size_t smem, cudaStream_t stream);
+
+}  // namespace gvm

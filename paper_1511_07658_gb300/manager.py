@@ -1,0 +1,318 @@
+"""Thin Python wrappers over the gvm C ABI.
+
+``Manager`` allocates the device arena and control block with PyTorch, takes
+its streams from PyTorch, and passes raw pointers to ``gvm_init``. ``Rank``
+wraps a rank handle (the paper's virtual GPU, Section 5): ``submit_*`` is
+SND()+STR(), ``sync`` is STP()+RCV(). Every step of a task runs in libgvm.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_uint32, c_uint64, c_void_p
+
+import torch
+
+from . import _abi
+from ._abi import (
+    GVM_EAGAIN,
+    GVM_MODE_BARRIER,
+    GVM_MODE_CONTINUOUS,
+    GVM_SGEMM_FMA,
+    GVM_SGEMM_SPLIT3,
+    GVM_TASK_RESIDENT,
+    GVM_TASK_SGEMM,
+    GVM_TASK_VADD,
+    GvmConfig,
+    GvmStats,
+    GvmTask,
+    check,
+    lib,
+)
+
+_PATHS = {"fma": GVM_SGEMM_FMA, "split3": GVM_SGEMM_SPLIT3}
+_MODES = {"barrier": GVM_MODE_BARRIER, "continuous": GVM_MODE_CONTINUOUS}
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Rank:
+    """One rank's virtual GPU: its ring, arena slice and streams."""
+
+    def __init__(self, mgr: "Manager", rank: int, handle: int):
+        self.mgr = mgr
+        self.rank = rank
+        self.handle = c_void_p(handle)
+        self.resident_bytes = mgr.resident_bytes
+
+    # -- submission -------------------------------------------------------
+    def submit(self, task: GvmTask, block: bool = True) -> int:
+        """Submit a task; returns its sequence number. With ``block`` the call
+        retries while the ring or staging space is full (syncing on the rank's
+        oldest unfinished task), otherwise GVM_EAGAIN raises."""
+        seq = c_uint64(0)
+        L = lib()
+        while True:
+            rc = L.gvm_submit(self.handle, byref(task), byref(seq))
+            if rc == GVM_EAGAIN and block:
+                self.mgr.flush_if_barrier()
+                L.gvm_sync(self.handle, self._oldest_pending())
+                continue
+            check(rc, "gvm_submit")
+            self._last = seq.value
+            return seq.value
+
+    def submit_many(self, tasks, block: bool = True) -> tuple[int, int]:
+        """Submit a ctypes array of GvmTask in order; returns (first_seq,
+        count). With ``block`` a full ring or staging ring is waited out."""
+        L = lib()
+        first = c_uint64(0)
+        total, first_seq = 0, None
+        n = len(tasks)
+        base = ctypes.addressof(tasks)
+        size = ctypes.sizeof(GvmTask)
+        while total < n:
+            ptr = ctypes.cast(base + total * size, ctypes.POINTER(GvmTask))
+            rc = L.gvm_submit_many(self.handle, ptr, n - total, byref(first))
+            check(rc, "gvm_submit_many")
+            if rc > 0:
+                if first_seq is None:
+                    first_seq = first.value
+                total += rc
+                self._last = first.value + rc - 1
+            if total < n:
+                if not block:
+                    break
+                self.mgr.flush_if_barrier()
+                L.gvm_sync(self.handle, self._oldest_pending())
+        return (first_seq if first_seq is not None else -1), total
+
+    def _oldest_pending(self) -> int:
+        last = getattr(self, "_last", None)
+        if last is None:
+            return 0
+        lo = max(0, last - self.mgr.ring_depth + 1)
+        for s in range(lo, last + 1):
+            if L_poll(self.handle, s) == 0:
+                return s
+        return last
+
+    def submit_vadd(self, a: torch.Tensor, b: torch.Tensor, c: torch.Tensor, block: bool = True) -> int:
+        """Host mode: a, b, c are pinned float32 host tensors of equal length."""
+        t = GvmTask()
+        t.type = GVM_TASK_VADD
+        t.flags = 0
+        t.n = a.numel()
+        t.a, t.b, t.c = _ptr(a), _ptr(b), _ptr(c)
+        return self.submit(t, block)
+
+    def submit_sgemm(self, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, block: bool = True) -> int:
+        """Host mode: pinned float32 host tensors A (m x k), B (k x n), C (m x n)."""
+        t = GvmTask()
+        t.type = GVM_TASK_SGEMM
+        t.flags = 0
+        t.m, t.k = A.shape
+        t.n = B.shape[1]
+        t.a, t.b, t.c = _ptr(A), _ptr(B), _ptr(C)
+        return self.submit(t, block)
+
+    def submit_vadd_resident(self, a_off: int, b_off: int, c_off: int, n: int, block: bool = True) -> int:
+        t = GvmTask()
+        t.type = GVM_TASK_VADD
+        t.flags = GVM_TASK_RESIDENT
+        t.n = n
+        t.a_off, t.b_off, t.c_off = a_off, b_off, c_off
+        return self.submit(t, block)
+
+    def submit_sgemm_resident(
+        self, a_off: int, b_off: int, c_off: int, m: int, n: int, k: int, block: bool = True
+    ) -> int:
+        t = GvmTask()
+        t.type = GVM_TASK_SGEMM
+        t.flags = GVM_TASK_RESIDENT
+        t.m, t.n, t.k = m, n, k
+        t.a_off, t.b_off, t.c_off = a_off, b_off, c_off
+        return self.submit(t, block)
+
+    # -- completion -------------------------------------------------------
+    def sync(self, seq: int) -> None:
+        check(lib().gvm_sync(self.handle, seq), "gvm_sync")
+
+    def poll(self, seq: int) -> bool:
+        return check(lib().gvm_poll(self.handle, seq), "gvm_poll") == 1
+
+    def task_times(self, seq: int) -> tuple[int, int]:
+        a, b = c_uint64(0), c_uint64(0)
+        check(lib().gvm_task_times(self.handle, seq, byref(a), byref(b)), "gvm_task_times")
+        return a.value, b.value
+
+    # -- resident region --------------------------------------------------
+    def write(self, off: int, src: torch.Tensor) -> None:
+        check(lib().gvm_rank_write(self.handle, off, _ptr(src), src.numel() * src.element_size()), "gvm_rank_write")
+
+    def read(self, off: int, dst: torch.Tensor) -> None:
+        check(lib().gvm_rank_read(self.handle, off, _ptr(dst), dst.numel() * dst.element_size()), "gvm_rank_read")
+
+    def resident_ptr(self) -> int:
+        return lib().gvm_rank_resident_ptr(self.handle)
+
+    def resident_view(self, off: int, shape, dtype=torch.float32) -> torch.Tensor:
+        """A torch view of the rank's resident region (the region is a slice of
+        the manager's torch arena)."""
+        n = 1
+        for s in shape:
+            n *= s
+        esz = torch.empty(0, dtype=dtype).element_size()
+        base = self.resident_ptr() - self.mgr.arena.data_ptr() + off
+        if off + n * esz > self.resident_bytes:
+            raise ValueError("view exceeds the resident region")
+        return self.mgr.arena[base : base + n * esz].view(dtype).view(*shape)
+
+    def detach(self) -> None:
+        check(lib().gvm_detach(self.handle), "gvm_detach")
+
+
+def L_poll(handle, seq):
+    return lib().gvm_poll(handle, seq)
+
+
+class Manager:
+    """One GPU virtualization manager on the current CUDA device."""
+
+    def __init__(
+        self,
+        ranks: int,
+        *,
+        ring_depth: int = 64,
+        mode: str = "barrier",
+        sgemm_path: str = "split3",
+        slice_bytes: int = 64 << 20,
+        resident_bytes: int = 0,
+        admission_cap_bytes: int = 0,
+        wait_timeout_s: float = 10.0,
+        idle_exit_s: float = 1.0,
+        grid_ctas: int = 0,
+        ingest_quantum: int = 4,
+        device: int | None = None,
+    ):
+        if not torch.cuda.is_available():
+            raise RuntimeError("gvm Manager needs a CUDA device")
+        L = lib()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.ranks = ranks
+        self.ring_depth = ring_depth
+        self.mode = mode
+        self.resident_bytes = resident_bytes
+        self.slice_bytes = slice_bytes
+        cfg = GvmConfig()
+        cfg.max_ranks = ranks
+        cfg.ring_depth = ring_depth
+        cfg.mode = _MODES[mode]
+        cfg.sgemm_path = _PATHS[sgemm_path]
+        ctrl_bytes = L.gvm_ctrl_bytes(byref(cfg))
+        if ctrl_bytes == 0:
+            raise ValueError("invalid manager configuration")
+        with torch.cuda.device(self.device):
+            self.arena = torch.empty(slice_bytes * ranks + 256, dtype=torch.uint8, device=self.device)
+            self.ctrl = torch.empty(ctrl_bytes + 256, dtype=torch.uint8, device=self.device)
+            self.sched_stream = torch.cuda.Stream(self.device)
+            self.copy_streams = [torch.cuda.Stream(self.device) for _ in range(2 * ranks)]
+        arena_ptr = (self.arena.data_ptr() + 255) // 256 * 256
+        ctrl_ptr = (self.ctrl.data_ptr() + 255) // 256 * 256
+        self._streams_arr = (c_void_p * (2 * ranks))(*[s.cuda_stream for s in self.copy_streams])
+        cfg.arena = arena_ptr
+        cfg.arena_bytes = slice_bytes * ranks
+        cfg.resident_bytes = resident_bytes
+        cfg.ctrl = ctrl_ptr
+        cfg.ctrl_bytes = ctrl_bytes
+        cfg.sched_stream = self.sched_stream.cuda_stream
+        cfg.copy_streams = ctypes.cast(self._streams_arr, ctypes.POINTER(c_void_p))
+        cfg.admission_cap_bytes = admission_cap_bytes
+        cfg.wait_timeout_ns = int(wait_timeout_s * 1e9)
+        cfg.idle_exit_ns = int(idle_exit_s * 1e9)
+        cfg.grid_ctas = grid_ctas
+        cfg.ingest_quantum = ingest_quantum
+        self.cfg = cfg
+        h = c_void_p()
+        with torch.cuda.device(self.device):
+            check(L.gvm_init(byref(cfg), byref(h)), "gvm_init")
+        self.handle = h
+        self._ranks: dict[int, Rank] = {}
+
+    def attach(self, rank: int) -> Rank:
+        h = c_void_p()
+        check(lib().gvm_attach(self.handle, rank, byref(h)), "gvm_attach")
+        r = Rank(self, rank, h.value)
+        self._ranks[rank] = r
+        return r
+
+    def flush(self) -> None:
+        check(lib().gvm_flush(self.handle), "gvm_flush")
+
+    def flush_if_barrier(self) -> None:
+        if self.mode == "barrier":
+            self.flush()
+
+    def wait_idle(self) -> None:
+        check(lib().gvm_wait_idle(self.handle), "gvm_wait_idle")
+
+    def stats(self) -> dict:
+        s = GvmStats()
+        check(lib().gvm_stats_get(self.handle, byref(s)), "gvm_stats_get")
+        return {name: getattr(s, name) for name, _ in GvmStats._fields_}
+
+    def shutdown(self) -> None:
+        if self.handle is not None:
+            rc = lib().gvm_shutdown(self.handle)
+            self.handle = None
+            check(rc, "gvm_shutdown")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.shutdown()
+
+
+def vadd_f32(a: torch.Tensor, b: torch.Tensor, c: torch.Tensor, stream=None) -> None:
+    """c = a + b on the device (the vector-add task kernel alone)."""
+    check(lib().gvm_vadd_f32(_ptr(a), _ptr(b), _ptr(c), a.numel(), _stream_handle(stream)), "gvm_vadd_f32")
+
+
+def sgemm_scratch_bytes(m: int, n: int, k: int, path: str = "split3") -> int:
+    return lib().gvm_sgemm_scratch_bytes(m, n, k, _PATHS[path])
+
+
+def sgemm_f32(
+    A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, path: str = "split3", scratch: torch.Tensor | None = None,
+    stream=None,
+) -> None:
+    """C = A B on the device (the matrix-multiply task kernel alone)."""
+    m, k = A.shape
+    n = B.shape[1]
+    sp, sb = 0, 0
+    if path == "split3":
+        need = sgemm_scratch_bytes(m, n, k, path)
+        if scratch is None:
+            scratch = torch.empty(need + 256, dtype=torch.uint8, device=A.device)
+        sp = (scratch.data_ptr() + 255) // 256 * 256
+        sb = scratch.numel() - (sp - scratch.data_ptr())
+    check(
+        lib().gvm_sgemm_f32(_ptr(A), _ptr(B), _ptr(C), m, n, k, _PATHS[path], sp, sb, _stream_handle(stream)),
+        "gvm_sgemm_f32",
+    )
+
+
+def kernel_status() -> int:
+    v = c_uint32(0)
+    check(lib().gvm_kernel_status(byref(v)), "gvm_kernel_status")
+    return v.value

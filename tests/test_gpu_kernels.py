@@ -1,0 +1,128 @@
+"""Parity of the task kernels alone (gvm_vadd_f32, gvm_sgemm_f32) against the
+CPU oracle, through the C ABI. Vector add: bit-exact. SGEMM: relative
+Frobenius error <= 1e-5 against the binary64 oracle, and exact on integer
+operands whose products and sums are exact in both arithmetics."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SGEMM_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gvm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1511_07658_gb300 as g
+
+    torch.cuda.set_device(0)
+    return g
+
+
+def bits(x):
+    return np.ascontiguousarray(x).view(np.uint32)
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 4097, 65536, 65536 + 3, (1 << 22) + 5])
+def test_vadd_bitexact(gvm, n):
+    a, b = synth.vadd_inputs(synth.task_seed(7, n % 1000), n)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    tc = torch.full_like(ta, float("nan"))
+    gvm.vadd_f32(ta, tb, tc)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(tc.cpu().numpy()), bits(oracle.vadd(a, b)))
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_vadd_misaligned(gvm, shift):
+    n = 100003
+    a, b = synth.vadd_inputs(99, n + 8)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    tc = torch.zeros(n + 8, device="cuda")
+    gvm.vadd_f32(ta[shift : shift + n], tb[(shift + 1) % 4 : (shift + 1) % 4 + n], tc[shift : shift + n])
+    torch.cuda.synchronize()
+    want = oracle.vadd(a[shift : shift + n], b[(shift + 1) % 4 : (shift + 1) % 4 + n])
+    got = tc.cpu().numpy()
+    assert np.array_equal(bits(got[shift : shift + n]), bits(want))
+    assert np.all(got[:shift] == 0) and np.all(got[shift + n :] == 0)
+
+
+def test_vadd_ieee_cases(gvm, golden):
+    rows = golden("vadd_ieee_cases.txt")
+    a = np.array([int(r[0], 16) for r in rows], dtype=np.uint32).view(np.float32)
+    b = np.array([int(r[1], 16) for r in rows], dtype=np.uint32).view(np.float32)
+    want = np.array([int(r[2], 16) for r in rows], dtype=np.uint32)
+    tc = torch.empty(len(rows), device="cuda")
+    gvm.vadd_f32(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), tc)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(tc.cpu().numpy()), want)
+
+
+SHAPES = [
+    (1, 1, 1),
+    (5, 7, 3),
+    (64, 64, 64),
+    (128, 256, 32),
+    (200, 136, 96),
+    (257, 130, 67),
+    (300, 520, 1000),
+    (512, 512, 512),
+    (129, 257, 513),
+]
+
+
+def run_sgemm(gvm, A, B, path):
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    tC = torch.full((A.shape[0], B.shape[1]), float("nan"), device="cuda")
+    gvm.sgemm_f32(tA, tB, tC, path=path)
+    torch.cuda.synchronize()
+    return tC.cpu().numpy()
+
+
+@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_sgemm_normal_inputs(gvm, path, shape):
+    m, n, k = shape
+    A, B = synth.sgemm_inputs(synth.task_seed(m, n % 1000), m, n, k)
+    C = run_sgemm(gvm, A, B, path)
+    err = oracle.rel_fro_err(C, oracle.sgemm64(A, B))
+    assert err <= SGEMM_TOL, (path, shape, err)
+    from paper_1511_07658_gb300.manager import kernel_status
+
+    assert kernel_status() == 0
+
+
+@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("shape", [(9, 11, 64), (130, 260, 100), (256, 256, 256)])
+def test_sgemm_integer_exact(gvm, path, shape):
+    # |x| <= 16 and K <= 256: every product and partial sum is an integer
+    # below 2^24, exact in binary32, and bf16 holds the operands exactly.
+    m, n, k = shape
+    A, B = synth.sgemm_int_inputs(1234 + k, m, n, k)
+    C = run_sgemm(gvm, A, B, path)
+    exact = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(C.astype(np.float64), exact)
+
+
+def test_split3_identity_closed_form(gvm):
+    # B = I: split3 returns Ah + Al (the dropped lo*lo term multiplies by 0),
+    # which differs from A by at most 2^-16 relative per element (two
+    # roundings to 8-bit significands, unit roundoff 2^-8 each).
+    m = k = 192
+    A, _ = synth.sgemm_inputs(77, m, k, k)
+    C = run_sgemm(gvm, A, np.eye(k, dtype=np.float32), "split3")
+    rel = np.abs(C.astype(np.float64) - A) / np.maximum(np.abs(A.astype(np.float64)), 1e-30)
+    assert rel.max() <= 2.0 ** -16
+    assert np.any(C != A)  # the residual below the two bf16 pieces is dropped
+
+
+def test_fma_identity_exact(gvm):
+    A, _ = synth.sgemm_inputs(78, 100, 60, 60)
+    C = run_sgemm(gvm, A, np.eye(60, dtype=np.float32), "fma")
+    assert np.array_equal(C, A)

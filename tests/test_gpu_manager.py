@@ -1,0 +1,250 @@
+"""Parity of the shared-GPU manager against the CPU oracle, through the C ABI.
+
+Each rank's tasks go through gvm_submit / gvm_flush / gvm_sync; every result
+must equal the oracle's solo result for that task (vector add bit-exact,
+SGEMM relative Frobenius error <= 1e-5), whatever else shares the GPU.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SGEMM_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gvm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1511_07658_gb300 as g
+
+    torch.cuda.set_device(0)
+    return g
+
+
+def bits(x):
+    return np.ascontiguousarray(x).view(np.uint32)
+
+
+def pinned(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+
+
+def submit_spec(rk, spec):
+    """Host-mode submission of a synth.TaskSpec; returns (seq, inputs, out)."""
+    if spec.kind == synth.TASK_VADD:
+        a, b = synth.vadd_inputs(spec.seed, spec.n)
+        out = torch.empty(spec.n, dtype=torch.float32).pin_memory()
+        seq = rk.submit_vadd(pinned(a), pinned(b), out)
+        return seq, (a, b), out
+    A, B = synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
+    out = torch.empty(spec.m, spec.n, dtype=torch.float32).pin_memory()
+    tA, tB = pinned(A), pinned(B)
+    seq = rk.submit_sgemm(tA, tB, out)
+    return seq, (A, B, tA, tB), out
+
+
+def check_result(spec, inputs, out):
+    if spec.kind == synth.TASK_VADD:
+        assert np.array_equal(bits(out.numpy()), bits(oracle.vadd(*inputs))), spec
+    else:
+        err = oracle.rel_fro_err(out.numpy(), oracle.sgemm64(inputs[0], inputs[1]))
+        assert err <= SGEMM_TOL, (spec, err)
+
+
+def run_workload(gvm, w, *, mode="barrier", path="split3", depth=16, slice_mb=128):
+    with gvm.Manager(w.ranks, ring_depth=depth, mode=mode, sgemm_path=path, slice_bytes=slice_mb << 20) as mgr:
+        ranks = [mgr.attach(r) for r in range(w.ranks)]
+        jobs = []
+        for spec in w.tasks:
+            jobs.append((spec, *submit_spec(ranks[spec.rank], spec)))
+        mgr.flush()
+        for spec, seq, inputs, out in jobs:
+            ranks[spec.rank].sync(seq)
+        stats = mgr.stats()
+        results = {(s.rank, s.index): out for s, _, _, out in jobs}
+        for spec, seq, inputs, out in jobs:
+            check_result(spec, inputs, out)
+    assert stats["device_status"] == 0
+    return results
+
+
+@pytest.mark.parametrize("mode", ["barrier", "continuous"])
+def test_vadd_tiny_config_bitexact(gvm, mode):
+    """4 ranks x 8 vector adds, n = 65536, seed rank*1000 + task."""
+    run_workload(gvm, synth.vadd_tiny(), mode=mode)
+
+
+@pytest.mark.parametrize("path", ["fma", "split3"])
+def test_sgemm_shared_subset(gvm, path):
+    """16 ranks sharing the GPU, SGEMM 512^3 (two tasks per rank here; the
+    full 64-per-rank configuration runs in test_gpu_fullsize)."""
+    run_workload(gvm, synth.sgemm_square(ranks=16, per_rank=2), path=path, slice_mb=64)
+
+
+@pytest.mark.parametrize("path", ["fma", "split3"])
+def test_mixed_ragged_tasks(gvm, path):
+    w = synth.Workload("mixed", 3)
+    shapes = [(1, 1, 1), (64, 64, 64), (130, 257, 65), (5, 300, 17)]
+    i = 0
+    for r in range(3):
+        for t in range(6):
+            if (r + t) % 2 == 0:
+                w.tasks.append(synth.TaskSpec(r, t, synth.TASK_VADD, n=[0, 1, 4099, 70001][i % 4], seed=1000 + i))
+            else:
+                m, n, k = shapes[i % 4]
+                w.tasks.append(synth.TaskSpec(r, t, synth.TASK_SGEMM, m=m, n=n, k=k, seed=2000 + i))
+            i += 1
+    run_workload(gvm, w, path=path, depth=8)
+
+
+@pytest.mark.parametrize("path", ["fma", "split3"])
+def test_solo_equals_mix_bitwise(gvm, path):
+    """A task's result alone on the GPU equals its result in the mix, bit for
+    bit (the tile shape is a function of the task's shape only)."""
+    w = synth.Workload("mix", 4)
+    for r in range(4):
+        for t in range(3):
+            if t == 1:
+                w.tasks.append(synth.TaskSpec(r, t, synth.TASK_VADD, n=50000 + r, seed=synth.task_seed(r, t)))
+            else:
+                w.tasks.append(
+                    synth.TaskSpec(r, t, synth.TASK_SGEMM, m=192 + 64 * r, n=320, k=256, seed=synth.task_seed(r, t))
+                )
+    mixed = run_workload(gvm, w, path=path)
+    for spec in w.tasks:
+        solo = synth.Workload("solo", 4, [spec])
+        alone = run_workload(gvm, solo, path=path)
+        key = (spec.rank, spec.index)
+        assert np.array_equal(bits(alone[key].numpy()), bits(mixed[key].numpy())), spec
+
+
+def test_resident_mode(gvm):
+    """Inputs placed in the rank's resident region; no copies in the task."""
+    m = n = k = 256
+    nv = 10000
+    res = 4 * (m * k + k * n + m * n) + 3 * 4 * nv + 1024
+    with gvm.Manager(2, ring_depth=8, sgemm_path="split3", slice_bytes=32 << 20, resident_bytes=res) as mgr:
+        for r in range(2):
+            rk = mgr.attach(r)
+            A, B = synth.sgemm_inputs(synth.task_seed(r, 0), m, n, k)
+            a, b = synth.vadd_inputs(synth.task_seed(r, 1), nv)
+            offA, offB, offC = 0, 4 * m * k, 4 * (m * k + k * n)
+            offa = 4 * (m * k + k * n + m * n)
+            offb, offc = offa + 4 * nv, offa + 8 * nv
+            rk.write(offA, torch.from_numpy(A))
+            rk.write(offB, torch.from_numpy(B))
+            rk.write(offa, torch.from_numpy(a))
+            rk.write(offb, torch.from_numpy(b))
+            s0 = rk.submit_sgemm_resident(offA, offB, offC, m, n, k)
+            s1 = rk.submit_vadd_resident(offa, offb, offc, nv)
+            mgr.flush()
+            rk.sync(s1)
+            assert rk.poll(s0)
+            C = torch.empty(m, n)
+            c = torch.empty(nv)
+            rk.read(offC, C)
+            rk.read(offc, c)
+            assert oracle.rel_fro_err(C.numpy(), oracle.sgemm64(A, B)) <= SGEMM_TOL
+            assert np.array_equal(bits(c.numpy()), bits(oracle.vadd(a, b)))
+
+
+def test_rank_isolation_canaries(gvm):
+    """Data of different ranks coexist safely (Section 5): tasks touch only
+    their own rank's buffers, so canaries elsewhere in the arena survive."""
+    R = 4
+    nv = 4096
+    res = 1 << 20
+    with gvm.Manager(R, ring_depth=8, sgemm_path="split3", slice_bytes=16 << 20, resident_bytes=res) as mgr:
+        ranks = [mgr.attach(r) for r in range(R)]
+        canary = torch.full((res // 4,), 1234.5)
+        for rk in ranks:
+            rk.write(0, canary)
+        seqs = []
+        for r, rk in enumerate(ranks):
+            a, b = synth.vadd_inputs(r, nv)
+            rk.write(0, torch.from_numpy(a))
+            rk.write(4 * nv, torch.from_numpy(b))
+            seqs.append(rk.submit_vadd_resident(0, 4 * nv, 8 * nv, nv))
+            A, B = synth.sgemm_inputs(r + 50, 64, 64, 64)
+            base = 16 * nv
+            rk.write(base, torch.from_numpy(A))
+            rk.write(base + 4 * 64 * 64, torch.from_numpy(B))
+            seqs.append(rk.submit_sgemm_resident(base, base + 4 * 4096, base + 8 * 4096, 64, 64, 64))
+        mgr.flush()
+        for r, rk in enumerate(ranks):
+            rk.sync(seqs[2 * r + 1])
+            back = torch.empty(res // 4)
+            rk.read(0, back)
+            tail = back[(16 * nv + 12 * 4096) // 4 :]
+            assert torch.all(tail == 1234.5), f"rank {r} canary overwritten"
+            assert torch.all(back[3 * nv : 4 * nv] == 1234.5)
+
+
+def test_errors_and_backpressure(gvm):
+    import ctypes
+
+    with gvm.Manager(1, ring_depth=4, sgemm_path="fma", slice_bytes=8 << 20) as mgr:
+        rk = mgr.attach(0)
+        with pytest.raises(gvm.GvmError) as e:
+            mgr.attach(0)
+        assert e.value.code == gvm.GVM_EBUSY
+        # pageable host buffers are refused
+        a = torch.zeros(16)
+        with pytest.raises(gvm.GvmError) as e:
+            rk.submit_vadd(a, a, a)
+        assert e.value.code == gvm.GVM_EINVAL
+        # bad shapes
+        t = gvm.GvmTask()
+        t.type, t.m, t.n, t.k = gvm.GVM_TASK_SGEMM, 0, 4, 4
+        assert gvm.lib().gvm_submit(rk.handle, ctypes.byref(t), None) == gvm.GVM_EINVAL
+        t.type = 7
+        assert gvm.lib().gvm_submit(rk.handle, ctypes.byref(t), None) == gvm.GVM_EINVAL
+        # resident offsets outside the (empty) resident region
+        with pytest.raises(gvm.GvmError) as e:
+            rk.submit_vadd_resident(0, 0, 0, 16)
+        assert e.value.code == gvm.GVM_EINVAL
+        # too big for the staging ring ever
+        big = torch.empty(3 << 20).pin_memory()
+        with pytest.raises(gvm.GvmError) as e:
+            rk.submit_vadd(big, big, big, block=False)
+        assert e.value.code == gvm.GVM_ENOMEM
+        # ring full: 4 slots, nothing runs until flush (barrier mode)
+        x = torch.ones(1000).pin_memory()
+        outs = [torch.empty(1000).pin_memory() for _ in range(5)]
+        seqs = [rk.submit_vadd(x, x, outs[i], block=False) for i in range(4)]
+        with pytest.raises(gvm.GvmError) as e:
+            rk.submit_vadd(x, x, outs[4], block=False)
+        assert e.value.code == gvm.GVM_EAGAIN
+        mgr.flush()
+        rk.sync(seqs[-1])
+        seqs.append(rk.submit_vadd(x, x, outs[4], block=False))
+        mgr.flush()
+        rk.sync(seqs[-1])
+        for o in outs:
+            assert torch.all(o == 2.0)
+
+
+def test_order_and_times(gvm):
+    """Per rank, sync(seq) implies every earlier task of the rank is done,
+    and device timestamps are consistent."""
+    w = synth.vadd_tiny(ranks=2, per_rank=6, n=30000)
+    with gvm.Manager(2, ring_depth=8, mode="continuous") as mgr:
+        ranks = [mgr.attach(r) for r in range(2)]
+        jobs = [(spec, *submit_spec(ranks[spec.rank], spec)) for spec in w.tasks]
+        last = {}
+        for spec, seq, inputs, out in jobs:
+            last[spec.rank] = seq
+        for r, rk in enumerate(ranks):
+            rk.sync(last[r])
+            for spec, seq, inputs, out in jobs:
+                if spec.rank == r:
+                    assert rk.poll(seq)
+                    t0, t1 = rk.task_times(seq)
+                    assert 0 < t0 <= t1
+                    check_result(spec, inputs, out)
