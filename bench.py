@@ -1,0 +1,628 @@
+#!/usr/bin/env python3
+"""Throughput of SPMD ranks sharing one GB300 through the gvm manager.
+
+Workload (default): 16 ranks (one GPU shared by 16 CPU cores), each
+submitting 64 SGEMM tasks C = A B with M = N = K = 512, A and B standard
+normal from seed rank*1000 + task (B from seed + 2^32). One step is the whole
+hot path over that batch: every rank submits its 64 tasks (gvm_submit_many),
+the request barrier flushes them (gvm_flush launches the persistent
+scheduler), every rank syncs (gvm_sync).
+
+  value  tasks/s with the operands resident in HBM (GVM_TASK_RESIDENT),
+         timed with CUDA events on the scheduler stream around each step.
+  e2e    tasks/s through the same API with pinned host buffers: the input
+         copies, the kernel and the output copies are inside the timed
+         region (host wall clock).
+  roofline     the scheduler kernel (the dominant kernel: it runs every tile)
+  cpu_baseline the CPU oracle (binary64) on the host cores, bounded sample
+  plain_per_rank  (--plain) each rank in its own process and context, default
+         stream, synchronous copies, the same FMA kernel (Section 4.1's
+         conventional sharing, Eq. 1)
+
+``--impl reference`` runs the reference arm: the CPU oracle as it stands on
+the host cores, one rank per thread, a bounded sample per step.
+
+Multi-GPU (torchrun): each process runs its own replica of the workload on
+its GPU (ranks are independent; no collective on the data path), and value
+is the tasks of all replicas over the slowest replica's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "tasks/s & GB/s, N ranks on 1 GB300, shared vs per-rank; p50/p99 task latency"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+GB300_SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["gvm", "reference"], default="gvm")
+    p.add_argument("--workload", choices=["sgemm512", "vadd_tiny"], default="sgemm512")
+    p.add_argument("--path", choices=["split3", "fma"], default="split3")
+    p.add_argument("--mode", choices=["barrier", "continuous"], default="barrier")
+    p.add_argument("--skip-e2e", action="store_true")
+    p.add_argument("--skip-cpu", action="store_true")
+    p.add_argument("--plain", action="store_true", help="also time the plain one-context-per-rank form")
+    p.add_argument("--quantum", type=int, default=8)
+    return p.parse_args()
+
+
+# --------------------------------------------------------------- workloads
+
+
+def workload(name):
+    if name == "sgemm512":
+        w = synth.sgemm_square(ranks=16, per_rank=64, side=512)
+        desc = "SGEMM M=N=K=512, 16 ranks x 64 tasks, standard-normal operands"
+    else:
+        w = synth.vadd_tiny(ranks=4, per_rank=8, n=65536)
+        desc = "vector add n=65536, 4 ranks x 8 tasks, uniform [-1,1) operands"
+    return w, desc
+
+
+def task_inputs(spec):
+    if spec.kind == synth.TASK_VADD:
+        return synth.vadd_inputs(spec.seed, spec.n)
+    return synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
+
+
+def gen_inputs(w):
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        return list(ex.map(task_inputs, w.tasks))
+
+
+# --------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+            )
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower() == "active":
+                    reasons.add(nm)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons),
+            "samples": len(self.rows),
+        }
+
+
+# --------------------------------------------------------------- helpers
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return FALLBACK_PEAKS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1511_07658_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources and the same workload; else None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def percentile(xs, q):
+    if not xs:
+        return None
+    xs = sorted(xs)
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+# --------------------------------------------------------------- GPU arm
+
+
+def build_tasks(w, inputs, resident, bufs):
+    """Per rank, a ctypes array of GvmTask for one step."""
+    import paper_1511_07658_gb300 as g
+
+    by_rank = [[] for _ in range(w.ranks)]
+    for spec, inp in zip(w.tasks, inputs):
+        by_rank[spec.rank].append((spec, inp))
+    arrays = []
+    for r, lst in enumerate(by_rank):
+        arr = (g.GvmTask * len(lst))()
+        for i, (spec, inp) in enumerate(lst):
+            t = arr[i]
+            t.type = g.GVM_TASK_VADD if spec.kind == synth.TASK_VADD else g.GVM_TASK_SGEMM
+            t.n = spec.n
+            t.m, t.k = spec.m, spec.k
+            if resident:
+                t.flags = g.GVM_TASK_RESIDENT
+                t.a_off, t.b_off, t.c_off = bufs["res_offs"][(r, spec.index)]
+            else:
+                t.flags = 0
+                a, b, c = bufs["host"][(r, spec.index)]
+                t.a, t.b, t.c = a.data_ptr(), b.data_ptr(), c.data_ptr()
+        arrays.append(arr)
+    return arrays
+
+
+def run_step(mgr, ranks, arrays, pool):
+    """Every rank submits its batch (one thread per rank), flush, sync all."""
+    def submit(r):
+        first, cnt = ranks[r].submit_many(arrays[r])
+        return first + cnt - 1
+
+    lasts = list(pool.map(submit, range(len(ranks))))
+    ev0 = ev1 = None
+    import torch
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(mgr.sched_stream)
+    mgr.flush()
+    ev1.record(mgr.sched_stream)
+    list(pool.map(lambda r: ranks[r].sync(lasts[r]), range(len(ranks))))
+    return ev0, ev1, lasts
+
+
+def gpu_arm(args, w, desc, rank, world):
+    import torch
+
+    import paper_1511_07658_gb300 as g
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    inputs = gen_inputs(w)
+    R = w.ranks
+    per_rank = len(w.tasks) // R
+    # resident region: every task's operands and result
+    sizes = {}
+    res_offs = {}
+    res_need = [0] * R
+    for spec in w.tasks:
+        if spec.kind == synth.TASK_VADD:
+            la = lb = lc = 4 * spec.n
+        else:
+            la, lb, lc = 4 * spec.m * spec.k, 4 * spec.k * spec.n, 4 * spec.m * spec.n
+        off = res_need[spec.rank]
+        res_offs[(spec.rank, spec.index)] = (off, off + la, off + la + lb)
+        res_need[spec.rank] = off + (la + lb + lc + 255) // 256 * 256
+        sizes[(spec.rank, spec.index)] = (la, lb, lc)
+    resident = max(res_need)
+    scratch = 0
+    if args.path == "split3":
+        scratch = sum(g.sgemm_scratch_bytes(s.m, s.n, s.k) for s in w.tasks if s.kind == synth.TASK_SGEMM) // R
+    host_stage = max(sum(sizes[(s.rank, s.index)]) for s in w.tasks) * per_rank
+    slice_bytes = resident + max(scratch, 1 << 20) + host_stage + (64 << 20)
+    slice_bytes = (slice_bytes + (1 << 20) - 1) // (1 << 20) * (1 << 20)
+    mgr = g.Manager(
+        R, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode=args.mode, sgemm_path=args.path,
+        slice_bytes=slice_bytes, resident_bytes=resident, ingest_quantum=args.quantum,
+    )
+    ranks = [mgr.attach(r) for r in range(R)]
+    # place resident operands
+    host = {}
+    for spec, inp in zip(w.tasks, inputs):
+        a, b = inp
+        ta = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        tb = torch.from_numpy(np.ascontiguousarray(b)).pin_memory()
+        la, lb, lc = sizes[(spec.rank, spec.index)]
+        tc = torch.empty(lc // 4, dtype=torch.float32).pin_memory()
+        host[(spec.rank, spec.index)] = (ta, tb, tc)
+        oa, ob, _ = res_offs[(spec.rank, spec.index)]
+        ranks[spec.rank].write(oa, ta)
+        ranks[spec.rank].write(ob, tb)
+    bufs = {"res_offs": res_offs, "host": host}
+    res_arrays = build_tasks(w, inputs, True, bufs)
+    host_arrays = build_tasks(w, inputs, False, bufs)
+    pool = ThreadPoolExecutor(max_workers=R)
+    sampler = ClockSampler(dev)
+
+    # ---- device-resident value
+    for _ in range(args.warmup):
+        run_step(mgr, ranks, res_arrays, pool)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.start()
+    t_step = []
+    t_kernel = []
+    st0 = torch.cuda.Event(enable_timing=True)
+    st1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    st0.record(mgr.sched_stream)
+    events = []
+    for _ in range(args.steps):
+        e_step0 = torch.cuda.Event(enable_timing=True)
+        e_step0.record(mgr.sched_stream)
+        ev0, ev1, lasts = run_step(mgr, ranks, res_arrays, pool)
+        e_step1 = torch.cuda.Event(enable_timing=True)
+        e_step1.record(mgr.sched_stream)
+        events.append((e_step0, ev0, ev1, e_step1))
+    st1.record(mgr.sched_stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    sampler.stop()
+    for e_step0, ev0, ev1, e_step1 in events:
+        t_step.append(e_step0.elapsed_time(e_step1) / 1e3)
+        t_kernel.append(ev0.elapsed_time(ev1) / 1e3)
+    total_s = st0.elapsed_time(st1) / 1e3
+    # device-side service latency of the last step's tasks
+    lat = []
+    for r, rk in enumerate(ranks):
+        for s in range(lasts[r] - per_rank + 1, lasts[r] + 1):
+            t0, t1 = rk.task_times(s)
+            lat.append((t1 - t0) / 1e3)
+    tasks_per_step = len(w.tasks)
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = tasks_per_step * args.steps * world / total_s
+    stats_after_value = mgr.stats()
+
+    # ---- end to end (host buffers, copies inside the timed region)
+    e2e = None
+    if not args.skip_e2e:
+        for _ in range(max(1, args.warmup)):
+            run_step(mgr, ranks, host_arrays, pool)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e_steps = max(3, args.steps // 2)
+        h0 = time.perf_counter()
+        for _ in range(e_steps):
+            run_step(mgr, ranks, host_arrays, pool)
+        h_s = time.perf_counter() - h0
+        if world > 1:
+            t = torch.tensor([h_s], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            h_s = float(t.item())
+        h2d = sum(sizes[k][0] + sizes[k][1] for k in sizes)
+        d2h = sum(sizes[k][2] for k in sizes)
+        e2e = {
+            "value": tasks_per_step * e_steps * world / h_s,
+            "unit": "tasks/s",
+            "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "host_link_gbs": (h2d + d2h) * e_steps / h_s / 1e9,
+            "ms_per_step": 1e3 * h_s / e_steps,
+        }
+
+    # ---- parity spot check of the last step (resident outputs), sampled rows
+    import oracle
+
+    spot = []
+    for r in (0, R - 1):
+        spec = [s for s in w.tasks if s.rank == r][-1]
+        inp = inputs[w.tasks.index(spec)]
+        _, _, oc = res_offs[(r, spec.index)]
+        if spec.kind == synth.TASK_SGEMM:
+            C = torch.empty(spec.m, spec.n)
+            ranks[r].read(oc, C)
+            rows = np.arange(0, spec.m, 37)
+            err = oracle.rel_fro_err(C.numpy()[rows], oracle.sgemm64(inp[0][rows], inp[1]))
+            spot.append(err)
+        else:
+            c = torch.empty(spec.n)
+            ranks[r].read(oc, c)
+            spot.append(0.0 if np.array_equal(c.numpy().view(np.uint32), oracle.vadd(*inp).view(np.uint32)) else 1.0)
+
+    mgr.shutdown()
+    pool.shutdown()
+    pk, pk_kind = peaks()
+    kmean = statistics.mean(t_kernel)
+    if w.tasks[0].kind == synth.TASK_SGEMM:
+        flops = sum(s.flops for s in w.tasks)
+        if args.path == "split3":
+            peak = pk["bf16_tflops"] / 3.0
+            roof = {"bound": "tensor", "unit": "TFLOP/s",
+                    "peak_basis": f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"}
+        else:
+            peak = GB300_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "unit": "TFLOP/s",
+                    "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+        achieved = flops / kmean / 1e12
+    else:
+        byts = sum(12 * s.n for s in w.tasks)
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "unit": "GB/s", "peak_basis": f"HBM copy {pk['hbm_gbs']} GB/s ({pk_kind})"}
+        achieved = byts / kmean / 1e9
+    key = f"sched_kernel/{args.path}/{args.workload}"
+    roof.update({"kernel": f"gvm::sched_kernel<{args.path}>", "achieved": achieved, "peak": peak,
+                 "frac": achieved / peak, "traffic": ncu_traffic(key), "launch_ms": kmean * 1e3})
+    clocks = sampler.summary()
+    cfg = {
+        "workload": desc,
+        "ranks": R,
+        "tasks_per_rank": per_rank,
+        "sgemm_path": args.path,
+        "mode": args.mode,
+        "operands": "resident in HBM for value; pinned host buffers for e2e",
+        "l2": "inputs larger than L2 (2 GiB of operands per step)" if args.workload == "sgemm512"
+        else "inputs smaller than L2; latency-bound",
+        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU, 16 SPMD ranks as host threads",
+    }
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "tasks/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16x3->f32" if args.path == "split3" else "f32",
+        "data": "synthetic",
+        "config": cfg,
+        "gbps": {"hbm_operands": sum(sum(v) for v in sizes.values()) * args.steps * world / total_s / 1e9},
+        "latency_us": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "kind": "device ingest->done, last step"},
+        "wall_tasks_per_s": tasks_per_step * args.steps / wall,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "parity_spot_rel_err": max(spot) if spot else None,
+        "manager_stats": {k: stats_after_value[k] for k in ("launches", "staged_peak", "device_status")},
+    }
+    return out
+
+
+# --------------------------------------------------------------- CPU oracle
+
+
+def oracle_rate(w, inputs_fn, max_tasks, threads):
+    """The CPU oracle as it stands: one rank per thread, each rank's first
+    tasks in order, until max_tasks tasks are done."""
+    import oracle
+
+    by_rank = w.by_rank()
+    picks = []
+    i = 0
+    while len(picks) < max_tasks:
+        for lst in by_rank:
+            if i < len(lst) and len(picks) < max_tasks:
+                picks.append(lst[i])
+        i += 1
+    data = [inputs_fn(s) for s in picks]
+    oracle.build()
+
+    def one(j):
+        s = picks[j]
+        if s.kind == synth.TASK_VADD:
+            oracle.vadd(*data[j])
+        else:
+            oracle.sgemm64(*data[j])
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(len(picks))))
+    dt = time.perf_counter() - t0
+    return len(picks) / dt, len(picks), dt
+
+
+def cpu_baseline(w):
+    threads = min(16, os.cpu_count() or 1)
+    n = 2 * threads if w.tasks[0].kind == synth.TASK_SGEMM else len(w.tasks)
+    rate, cnt, dt = oracle_rate(w, task_inputs, n, threads)
+    return {"value": rate, "unit": "tasks/s", "cores": threads, "kind": "oracle",
+            "sample": f"{cnt} tasks of the workload ({dt:.1f} s), one rank per thread, binary64 SGEMM"}
+
+
+def reference_arm(args, w, desc):
+    threads = min(16, os.cpu_count() or 1)
+    n = threads if w.tasks[0].kind == synth.TASK_SGEMM else len(w.tasks)
+    for _ in range(args.warmup):
+        oracle_rate(w, task_inputs, n, threads)
+    total = 0.0
+    cnt_all = 0
+    for _ in range(args.steps):
+        rate, cnt, dt = oracle_rate(w, task_inputs, n, threads)
+        total += dt
+        cnt_all += cnt
+    value = cnt_all / total
+    sample = f"{n} tasks per step (one per rank thread) of the workload, binary64 SGEMM"
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "tasks/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "ranks": w.ranks, "tasks_per_rank": len(w.tasks) // w.ranks},
+        "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# --------------------------------------------------------------- plain form
+
+
+def _plain_worker(args_tuple):
+    """One rank in its own process and CUDA context (the conventional,
+    non-virtualized sharing of Section 4.1): default stream, synchronous
+    copies, one task after another."""
+    (rank, per_rank, m, n, k, path, barrier, q) = args_tuple
+    t_import = time.perf_counter()
+    import torch
+
+    import paper_1511_07658_gb300 as g
+
+    A, B = synth.sgemm_inputs(synth.task_seed(rank, 0), m, n, k)
+    hA = torch.from_numpy(A)
+    hB = torch.from_numpy(B)
+    barrier.wait()
+    t0 = time.time()
+    torch.cuda.init()
+    dA = torch.empty(m, k, device="cuda")
+    dB = torch.empty(k, n, device="cuda")
+    dC = torch.empty(m, n, device="cuda")
+    hA = hA.pin_memory()
+    hB = hB.pin_memory()
+    hC = torch.empty(m, n).pin_memory()
+    torch.cuda.synchronize()
+    t_init = time.time() - t0
+    for _ in range(per_rank):
+        dA.copy_(hA)
+        dB.copy_(hB)
+        g.sgemm_f32(dA, dB, dC, path="fma")
+        hC.copy_(dC)
+        torch.cuda.synchronize()
+    t1 = time.time()
+    q.put((rank, t0, t1, t_init, time.perf_counter() - t_import))
+
+
+def plain_per_rank(w):
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    R = w.ranks
+    per_rank = len(w.tasks) // R
+    spec = w.tasks[0]
+    barrier = ctx.Barrier(R)
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_plain_worker, args=((r, per_rank, spec.m, spec.n, spec.k, "fma", barrier, q),))
+             for r in range(R)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=600) for _ in range(R)]
+    for p in procs:
+        p.join(timeout=60)
+    t0 = min(r[1] for r in res)
+    t1 = max(r[2] for r in res)
+    init = statistics.mean(r[3] for r in res)
+    turnaround = t1 - t0
+    return {
+        "value": len(w.tasks) / turnaround,
+        "value_excl_init": len(w.tasks) / max(1e-9, turnaround - max(r[3] for r in res)),
+        "unit": "tasks/s",
+        "turnaround_s": turnaround,
+        "mean_t_init_s": init,
+        "form": f"{R} processes, one CUDA context each, default stream, synchronous copies, FMA SGEMM",
+    }
+
+
+# --------------------------------------------------------------- main
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    w, desc = workload(args.workload)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(reference_arm(args, w, desc)))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out = gpu_arm(args, w, desc, rank, world)
+    if rank == 0:
+        if not args.skip_cpu:
+            out["cpu_baseline"] = cpu_baseline(w)
+        if args.plain and w.tasks[0].kind == synth.TASK_SGEMM:
+            out["plain_per_rank"] = plain_per_rank(w)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -70,9 +70,9 @@ extern "C" {
 /* ---- manager modes ------------------------------------------------------ */
 #define GVM_MODE_BARRIER 0    /* Section 5 request barrier: gvm_flush runs the scheduler
                                  until every task submitted before it has completed */
-#define GVM_MODE_CONTINUOUS 1 /* the scheduler stays resident and takes tasks as they
-                                 arrive; it exits after idle_exit_ns without work and is
-                                 relaunched by the next gvm_submit / gvm_sync */
+#define GVM_MODE_CONTINUOUS 1 /* the scheduler is launched by gvm_init, stays resident
+                                 and takes tasks as they arrive, until gvm_shutdown. It
+                                 holds every SM meanwhile (idle CTAs sleep between polls) */
 
 #define GVM_MAX_RANKS 1024
 
@@ -99,8 +99,8 @@ typedef struct gvm_config {
                                    across all ranks; 0 = only the slices bound it */
   uint64_t wait_timeout_ns; /* bound on each device-side dependency wait and on each
                                host wait in gvm_sync / gvm_wait_idle; 0 = 10 s */
-  uint64_t idle_exit_ns;    /* continuous mode: idle time after which the scheduler
-                               kernel exits; 0 = 1 s */
+  uint64_t idle_poll_ns;    /* sleep of an idle scheduler CTA between polls of the
+                               rings; 0 = 1000 ns */
   int32_t grid_ctas;        /* scheduler CTAs; 0 = one per SM */
   int32_t ingest_quantum;   /* tasks taken from one rank per ingest pass; 0 = 4 */
 } gvm_config;
@@ -185,8 +185,12 @@ GVM_API int gvm_sync(gvm_rank* rank, uint64_t seq);
 GVM_API int gvm_poll(gvm_rank* rank, uint64_t seq);
 
 /* Barrier mode: launches the scheduler on sched_stream; it drains every task
-   submitted (on any rank) before this call and then exits. Continuous mode:
-   makes sure the scheduler is running. Returns without waiting. */
+   submitted (on any rank) before this call and then exits. A task submitted
+   after the last flush is not run (gvm_sync on it returns GVM_ESTATE) until
+   the next flush. Continuous mode: nothing to do. Returns without waiting.
+   Output copies of host-mode tasks are enqueued only after the launch that
+   produces them (by gvm_sync / gvm_poll of the owning rank), so a stream wait
+   never sits ahead of its producer in a shared hardware queue. */
 GVM_API int gvm_flush(gvm_ctx* ctx);
 
 /* Waits until the scheduler kernel and all copy streams are idle. */
@@ -203,7 +207,8 @@ GVM_API int gvm_rank_read(gvm_rank* rank, uint64_t off, void* dst, uint64_t byte
    with their own kernels or copies), or NULL for a bad handle. */
 GVM_API void* gvm_rank_resident_ptr(gvm_rank* rank);
 
-/* RLS(): waits for the rank's tasks, then releases the rank. */
+/* RLS(): waits for the rank's tasks, then releases the rank. Barrier mode:
+   GVM_ESTATE if some task was submitted after the last gvm_flush. */
 GVM_API int gvm_detach(gvm_rank* rank);
 
 /* Stops the scheduler after in-flight work, waits for the streams, frees the

@@ -44,7 +44,7 @@ class GvmConfig(ctypes.Structure):
         ("copy_streams", POINTER(c_void_p)),
         ("admission_cap_bytes", c_uint64),
         ("wait_timeout_ns", c_uint64),
-        ("idle_exit_ns", c_uint64),
+        ("idle_poll_ns", c_uint64),
         ("grid_ctas", c_int32),
         ("ingest_quantum", c_int32),
     ]

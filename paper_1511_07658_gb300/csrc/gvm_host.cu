@@ -34,6 +34,12 @@ namespace {
 struct SlotInfo {
   uint64_t stage_end = 0;  // staging-ring counter after this task's allocation
   uint64_t bytes = 0;      // staging bytes this task holds (incl. wrap waste)
+  // Output operations of a host-mode task, pushed on the rank's output stream
+  // only after the scheduler launch that will write its done word.
+  void* c_host = nullptr;
+  uint64_t c_dev = 0;
+  uint64_t c_bytes = 0;
+  bool needs_out = false;
 };
 
 inline uint32_t tag_of(uint64_t seq) { return (uint32_t)(seq + 1); }
@@ -52,6 +58,9 @@ struct gvm_rank {
   bool attached = false;
   uint64_t next_seq = 0;  // sequence number of the next submission
   uint64_t synced = 0;    // tasks 0 .. synced-1 are known complete
+  uint64_t out_pushed = 0;           // tasks whose output operations are on the output stream
+  std::atomic<uint64_t> published{0};  // next_seq as seen by gvm_flush
+  std::atomic<uint64_t> flushed{0};    // barrier mode: tasks covered by a launched flush
   uint64_t slice = 0;     // device address of the rank's slice
   uint64_t ring_base = 0, ring_bytes = 0;
   uint64_t ring_head = 0, ring_tail = 0;  // monotonic byte counters
@@ -112,16 +121,6 @@ int launch_locked(gvm_ctx* ctx, uint32_t drain) {
   return GVM_OK;
 }
 
-// Continuous mode: relaunch if the last launch has exited (idle timeout).
-int ensure_running(gvm_ctx* ctx) {
-  if (ctx->cfg.mode != GVM_MODE_CONTINUOUS) return GVM_OK;
-  if (ld_acq(&ctx->shared->exit_gen) != ctx->launch_gen) return GVM_OK;  // running
-  std::lock_guard<std::mutex> g(ctx->launch_mu);
-  if (ctx->shut) return GVM_OK;
-  if (ld_acq(&ctx->shared->exit_gen) != ctx->launch_gen) return GVM_OK;
-  return launch_locked(ctx, 0);
-}
-
 // Advance `synced` over completed tasks and release their staging bytes.
 void reap(gvm_rank* r) {
   gvm_ctx* ctx = r->ctx;
@@ -158,6 +157,48 @@ uint64_t stage_alloc(gvm_rank* r, uint64_t bytes, uint64_t* held) {
   r->ring_head = pos + bytes;
   *held = waste + bytes;
   return r->ring_base + (pos % r->ring_bytes);
+}
+
+// Pushes the output operations (wait on done, device-to-host copy, completion
+// word) of tasks out_pushed .. upto-1 on the rank's output stream. Called only
+// once the scheduler launch that will write those done words has been pushed:
+// a blocked wait can then never sit ahead of its own producer in a hardware
+// queue that two streams share.
+int push_out_ops(gvm_rank* r, uint64_t upto) {
+  gvm_ctx* ctx = r->ctx;
+  const DriverApi* api = driver_api();
+  const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
+  while (r->out_pushed < upto) {
+    const uint64_t s = r->out_pushed;
+    SlotInfo& si = r->slots[s & (D - 1)];
+    if (si.needs_out) {
+      const uint32_t idx = (uint32_t)r->id * D + (uint32_t)(s & (D - 1));
+      const uint32_t tag = tag_of(s);
+      CUresult cr = api->wait_value32(reinterpret_cast<CUstream>(r->out_stream),
+                                      reinterpret_cast<CUdeviceptr>(ctx->params.done + idx), tag,
+                                      CU_STREAM_WAIT_VALUE_EQ);
+      cudaError_t e = cudaSuccess;
+      if (cr == CUDA_SUCCESS && si.c_bytes)
+        e = cudaMemcpyAsync(si.c_host, reinterpret_cast<void*>(si.c_dev), si.c_bytes, cudaMemcpyDeviceToHost,
+                            r->out_stream);
+      if (cr == CUDA_SUCCESS && e == cudaSuccess)
+        cr = api->write_value32(reinterpret_cast<CUstream>(r->out_stream),
+                                reinterpret_cast<CUdeviceptr>(&ctx->params.host_complete[idx].tag), tag,
+                                CU_STREAM_WRITE_VALUE_DEFAULT);
+      if (cr != CUDA_SUCCESS || e != cudaSuccess) return GVM_EDEVICE;
+      ctx->d2h.fetch_add(si.c_bytes);
+      si.needs_out = false;
+    }
+    r->out_pushed = s + 1;
+  }
+  return GVM_OK;
+}
+
+// Barrier mode: output operations for the tasks covered by a launched flush.
+int push_flushed(gvm_rank* r) {
+  if (r->ctx->cfg.mode != GVM_MODE_BARRIER) return GVM_OK;
+  const uint64_t f = std::min(r->flushed.load(std::memory_order_acquire), r->next_seq);
+  return push_out_ops(r, f);
 }
 
 bool is_pinned(const void* p) {
@@ -207,7 +248,7 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   const uint64_t resident = align_up(cfg.resident_bytes, 256);
   if (slice == 0 || resident > slice) return GVM_EINVAL;
   if (cfg.wait_timeout_ns == 0) cfg.wait_timeout_ns = 10ull * 1000 * 1000 * 1000;
-  if (cfg.idle_exit_ns == 0) cfg.idle_exit_ns = 1000ull * 1000 * 1000;
+  if (cfg.idle_poll_ns == 0) cfg.idle_poll_ns = 1000;
   if (cfg.ingest_quantum <= 0) cfg.ingest_quantum = 4;
   for (int i = 0; i < 2 * cfg.max_ranks; ++i)
     if (!cfg.copy_streams[i]) return GVM_EINVAL;
@@ -280,7 +321,7 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   p.drain = 0;
   p.launch_gen = 0;
   p.wait_timeout_ns = cfg.wait_timeout_ns;
-  p.idle_exit_ns = cfg.idle_exit_ns;
+  p.idle_poll_ns = cfg.idle_poll_ns;
 
   ctx->ranks.resize(R);
   for (uint32_t r = 0; r < R; ++r) {
@@ -297,6 +338,7 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   }
 
   if (cfg.mode == GVM_MODE_CONTINUOUS) {
+    // Resident until gvm_shutdown: launched before any output wait is pushed.
     std::lock_guard<std::mutex> g(ctx->launch_mu);
     int rc = launch_locked(ctx.get(), 0);
     if (rc != GVM_OK) {
@@ -458,26 +500,27 @@ int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
       cr = api->write_value32(reinterpret_cast<CUstream>(r->in_stream),
                               reinterpret_cast<CUdeviceptr>(ctx->params.ready + idx), tag,
                               CU_STREAM_WRITE_VALUE_DEFAULT);
-    if (e == cudaSuccess && cr == CUDA_SUCCESS)
-      cr = api->wait_value32(reinterpret_cast<CUstream>(r->out_stream),
-                             reinterpret_cast<CUdeviceptr>(ctx->params.done + idx), tag, CU_STREAM_WAIT_VALUE_EQ);
-    if (e == cudaSuccess && cr == CUDA_SUCCESS && bytes_c)
-      e = cudaMemcpyAsync(t->c, reinterpret_cast<void*>(dcp), bytes_c, cudaMemcpyDeviceToHost, r->out_stream);
-    if (e == cudaSuccess && cr == CUDA_SUCCESS)
-      cr = api->write_value32(reinterpret_cast<CUstream>(r->out_stream),
-                              reinterpret_cast<CUdeviceptr>(&ctx->params.host_complete[idx].tag), tag,
-                              CU_STREAM_WRITE_VALUE_DEFAULT);
     if (e != cudaSuccess || cr != CUDA_SUCCESS) return GVM_EDEVICE;  // manager now unusable for this rank
     ctx->h2d.fetch_add(bytes_a + bytes_b);
-    ctx->d2h.fetch_add(bytes_c);
+    si.c_host = t->c;
+    si.c_dev = dcp;
+    si.c_bytes = bytes_c;
+    si.needs_out = true;
+  } else {
+    si.needs_out = false;
   }
 
   // ---- publish
   __atomic_store_n(&ctx->heads[r->id].head, (uint32_t)(seq + 1), __ATOMIC_RELEASE);
   r->next_seq = seq + 1;
+  r->published.store(seq + 1, std::memory_order_release);
   ctx->submitted.fetch_add(1);
   if (seq_out) *seq_out = seq;
-  return ensure_running(ctx);
+  if (ctx->cfg.mode == GVM_MODE_CONTINUOUS) {
+    // The resident scheduler was launched before any output wait was pushed.
+    return push_out_ops(r, r->next_seq);
+  }
+  return GVM_OK;
 }
 
 int gvm_submit_many(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* first_seq) {
@@ -499,6 +542,7 @@ int gvm_poll(gvm_rank* r, uint64_t seq) {
   if (!r) return GVM_EINVAL;
   std::lock_guard<std::mutex> g(r->mu);
   if (seq >= r->next_seq) return GVM_EINVAL;
+  if (push_flushed(r) != GVM_OK) return GVM_EDEVICE;
   reap(r);
   if (r->synced > seq) return 1;
   const uint32_t D = (uint32_t)r->ctx->cfg.ring_depth;
@@ -513,6 +557,11 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
   gvm_ctx* ctx = r->ctx;
   std::unique_lock<std::mutex> g(r->mu);
   if (seq >= r->next_seq) return GVM_EINVAL;
+  // Barrier mode: a task submitted after the last gvm_flush never runs
+  // until the next one.
+  if (ctx->cfg.mode == GVM_MODE_BARRIER && seq >= r->flushed.load(std::memory_order_acquire))
+    return GVM_ESTATE;
+  if (push_flushed(r) != GVM_OK) return GVM_EDEVICE;
   uint64_t last = r->synced;
   uint64_t t_prog = now_ns();
   uint32_t spins = 0;
@@ -528,8 +577,6 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
       return GVM_ETIMEDOUT;
     }
     if ((++spins & 63) == 0) {
-      int rc = ensure_running(ctx);
-      if (rc != GVM_OK) return rc;
       cudaError_t e = cudaStreamQuery(ctx->sched);
       if (e != cudaSuccess && e != cudaErrorNotReady) return GVM_EDEVICE;
       g.unlock();
@@ -542,9 +589,19 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
 int gvm_flush(gvm_ctx* ctx) {
   if (!ctx) return GVM_EINVAL;
   if (ctx->shut) return GVM_ESTATE;
-  if (ctx->cfg.mode == GVM_MODE_CONTINUOUS) return ensure_running(ctx);
+  if (ctx->cfg.mode == GVM_MODE_CONTINUOUS) return GVM_OK;  // the scheduler is resident
   std::lock_guard<std::mutex> g(ctx->launch_mu);
-  return launch_locked(ctx, 1);
+  // Every task published before this point is drained by the launch below.
+  std::vector<uint64_t> upto(ctx->ranks.size());
+  for (size_t i = 0; i < ctx->ranks.size(); ++i) upto[i] = ctx->ranks[i]->published.load(std::memory_order_acquire);
+  const int rc = launch_locked(ctx, 1);
+  if (rc != GVM_OK) return rc;
+  for (size_t i = 0; i < ctx->ranks.size(); ++i) {
+    uint64_t f = ctx->ranks[i]->flushed.load();
+    while (f < upto[i] && !ctx->ranks[i]->flushed.compare_exchange_weak(f, upto[i])) {
+    }
+  }
+  return GVM_OK;
 }
 
 int gvm_wait_idle(gvm_ctx* ctx) {
@@ -583,6 +640,7 @@ void* gvm_rank_resident_ptr(gvm_rank* r) { return r ? reinterpret_cast<void*>(r-
 int gvm_detach(gvm_rank* r) {
   if (!r) return GVM_EINVAL;
   if (!r->attached) return GVM_ESTATE;
+  if (r->ctx->cfg.mode == GVM_MODE_BARRIER && r->flushed.load() < r->published.load()) return GVM_ESTATE;
   if (r->next_seq > 0) {
     int rc = gvm_sync(r, r->next_seq - 1);
     if (rc != GVM_OK) return rc;
@@ -598,20 +656,22 @@ int gvm_shutdown(gvm_ctx* ctx) {
   {
     std::lock_guard<std::mutex> g(ctx->launch_mu);
     if (ctx->shut) return GVM_ESTATE;
-    // Drain: every task already submitted runs to completion first.
+    ctx->shut = true;
+    // Barrier mode: one last drain for tasks submitted since the last flush.
     bool pending = false;
     for (auto& rk : ctx->ranks)
-      if (__atomic_load_n(&ctx->heads[rk->id].head, __ATOMIC_ACQUIRE) != (uint32_t)rk->next_seq ||
-          rk->synced < rk->next_seq)
-        pending = true;
-    if (ctx->cfg.mode == GVM_MODE_BARRIER) {
-      if (pending && launch_locked(ctx, 1) != GVM_OK) rc = GVM_EDEVICE;
-    } else if (ld_acq(&ctx->shared->exit_gen) == ctx->launch_gen && pending) {
-      if (launch_locked(ctx, 0) != GVM_OK) rc = GVM_EDEVICE;
+      if (rk->flushed.load() < rk->published.load()) pending = true;
+    if (ctx->cfg.mode == GVM_MODE_BARRIER && pending) {
+      if (launch_locked(ctx, 1) != GVM_OK) rc = GVM_EDEVICE;
+      for (auto& rk : ctx->ranks) rk->flushed.store(rk->published.load());
     }
-    ctx->shut = true;
   }
+  // Continuous mode: the resident scheduler drains what is pending, then exits.
   __atomic_store_n(&ctx->shared->stop, 1u, __ATOMIC_RELEASE);
+  for (auto& rk : ctx->ranks) {
+    std::lock_guard<std::mutex> g(rk->mu);
+    if (rc == GVM_OK && push_out_ops(rk.get(), rk->next_seq) != GVM_OK) rc = GVM_EDEVICE;
+  }
   if (cudaStreamSynchronize(ctx->sched) != cudaSuccess) rc = GVM_EDEVICE;
   const bool device_ok = ld_acq(&ctx->shared->status) == 0;
   for (auto& rk : ctx->ranks) {

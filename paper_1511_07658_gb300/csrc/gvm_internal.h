@@ -152,7 +152,7 @@ struct SchedParams {
   uint32_t drain;        // 1: exit once every published descriptor is consumed
   uint32_t launch_gen;
   uint64_t wait_timeout_ns;
-  uint64_t idle_exit_ns;
+  uint64_t idle_poll_ns;
 };
 
 // Control-block layout inside the caller's ctrl buffer.

@@ -23,8 +23,9 @@
 //
 // Every wait is bounded (wait_timeout_ns); a wait that runs out records a
 // status word in host memory and stops the kernel. In continuous mode the
-// kernel exits after idle_exit_ns without work; in barrier (drain) mode it
-// exits once every descriptor published before its launch has been taken.
+// kernel stays resident until the host sets the stop word (idle CTAs sleep
+// idle_poll_ns between polls); in barrier (drain) mode it exits once every
+// descriptor published before its launch has been taken.
 #include "gvm_device.cuh"
 #include "gvm_runtime.h"
 
@@ -302,8 +303,6 @@ __device__ int acquire(const SchedParams& p, uint32_t& task, uint32_t& phase, ui
         uint32_t stop = 0;
         if (lane == 0) stop = ld_acquire_sys(&p.host_shared->stop);
         if (bcast(stop)) return 0;
-        if (idle_since == 0) idle_since = now;
-        else if (now - idle_since > p.idle_exit_ns) return 0;
       } else {
         if (stall_since == 0) stall_since = now;
         else if (now - stall_since > p.wait_timeout_ns) {
@@ -313,7 +312,7 @@ __device__ int acquire(const SchedParams& p, uint32_t& task, uint32_t& phase, ui
         }
       }
     }
-    __nanosleep(r.locked_out ? 200 : 1000);
+    __nanosleep(r.locked_out ? 200u : (uint32_t)p.idle_poll_ns);
   }
 }
 

@@ -199,7 +199,7 @@ class Manager:
         resident_bytes: int = 0,
         admission_cap_bytes: int = 0,
         wait_timeout_s: float = 10.0,
-        idle_exit_s: float = 1.0,
+        idle_poll_ns: int = 1000,
         grid_ctas: int = 0,
         ingest_quantum: int = 4,
         device: int | None = None,
@@ -238,7 +238,7 @@ class Manager:
         cfg.copy_streams = ctypes.cast(self._streams_arr, ctypes.POINTER(c_void_p))
         cfg.admission_cap_bytes = admission_cap_bytes
         cfg.wait_timeout_ns = int(wait_timeout_s * 1e9)
-        cfg.idle_exit_ns = int(idle_exit_s * 1e9)
+        cfg.idle_poll_ns = idle_poll_ns
         cfg.grid_ctas = grid_ctas
         cfg.ingest_quantum = ingest_quantum
         self.cfg = cfg
