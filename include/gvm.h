@@ -72,7 +72,10 @@ extern "C" {
                                  until every task submitted before it has completed */
 #define GVM_MODE_CONTINUOUS 1 /* the scheduler is launched by gvm_init, stays resident
                                  and takes tasks as they arrive, until gvm_shutdown. It
-                                 holds every SM meanwhile (idle CTAs sleep between polls) */
+                                 holds every SM meanwhile (idle CTAs sleep between polls),
+                                 so a device-wide synchronisation in the process
+                                 (cudaDeviceSynchronize, cudaFree, cudaFreeHost) waits
+                                 until gvm_shutdown */
 
 #define GVM_MAX_RANKS 1024
 
@@ -91,10 +94,13 @@ typedef struct gvm_config {
   void* ctrl;             /* caller-owned device memory for control words and the
                              device task table, >= gvm_ctrl_bytes(cfg), 256-aligned */
   uint64_t ctrl_bytes;
-  void* sched_stream;     /* cudaStream_t on which the scheduler kernel is launched */
-  void* const* copy_streams; /* 2*max_ranks cudaStream_t: [2r] carries rank r's input
-                                copies, [2r+1] its output copies (Section 4.2.1: one
-                                stream per process) */
+  void* sched_stream;     /* cudaStream_t on which the scheduler kernel is launched, or
+                             NULL: the manager creates a non-blocking stream */
+  void* const* copy_streams; /* 2*max_ranks distinct cudaStream_t: [2r] carries rank r's
+                                input copies, [2r+1] its output copies (Section 4.2.1:
+                                one stream per process), or NULL: the manager creates
+                                them. Streams it creates are destroyed by gvm_shutdown;
+                                see gvm_stream */
   uint64_t admission_cap_bytes; /* cap on staging bytes held by admitted, unfinished tasks
                                    across all ranks; 0 = only the slices bound it */
   uint64_t wait_timeout_ns; /* bound on each device-side dependency wait and on each
@@ -202,6 +208,11 @@ GVM_API int gvm_wait_idle(gvm_ctx* ctx);
    outputs back; they are not part of a task. */
 GVM_API int gvm_rank_write(gvm_rank* rank, uint64_t off, const void* src, uint64_t bytes);
 GVM_API int gvm_rank_read(gvm_rank* rank, uint64_t off, void* dst, uint64_t bytes);
+
+/* The manager's streams (cudaStream_t as void*): which = -1 is the scheduler
+   stream, 2r / 2r+1 the input / output stream of rank r. NULL when out of
+   range. Valid until gvm_shutdown. */
+GVM_API void* gvm_stream(gvm_ctx* ctx, int32_t which);
 
 /* Device address of the rank's resident region (for callers that fill it
    with their own kernels or copies), or NULL for a bad handle. */

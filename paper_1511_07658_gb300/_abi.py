@@ -101,6 +101,7 @@ PROTOTYPES = {
     "gvm_rank_write": (c_int, [c_void_p, c_uint64, c_void_p, c_uint64]),
     "gvm_rank_read": (c_int, [c_void_p, c_uint64, c_void_p, c_uint64]),
     "gvm_rank_resident_ptr": (c_void_p, [c_void_p]),
+    "gvm_stream": (c_void_p, [c_void_p, c_int32]),
     "gvm_detach": (c_int, [c_void_p]),
     "gvm_shutdown": (c_int, [c_void_p]),
     "gvm_stats_get": (c_int, [c_void_p, POINTER(GvmStats)]),

@@ -14,6 +14,8 @@
 // Resident-mode tasks use no stream at all: the scheduler reads the ring and
 // writes the completion word itself.
 #include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -43,6 +45,22 @@ struct SlotInfo {
 };
 
 inline uint32_t tag_of(uint64_t seq) { return (uint32_t)(seq + 1); }
+
+// GVM_DEBUG=1 in the environment traces manager state changes on stderr.
+bool debug_on() {
+  static const bool on = getenv("GVM_DEBUG") != nullptr;
+  return on;
+}
+#define GVM_TRACE(...)                     \
+  do {                                     \
+    if (debug_on()) {                      \
+      fprintf(stderr, "[gvm] " __VA_ARGS__); \
+      fputc('\n', stderr);                 \
+    }                                      \
+  } while (0)
+
+// gvm_sync gives the device this long beyond its own wait limit to report.
+constexpr uint64_t kHostGraceNs = 1000ull * 1000 * 1000;
 
 inline uint64_t now_ns() {
   return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -88,6 +106,11 @@ struct gvm_ctx {
   uint32_t launch_gen = 0;
   std::atomic<uint64_t> staged{0}, staged_peak{0}, submitted{0}, completed{0}, h2d{0}, d2h{0}, launches{0};
   bool shut = false;
+  int device = 0;
+  std::vector<cudaStream_t> owned_streams;  // created by gvm_init, destroyed by gvm_shutdown
+  ~gvm_ctx() {
+    for (cudaStream_t st : owned_streams) cudaStreamDestroy(st);
+  }
 };
 
 namespace {
@@ -108,6 +131,18 @@ int cuda_err(cudaError_t e) {
 }
 
 uint32_t ld_acq(const uint32_t* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+
+// Makes the manager's device (its primary context) current in the calling
+// thread before CUDA or driver calls: rank threads may never have touched
+// CUDA themselves.
+thread_local bool tl_bound = false;
+inline void bind_device(const gvm_ctx* ctx) {
+  int d = -1;
+  if (!tl_bound || cudaGetDevice(&d) != cudaSuccess || d != ctx->device) {
+    cudaSetDevice(ctx->device);
+    tl_bound = true;
+  }
+}
 
 // Launch the scheduler once (caller holds launch_mu).
 int launch_locked(gvm_ctx* ctx, uint32_t drain) {
@@ -241,7 +276,6 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   gvm_config cfg = *cfg_in;
   if (!cfg.arena || (reinterpret_cast<uintptr_t>(cfg.arena) & 255)) return GVM_EINVAL;
   if (!cfg.ctrl || (reinterpret_cast<uintptr_t>(cfg.ctrl) & 255)) return GVM_EINVAL;
-  if (!cfg.sched_stream || !cfg.copy_streams) return GVM_EINVAL;
   const CtrlLayout L = ctrl_layout((uint32_t)cfg.max_ranks, (uint32_t)cfg.ring_depth);
   if (cfg.ctrl_bytes < L.total) return GVM_EINVAL;
   const uint64_t slice = (cfg.arena_bytes / (uint64_t)cfg.max_ranks) & ~uint64_t(255);
@@ -250,8 +284,9 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   if (cfg.wait_timeout_ns == 0) cfg.wait_timeout_ns = 10ull * 1000 * 1000 * 1000;
   if (cfg.idle_poll_ns == 0) cfg.idle_poll_ns = 1000;
   if (cfg.ingest_quantum <= 0) cfg.ingest_quantum = 4;
-  for (int i = 0; i < 2 * cfg.max_ranks; ++i)
-    if (!cfg.copy_streams[i]) return GVM_EINVAL;
+  if (cfg.copy_streams)
+    for (int i = 0; i < 2 * cfg.max_ranks; ++i)
+      if (!cfg.copy_streams[i]) return GVM_EINVAL;
   if (!driver_api()) return GVM_ENODEV;
 
   int dev = 0, sms = 0;
@@ -265,7 +300,14 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   ctx->L = L;
   ctx->path = cfg.sgemm_path == GVM_SGEMM_SPLIT3 ? kPathSplit3 : kPathFma;
   ctx->slice_bytes = slice;
-  ctx->sched = static_cast<cudaStream_t>(cfg.sched_stream);
+  ctx->device = dev;
+  if (cfg.sched_stream) {
+    ctx->sched = static_cast<cudaStream_t>(cfg.sched_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->sched, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_err(e);
+    ctx->owned_streams.push_back(ctx->sched);
+  }
   int bps = 0;
   e = scheduler_setup(ctx->path, &bps, &ctx->smem);
   if (e != cudaSuccess) return cuda_err(e);
@@ -332,8 +374,19 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
     rk->ring_base = rk->slice + resident;
     rk->ring_bytes = slice - resident;
     rk->slots.resize(D);
-    rk->in_stream = static_cast<cudaStream_t>(cfg.copy_streams[2 * r]);
-    rk->out_stream = static_cast<cudaStream_t>(cfg.copy_streams[2 * r + 1]);
+    if (cfg.copy_streams) {
+      rk->in_stream = static_cast<cudaStream_t>(cfg.copy_streams[2 * r]);
+      rk->out_stream = static_cast<cudaStream_t>(cfg.copy_streams[2 * r + 1]);
+    } else {
+      e = cudaStreamCreateWithFlags(&rk->in_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) ctx->owned_streams.push_back(rk->in_stream);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&rk->out_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) ctx->owned_streams.push_back(rk->out_stream);
+      if (e != cudaSuccess) {
+        cudaFreeHost(hb);
+        return GVM_EDEVICE;
+      }
+    }
     ctx->ranks[r] = std::move(rk);
   }
 
@@ -348,6 +401,14 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   }
   *out = ctx.release();
   return GVM_OK;
+}
+
+void* gvm_stream(gvm_ctx* ctx, int32_t which) {
+  if (!ctx) return nullptr;
+  if (which == -1) return ctx->sched;
+  if (which < 0 || which >= 2 * ctx->cfg.max_ranks) return nullptr;
+  gvm_rank* r = ctx->ranks[which / 2].get();
+  return (which & 1) ? r->out_stream : r->in_stream;
 }
 
 int gvm_attach(gvm_ctx* ctx, int32_t rank, gvm_rank** out) {
@@ -367,6 +428,7 @@ int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
   gvm_ctx* ctx = r->ctx;
   std::lock_guard<std::mutex> g(r->mu);
   if (!r->attached || ctx->shut) return GVM_ESTATE;
+  bind_device(ctx);
   const bool resident = (t->flags & GVM_TASK_RESIDENT) != 0;
   if (t->flags & ~GVM_TASK_RESIDENT) return GVM_EINVAL;
   const bool split3 = ctx->path == kPathSplit3;
@@ -542,6 +604,7 @@ int gvm_poll(gvm_rank* r, uint64_t seq) {
   if (!r) return GVM_EINVAL;
   std::lock_guard<std::mutex> g(r->mu);
   if (seq >= r->next_seq) return GVM_EINVAL;
+  bind_device(r->ctx);
   if (push_flushed(r) != GVM_OK) return GVM_EDEVICE;
   reap(r);
   if (r->synced > seq) return 1;
@@ -561,6 +624,7 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
   // until the next one.
   if (ctx->cfg.mode == GVM_MODE_BARRIER && seq >= r->flushed.load(std::memory_order_acquire))
     return GVM_ESTATE;
+  bind_device(ctx);
   if (push_flushed(r) != GVM_OK) return GVM_EDEVICE;
   uint64_t last = r->synced;
   uint64_t t_prog = now_ns();
@@ -573,7 +637,7 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
     if (r->synced != last) {
       last = r->synced;
       t_prog = now;
-    } else if (now - t_prog > ctx->cfg.wait_timeout_ns) {
+    } else if (now - t_prog > ctx->cfg.wait_timeout_ns + kHostGraceNs) {
       return GVM_ETIMEDOUT;
     }
     if ((++spins & 63) == 0) {
@@ -590,11 +654,13 @@ int gvm_flush(gvm_ctx* ctx) {
   if (!ctx) return GVM_EINVAL;
   if (ctx->shut) return GVM_ESTATE;
   if (ctx->cfg.mode == GVM_MODE_CONTINUOUS) return GVM_OK;  // the scheduler is resident
+  bind_device(ctx);
   std::lock_guard<std::mutex> g(ctx->launch_mu);
   // Every task published before this point is drained by the launch below.
   std::vector<uint64_t> upto(ctx->ranks.size());
   for (size_t i = 0; i < ctx->ranks.size(); ++i) upto[i] = ctx->ranks[i]->published.load(std::memory_order_acquire);
   const int rc = launch_locked(ctx, 1);
+  GVM_TRACE("flush: launch %u rc=%d", ctx->launch_gen, rc);
   if (rc != GVM_OK) return rc;
   for (size_t i = 0; i < ctx->ranks.size(); ++i) {
     uint64_t f = ctx->ranks[i]->flushed.load();
@@ -606,6 +672,7 @@ int gvm_flush(gvm_ctx* ctx) {
 
 int gvm_wait_idle(gvm_ctx* ctx) {
   if (!ctx) return GVM_EINVAL;
+  bind_device(ctx);
   cudaError_t e = cudaStreamSynchronize(ctx->sched);
   if (e != cudaSuccess) return GVM_EDEVICE;
   for (auto& rk : ctx->ranks) {
@@ -620,6 +687,7 @@ static int rank_copy(gvm_rank* r, uint64_t off, void* host, uint64_t bytes, bool
   const uint64_t res = r->ring_base - r->slice;
   if (off > res || bytes > res - off) return GVM_EINVAL;
   if (!bytes) return GVM_OK;
+  bind_device(r->ctx);
   void* dev = reinterpret_cast<void*>(r->slice + off);
   cudaError_t e = to_dev ? cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, r->in_stream)
                          : cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, r->in_stream);
@@ -652,6 +720,7 @@ int gvm_detach(gvm_rank* r) {
 
 int gvm_shutdown(gvm_ctx* ctx) {
   if (!ctx) return GVM_EINVAL;
+  bind_device(ctx);
   int rc = GVM_OK;
   {
     std::lock_guard<std::mutex> g(ctx->launch_mu);
@@ -666,21 +735,42 @@ int gvm_shutdown(gvm_ctx* ctx) {
       for (auto& rk : ctx->ranks) rk->flushed.store(rk->published.load());
     }
   }
+  GVM_TRACE("shutdown: stop (launches=%llu)", (unsigned long long)ctx->launches.load());
   // Continuous mode: the resident scheduler drains what is pending, then exits.
   __atomic_store_n(&ctx->shared->stop, 1u, __ATOMIC_RELEASE);
   for (auto& rk : ctx->ranks) {
     std::lock_guard<std::mutex> g(rk->mu);
     if (rc == GVM_OK && push_out_ops(rk.get(), rk->next_seq) != GVM_OK) rc = GVM_EDEVICE;
   }
+  GVM_TRACE("shutdown: output ops pushed, syncing scheduler stream");
   if (cudaStreamSynchronize(ctx->sched) != cudaSuccess) rc = GVM_EDEVICE;
   const bool device_ok = ld_acq(&ctx->shared->status) == 0;
+  GVM_TRACE("shutdown: scheduler idle, device_ok=%d", (int)device_ok);
+  const DriverApi* api = driver_api();
+  const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
   for (auto& rk : ctx->ranks) {
     if (cudaStreamSynchronize(rk->in_stream) != cudaSuccess) rc = GVM_EDEVICE;
-    // After a device error an output stream may wait on a done word that is
-    // never written; it is left as it is rather than waited on.
-    if (device_ok && cudaStreamSynchronize(rk->out_stream) != cudaSuccess) rc = GVM_EDEVICE;
+    if (!device_ok) {
+      // The scheduler stopped on an error: release every output-stream wait
+      // whose done word will never be written, so that the caller's streams
+      // do not stay blocked after the manager is gone. Those tasks' outputs
+      // are not valid.
+      reap(rk.get());
+      for (uint64_t s = rk->synced; s < rk->out_pushed; ++s) {
+        const uint32_t idx = (uint32_t)rk->id * D + (uint32_t)(s & (D - 1));
+        if (api->write_value32(reinterpret_cast<CUstream>(rk->in_stream),
+                               reinterpret_cast<CUdeviceptr>(ctx->params.done + idx), tag_of(s),
+                               CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
+          rc = GVM_EDEVICE;
+      }
+      if (cudaStreamSynchronize(rk->in_stream) != cudaSuccess) rc = GVM_EDEVICE;
+    }
+    if (cudaStreamSynchronize(rk->out_stream) != cudaSuccess) rc = GVM_EDEVICE;
+    GVM_TRACE("shutdown: rank %d streams idle (synced=%llu next=%llu)", rk->id, (unsigned long long)rk->synced,
+              (unsigned long long)rk->next_seq);
   }
   if (!device_ok) rc = GVM_EDEVICE;
+  GVM_TRACE("shutdown: freeing host rings");
   cudaFreeHost(ctx->host_block);
   delete ctx;
   return rc;

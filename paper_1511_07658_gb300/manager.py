@@ -224,18 +224,17 @@ class Manager:
         with torch.cuda.device(self.device):
             self.arena = torch.empty(slice_bytes * ranks + 256, dtype=torch.uint8, device=self.device)
             self.ctrl = torch.empty(ctrl_bytes + 256, dtype=torch.uint8, device=self.device)
-            self.sched_stream = torch.cuda.Stream(self.device)
-            self.copy_streams = [torch.cuda.Stream(self.device) for _ in range(2 * ranks)]
         arena_ptr = (self.arena.data_ptr() + 255) // 256 * 256
         ctrl_ptr = (self.ctrl.data_ptr() + 255) // 256 * 256
-        self._streams_arr = (c_void_p * (2 * ranks))(*[s.cuda_stream for s in self.copy_streams])
         cfg.arena = arena_ptr
         cfg.arena_bytes = slice_bytes * ranks
         cfg.resident_bytes = resident_bytes
         cfg.ctrl = ctrl_ptr
         cfg.ctrl_bytes = ctrl_bytes
-        cfg.sched_stream = self.sched_stream.cuda_stream
-        cfg.copy_streams = ctypes.cast(self._streams_arr, ctypes.POINTER(c_void_p))
+        # Streams: the manager creates dedicated non-blocking ones (PyTorch's
+        # stream pool recycles a fixed set, so two pool streams can alias).
+        cfg.sched_stream = None
+        cfg.copy_streams = None
         cfg.admission_cap_bytes = admission_cap_bytes
         cfg.wait_timeout_ns = int(wait_timeout_s * 1e9)
         cfg.idle_poll_ns = idle_poll_ns
@@ -247,6 +246,12 @@ class Manager:
             check(L.gvm_init(byref(cfg), byref(h)), "gvm_init")
         self.handle = h
         self._ranks: dict[int, Rank] = {}
+        # PyTorch views of the manager's streams, for events and for queueing
+        # work on them; valid until shutdown.
+        self.sched_stream = torch.cuda.ExternalStream(L.gvm_stream(h, -1), device=self.device)
+        self.copy_streams = [
+            torch.cuda.ExternalStream(L.gvm_stream(h, i), device=self.device) for i in range(2 * ranks)
+        ]
 
     def attach(self, rank: int) -> Rank:
         h = c_void_p()
