@@ -68,20 +68,25 @@ def parse():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--plain", action="store_true", help="also time the plain one-context-per-rank form")
+    p.add_argument("--model", action="store_true", help="also check timings against Eqs. 1, 2 and 7")
     p.add_argument("--quantum", type=int, default=8)
+    p.add_argument("--ranks", type=int, default=0, help="smaller case for profiling (not a bench line)")
+    p.add_argument("--per-rank", type=int, default=0, help="smaller case for profiling (not a bench line)")
     return p.parse_args()
 
 
 # --------------------------------------------------------------- workloads
 
 
-def workload(name):
+def workload(name, ranks=0, per_rank=0):
     if name == "sgemm512":
-        w = synth.sgemm_square(ranks=16, per_rank=64, side=512)
-        desc = "SGEMM M=N=K=512, 16 ranks x 64 tasks, standard-normal operands"
+        R, P = ranks or 16, per_rank or 64
+        w = synth.sgemm_square(ranks=R, per_rank=P, side=512)
+        desc = f"SGEMM M=N=K=512, {R} ranks x {P} tasks, standard-normal operands"
     else:
-        w = synth.vadd_tiny(ranks=4, per_rank=8, n=65536)
-        desc = "vector add n=65536, 4 ranks x 8 tasks, uniform [-1,1) operands"
+        R, P = ranks or 4, per_rank or 8
+        w = synth.vadd_tiny(ranks=R, per_rank=P, n=65536)
+        desc = f"vector add n=65536, {R} ranks x {P} tasks, uniform [-1,1) operands"
     return w, desc
 
 
@@ -592,6 +597,93 @@ def plain_per_rank(w):
     }
 
 
+# --------------------------------------------------------------- model check
+
+
+def model_check(args, w):
+    """Measured shared time against the execution model (Section 4.2.3).
+
+    T_in, T_out: one task's input / output copy alone (pinned host memory,
+    CUDA events). T_comp: the task kernel alone. Shared: N ranks, one task
+    each, through the manager (host buffers), N = 1, 2, 4, 8, 16, as the
+    paper's validation varies the process count (Section 6). Predictions:
+    Eq. 2 or Eq. 7 by the task's class, and the duplex, wave-aware variant.
+    """
+    import torch
+
+    import paper_1511_07658_gb300 as g
+    from oracle import model
+
+    spec = w.tasks[0]
+    reps = 20
+    if spec.kind == synth.TASK_SGEMM:
+        m, n, k = spec.m, spec.n, spec.k
+        hin = [torch.randn(m, k).pin_memory(), torch.randn(k, n).pin_memory()]
+        hout = torch.empty(m, n).pin_memory()
+    else:
+        hin = [torch.randn(spec.n).pin_memory(), torch.randn(spec.n).pin_memory()]
+        hout = torch.empty(spec.n).pin_memory()
+    din = [x.cuda() for x in hin]
+    dout = torch.empty_like(hout, device="cuda")
+    s = torch.cuda.Stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    t_in = timed(lambda: [d.copy_(h, non_blocking=True) for d, h in zip(din, hin)])
+    t_out = timed(lambda: hout.copy_(dout, non_blocking=True))
+    if spec.kind == synth.TASK_SGEMM:
+        scratch = torch.empty(g.sgemm_scratch_bytes(m, n, k, args.path) + 256, dtype=torch.uint8, device="cuda")
+        t_comp = timed(lambda: g.sgemm_f32(din[0], din[1], dout, path=args.path, scratch=scratch, stream=s))
+    else:
+        t_comp = timed(lambda: g.vadd_f32(din[0], din[1], dout, stream=s))
+    cls = model.classify(t_in, t_comp, t_out)
+    rows = []
+    for N in (1, 2, 4, 8, 16):
+        mgr = g.Manager(N, ring_depth=4, sgemm_path=args.path, slice_bytes=64 << 20)
+        ranks = [mgr.attach(r) for r in range(N)]
+        outs = [torch.empty_like(hout).pin_memory() for _ in range(N)]
+
+        def step():
+            seqs = []
+            for r in range(N):
+                if spec.kind == synth.TASK_SGEMM:
+                    seqs.append(ranks[r].submit_sgemm(hin[0], hin[1], outs[r]))
+                else:
+                    seqs.append(ranks[r].submit_vadd(hin[0], hin[1], outs[r]))
+            mgr.flush()
+            for r in range(N):
+                ranks[r].sync(seqs[r])
+
+        for _ in range(3):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            step()
+        shared = (time.perf_counter() - t0) / reps
+        mgr.shutdown()
+        pred = model.shared_time(N, t_in, t_comp, t_out)
+        rows.append({
+            "N": N,
+            "measured_s": shared,
+            "eq2_or_eq7_s": pred,
+            "deviation": model.deviation(shared, pred),
+            "duplex_s": model.shared_time_duplex(N, t_in, t_comp, t_out, 1),
+            "eq1_no_init_s": model.t_total_no_vt(N, 0.0, t_in, t_comp, t_out, 0.0),
+        })
+    return {"t_in_s": t_in, "t_comp_s": t_comp, "t_out_s": t_out, "class": cls, "rows": rows,
+            "mean_deviation": statistics.mean(r["deviation"] for r in rows)}
+
+
 # --------------------------------------------------------------- main
 
 
@@ -599,7 +691,7 @@ def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    w, desc = workload(args.workload)
+    w, desc = workload(args.workload, args.ranks, args.per_rank)
     if args.impl == "reference":
         if rank != 0:
             return
@@ -617,6 +709,8 @@ def main():
             out["cpu_baseline"] = cpu_baseline(w)
         if args.plain and w.tasks[0].kind == synth.TASK_SGEMM:
             out["plain_per_rank"] = plain_per_rank(w)
+        if args.model:
+            out["model_check"] = model_check(args, w)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -167,7 +167,7 @@ inline CtrlLayout ctrl_layout(uint32_t ranks, uint32_t depth) {
   CtrlLayout L;
   uint64_t slots = (uint64_t)ranks * depth;
   uint32_t q = 1;
-  while (q < 4 * slots) q <<= 1;
+  while (q < 4 * slots || q < 256) q <<= 1;
   L.qcap = q;
   uint64_t off = sizeof(DevCtrl);
   L.off_tail = off;   off = align_up(off + 4ull * ranks, 256);

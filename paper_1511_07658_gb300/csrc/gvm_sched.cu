@@ -115,7 +115,9 @@ __device__ IngestOut ingest(const SchedParams& p) {
     const uint32_t used = (uint32_t)(pub - cur);
     const uint32_t space = used < p.qcap ? p.qcap - used : 0u;
     uint32_t quantum = min(p.quantum, kMaxQuantum);
-    if (2u * 32u * quantum > space) quantum = space / 64u;
+    // Each task takes at most two queue entries; keep this pass within the free space.
+    const uint32_t lanes = min(32u, p.ranks - g);
+    if (2u * lanes * quantum > space) quantum = space / (2u * lanes);
 
     uint32_t r = 0, t = 0, take = 0, avail = 0;
     const bool valid = (g + lane) < p.ranks;
