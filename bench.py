@@ -346,6 +346,16 @@ def gpu_arm(args, w, desc, rank, world):
         total_s = float(t.item())
     value = tasks_per_step * args.steps * world / total_s
     stats_after_value = mgr.stats()
+    st = stats_after_value
+    ph = st["launch_phase"]
+    timeline = {
+        "start_to_last_done_us": (st["launch_last_done_ns"] - st["launch_start_ns"]) / 1e3,
+        "last_done_to_exit_us": (st["launch_exit_ns"] - st["launch_last_done_ns"]) / 1e3,
+        "cta_ms": {"acquire": ph[0] / 1e6, "ingest": ph[1] / 1e6, "split": ph[2] / 1e6, "gemm": ph[3] / 1e6,
+                   "gemm_split_wait": ph[4] / 1e6, "vadd": ph[5] / 1e6},
+        "tiles": ph[6],
+        "ingest_passes": ph[7],
+    }
 
     # ---- end to end (host buffers, copies inside the timed region)
     e2e = None
@@ -447,6 +457,7 @@ def gpu_arm(args, w, desc, rank, world):
         "latency_us": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "kind": "device ingest->done, last step"},
         "wall_tasks_per_s": tasks_per_step * args.steps / wall,
         "roofline": roof,
+        "sched_timeline_last_launch": timeline,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,

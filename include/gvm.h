@@ -140,6 +140,15 @@ typedef struct gvm_stats {
   uint64_t d2h_bytes;      /* bytes copied device to host by the manager */
   uint32_t device_status;  /* last error status word written by the scheduler (0 = ok) */
   uint32_t device_where;   /* which wait or check set device_status */
+  uint64_t launch_start_ns;     /* last scheduler launch that exited: first CTA start, */
+  uint64_t launch_last_done_ns; /* its last task completion and its last CTA exit */
+  uint64_t launch_exit_ns;      /* (device %globaltimer, ns; 0 before any exit) */
+  uint64_t launch_phase[8];     /* that launch's CTA time per phase, summed over CTAs (ns):
+                                   [0] finding work (claims, ingest, idle polling),
+                                   [1] ingest passes that published work, [2] split3
+                                   pre-pass tiles, [3] GEMM tiles, [4] GEMM tiles waiting
+                                   for their split pass, [5] vector-add tiles; then counts:
+                                   [6] tiles run, [7] ingest passes that published work */
 } gvm_stats;
 
 typedef struct gvm_ctx gvm_ctx;

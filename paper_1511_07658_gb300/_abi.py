@@ -77,6 +77,10 @@ class GvmStats(ctypes.Structure):
         ("d2h_bytes", c_uint64),
         ("device_status", c_uint32),
         ("device_where", c_uint32),
+        ("launch_start_ns", c_uint64),
+        ("launch_last_done_ns", c_uint64),
+        ("launch_exit_ns", c_uint64),
+        ("launch_phase", c_uint64 * 8),
     ]
 
 

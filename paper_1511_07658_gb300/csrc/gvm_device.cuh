@@ -380,52 +380,85 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Rows [r0, r0 + kSplitRows) of A (m x k, row-major) into the hi plane
+// Rows [r0, r0 + rows) of A (m x k, row-major) into the hi plane
 // (planes + row * kp) and the lo plane (+ m * kp). Columns k .. kp-1 get 0.
+// Each thread keeps kSplitUnroll groups of 8 elements in flight, so that a
+// CTA has ~32 KB of loads outstanding (the pass is bound by memory latency
+// otherwise).
+constexpr int kSplitUnroll = 4;
+
 __device__ __forceinline__ void split_a_tile(const float* __restrict__ A, __nv_bfloat16* __restrict__ planes,
-                                             int m, int k, int kp, int r0) {
+                                             int m, int k, int kp, int r0, int rows) {
   const int groups = kp >> 3;
-  const int rows = min(kSplitRows, m - r0);
+  rows = min(rows, m - r0);
   const bool vec = ((k & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
   const int64_t total = (int64_t)rows * groups;
-  for (int64_t g = threadIdx.x; g < total; g += kThreads) {
-    const int r = r0 + (int)(g / groups);
-    const int kk = (int)(g % groups) * 8;
-    const float* src = A + (int64_t)r * k + kk;
-    float v[8];
-    if (vec && kk + 8 <= k) {
-      const float4 x0 = __ldcs(reinterpret_cast<const float4*>(src));
-      const float4 x1 = __ldcs(reinterpret_cast<const float4*>(src + 4));
-      v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
-      v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
-    } else {
+  for (int64_t gb = 0; gb < total; gb += (int64_t)kThreads * kSplitUnroll) {
+    float v[kSplitUnroll][8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = (kk + i < k) ? src[i] : 0.f;
+    for (int u = 0; u < kSplitUnroll; ++u) {
+      const int64_t g = gb + threadIdx.x + (int64_t)u * kThreads;
+      if (g >= total) continue;
+      const int r = r0 + (int)(g / groups);
+      const int kk = (int)(g % groups) * 8;
+      const float* src = A + (int64_t)r * k + kk;
+      if (vec && kk + 8 <= k) {
+        const float4 x0 = __ldcs(reinterpret_cast<const float4*>(src));
+        const float4 x1 = __ldcs(reinterpret_cast<const float4*>(src + 4));
+        v[u][0] = x0.x; v[u][1] = x0.y; v[u][2] = x0.z; v[u][3] = x0.w;
+        v[u][4] = x1.x; v[u][5] = x1.y; v[u][6] = x1.z; v[u][7] = x1.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[u][i] = (kk + i < k) ? src[i] : 0.f;
+      }
     }
-    uint4 hi, lo;
-    split8(v, hi, lo);
-    st_cg_v4(planes + (int64_t)r * kp + kk, hi);
-    st_cg_v4(planes + (int64_t)m * kp + (int64_t)r * kp + kk, lo);
+#pragma unroll
+    for (int u = 0; u < kSplitUnroll; ++u) {
+      const int64_t g = gb + threadIdx.x + (int64_t)u * kThreads;
+      if (g >= total) continue;
+      const int r = r0 + (int)(g / groups);
+      const int kk = (int)(g % groups) * 8;
+      uint4 hi, lo;
+      split8(v[u], hi, lo);
+      st_cg_v4(planes + (int64_t)r * kp + kk, hi);
+      st_cg_v4(planes + (int64_t)m * kp + (int64_t)r * kp + kk, lo);
+    }
   }
 }
 
-// Columns [c0, c0 + kSplitRows) of B (k x n, row-major) into rows of the
-// transposed planes: hi at planes + col * kp, lo at + n * kp.
+// Columns [c0, c0 + cols) of B (k x n, row-major) into rows of the
+// transposed planes: hi at planes + col * kp, lo at + n * kp. Threads are
+// laid out (column, k-group) so that every load instruction of a warp reads
+// 32 consecutive floats of one row of B; each thread keeps kSplitUnroll
+// groups of 8 loads in flight.
 __device__ __forceinline__ void split_b_tile(const float* __restrict__ B, __nv_bfloat16* __restrict__ planes,
-                                             int64_t n, int k, int kp, int64_t c0) {
-  const int cols = (int)min((int64_t)kSplitRows, n - c0);
-  const int lane_c = threadIdx.x % kSplitRows;      // column within the tile
-  const int grp = threadIdx.x / kSplitRows;         // 0 or 1
+                                             int64_t n, int k, int kp, int64_t c0, int cols) {
+  cols = (int)min((int64_t)cols, n - c0);
+  const int width = cols <= 32 ? 32 : (cols <= 64 ? 64 : 128);  // threads per k-group
+  const int lane_c = threadIdx.x % width;
+  const int grp = threadIdx.x / width;
+  const int ngrp = kThreads / width;
   if (lane_c >= cols) return;
   const int64_t col = c0 + lane_c;
-  for (int kk = grp * 8; kk < kp; kk += 16) {
-    float v[8];
+  const int step = 8 * ngrp;
+  for (int kb = grp * 8; kb < kp; kb += step * kSplitUnroll) {
+    float v[kSplitUnroll][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = (kk + i < k) ? __ldcs(B + (int64_t)(kk + i) * n + col) : 0.f;
-    uint4 hi, lo;
-    split8(v, hi, lo);
-    st_cg_v4(planes + col * kp + kk, hi);
-    st_cg_v4(planes + n * kp + col * kp + kk, lo);
+    for (int u = 0; u < kSplitUnroll; ++u) {
+      const int kk = kb + u * step;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        v[u][i] = (kk + i < k) ? __ldcs(B + (int64_t)(kk + i) * n + col) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kSplitUnroll; ++u) {
+      const int kk = kb + u * step;
+      if (kk >= kp) continue;
+      uint4 hi, lo;
+      split8(v[u], hi, lo);
+      st_cg_v4(planes + col * kp + kk, hi);
+      st_cg_v4(planes + n * kp + col * kp + kk, lo);
+    }
   }
 }
 
@@ -483,14 +516,16 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* tmA, const CUtensorMa
                                         int m, int64_t n, int k, int tm, int tn, uint8_t* stages, TcShared* ts,
                                         uint32_t& it, uint32_t& tile_no, uint64_t timeout_ns,
                                         const uint32_t* split_done, uint32_t nsplit,
-                                        volatile uint32_t* cta_abort, uint32_t* fail_where, bool tmap_global) {
+                                        volatile uint32_t* cta_abort, uint32_t* fail_where, bool tmap_global,
+                                        uint64_t* wait_acc = nullptr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkb = (k + kTcBK - 1) / kTcBK;
   if (warp == 0) {
     if (lane == 0) {
       bool ok = true;
       if (split_done != nullptr) {
-        const uint64_t deadline = globaltimer() + timeout_ns;
+        const uint64_t t0 = globaltimer();
+        const uint64_t deadline = t0 + timeout_ns;
         while (ld_acquire_gpu(split_done) < nsplit) {
           if (*cta_abort || globaltimer() > deadline) {
             ok = false;
@@ -499,6 +534,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* tmA, const CUtensorMa
           }
           __nanosleep(256);
         }
+        if (wait_acc) *wait_acc += globaltimer() - t0;
       }
       fence_proxy_async_global();
       if (tmap_global) {

@@ -110,6 +110,23 @@ struct alignas(64) HostShared {
   uint32_t where;
   uint32_t info;
   uint32_t pad2[13];
+  // device: timeline of the last scheduler launch that exited (globaltimer, ns)
+  uint64_t k_start;      // first CTA started
+  uint64_t k_last_done;  // last task completion
+  uint64_t k_exit;       // last CTA left
+  uint64_t k_prof[8];    // per-phase CTA time summed over CTAs (kProf* order)
+};
+
+// Per-launch phase counters (nanoseconds of CTA time summed over CTAs, and counts).
+enum : int {
+  kProfAcquire = 0,    // warp 0 finding the next tile (claims, ingest, idle polling)
+  kProfIngest = 1,     // inside ingest passes that published work
+  kProfSplit = 2,      // split3 pre-pass tiles
+  kProfGemm = 3,       // GEMM tiles (FMA or tensor core), waits included
+  kProfSplitWait = 4,  // GEMM producer waiting for its task's split pass
+  kProfVadd = 5,       // vector-add tiles
+  kProfTiles = 6,      // tiles run
+  kProfIngests = 7,    // ingest passes that published work
 };
 
 // Device control block (front of the caller's ctrl buffer).
@@ -123,7 +140,10 @@ struct alignas(256) DevCtrl {
   uint32_t drained;       // drain mode: every published descriptor has been taken
   uint32_t pad0;
   uint64_t quiet_until;   // globaltimer before which look-ahead ingest is skipped
-  uint32_t pad[52];
+  uint64_t t_start;       // this launch: first CTA start (0 = unset)
+  uint64_t t_last_done;   // this launch: last task completion
+  uint64_t prof[8];       // this launch: summed CTA time per phase (see kProf*)
+  uint32_t pad[32];
 };
 static_assert(sizeof(DevCtrl) == 256, "DevCtrl layout");
 

@@ -28,14 +28,18 @@ __global__ void __launch_bounds__(kThreads, 2) fma_sgemm_kernel(const float* A, 
   fma_tile(A, B, C, m, n, k, blockIdx.y, blockIdx.x, reinterpret_cast<FmaSmem*>(dyn_smem));
 }
 
+// Standalone split pass: finer tiles than the scheduler's so that one task
+// alone spreads over more SMs.
+constexpr int kSplitRowsAlone = 32;
+
 __global__ void __launch_bounds__(kThreads) split_kernel(const float* A, const float* B, __nv_bfloat16* pa,
                                                          __nv_bfloat16* pb, int m, int n, int k, int kp) {
-  const int tiles_a = (m + kSplitRows - 1) / kSplitRows;
+  const int tiles_a = (m + kSplitRowsAlone - 1) / kSplitRowsAlone;
   const int t = blockIdx.x;
   if (t < tiles_a) {
-    split_a_tile(A, pa, m, k, kp, t * kSplitRows);
+    split_a_tile(A, pa, m, k, kp, t * kSplitRowsAlone, kSplitRowsAlone);
   } else {
-    split_b_tile(B, pb, n, k, kp, (int64_t)(t - tiles_a) * kSplitRows);
+    split_b_tile(B, pb, n, k, kp, (int64_t)(t - tiles_a) * kSplitRowsAlone, kSplitRowsAlone);
   }
 }
 
@@ -179,7 +183,7 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
   const int kp = (int)split_kp(k);
   uint8_t* pa = static_cast<uint8_t*>(scratch);
   uint8_t* pb = pa + split_a_bytes(m, k);
-  const int nsplit = (m + kSplitRows - 1) / kSplitRows + (n + kSplitRows - 1) / kSplitRows;
+  const int nsplit = (m + kSplitRowsAlone - 1) / kSplitRowsAlone + (n + kSplitRowsAlone - 1) / kSplitRowsAlone;
   split_kernel<<<nsplit, kThreads, 0, s>>>(A, B, reinterpret_cast<__nv_bfloat16*>(pa),
                                            reinterpret_cast<__nv_bfloat16*>(pb), m, n, k, kp);
   if (cudaGetLastError() != cudaSuccess) return GVM_EDEVICE;

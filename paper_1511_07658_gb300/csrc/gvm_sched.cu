@@ -40,6 +40,7 @@ struct alignas(128) SchedShared {
   uint32_t abort;
   uint32_t fail_where;
   uint32_t pad[2];
+  uint64_t prof[8];  // this CTA's phase counters (kProf*), written by thread 0 only
   TcShared tc;
 };
 
@@ -64,8 +65,10 @@ __device__ void report_error(const SchedParams& p, uint32_t status, uint32_t whe
 __device__ void complete_task(const SchedParams& p, uint32_t idx, uint32_t tag, uint32_t flags,
                               uint64_t t_ingest) {
   HostComplete* hc = &p.host_complete[idx];
+  const uint64_t now = globaltimer();
   st_relaxed_sys64(&hc->t_ingest, t_ingest);
-  st_relaxed_sys64(&hc->t_done, globaltimer());
+  st_relaxed_sys64(&hc->t_done, now);
+  atomicMax(reinterpret_cast<unsigned long long*>(&p.ctrl->t_last_done), (unsigned long long)now);
   __threadfence_system();
   if (flags & kFlagNeedsD2H) {
     st_release_sys(&p.done[idx], tag);
@@ -92,7 +95,7 @@ struct IngestOut {
 
 // Warp 0 of one CTA: move ready descriptors from the host rings into the
 // device table and the publication queue. All lanes call.
-__device__ IngestOut ingest(const SchedParams& p) {
+__device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
   const int lane = threadIdx.x & 31;
   IngestOut out{0, 0, 0};
   uint32_t got = 0;
@@ -225,6 +228,10 @@ __device__ IngestOut ingest(const SchedParams& p) {
   __syncwarp();
   out.published = (uint32_t)(pub - pub0);
   out.pending = pending;
+  if (lane == 0 && out.published) {
+    prof[kProfIngest] += globaltimer() - now;
+    prof[kProfIngests] += 1;
+  }
   return out;
 }
 
@@ -239,7 +246,7 @@ __device__ __forceinline__ uint64_t bcast64(uint64_t v) {
 // or 0 when the kernel should exit. Every decision is taken on values lane 0
 // read and broadcast, so the warp never diverges across the shuffles.
 __device__ int acquire(const SchedParams& p, uint32_t& task, uint32_t& phase, uint32_t& tile,
-                       uint64_t& idle_since) {
+                       uint64_t& idle_since, uint64_t* prof) {
   const int lane = threadIdx.x & 31;
   uint64_t stall_since = 0;
   while (true) {
@@ -261,7 +268,7 @@ __device__ int acquire(const SchedParams& p, uint32_t& task, uint32_t& phase, ui
     quiet = bcast64(quiet);
     if (cur < pub) {
       // Keep the queue ahead of the CTAs, unless a recent pass found the rings empty.
-      if (pub - cur <= kLookahead && now >= quiet) (void)ingest(p);
+      if (pub - cur <= kLookahead && now >= quiet) (void)ingest(p, prof);
       uint32_t x = 0, etask = 0, ephase = 0, cnt = 0;
       if (lane == 0) {
         const uint64_t raw = ld_relaxed_gpu64(reinterpret_cast<const uint64_t*>(&p.pubq[cur & (p.qcap - 1)]));
@@ -288,7 +295,7 @@ __device__ int acquire(const SchedParams& p, uint32_t& task, uint32_t& phase, ui
       continue;
     }
     if (p.drain && drained) return 0;
-    const IngestOut r = ingest(p);
+    const IngestOut r = ingest(p, prof);
     if (r.published) {
       stall_since = 0;
       idle_since = 0;
@@ -327,6 +334,10 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
   if (tid == 0) {
     sh.abort = 0;
     sh.fail_where = 0;
+    for (int i = 0; i < 8; ++i) sh.prof[i] = 0;
+    const unsigned long long t0 = globaltimer();
+    unsigned long long* ts = reinterpret_cast<unsigned long long*>(&p.ctrl->t_start);
+    if (atomicCAS(ts, 0ull, t0) != 0ull) atomicMin(ts, t0);
   }
   uint32_t it = 0, tile_no = 0;
   if constexpr (PATH == kPathSplit3) {
@@ -338,8 +349,9 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
 
   while (true) {
     if (warp == 0) {
+      const uint64_t t_acq = globaltimer();
       uint32_t task = 0, phase = 0, tile = 0;
-      const int got = acquire(p, task, phase, tile, idle_since);
+      const int got = acquire(p, task, phase, tile, idle_since, sh.prof);
       if (lane == 0) {
         sh.go = (uint32_t)got;
         sh.task = task;
@@ -350,11 +362,14 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
         const uint4 v = ld_cg_v4(reinterpret_cast<const uint4*>(&p.tasks[task].body) + lane);
         reinterpret_cast<uint4*>(&sh.body)[lane] = v;
       }
+      if (lane == 0) sh.prof[kProfAcquire] += globaltimer() - t_acq;
     }
     __syncthreads();
     if (!sh.go || sh.abort) break;
+    const uint64_t t_tile = tid == 0 ? globaltimer() : 0;
     const TaskBody& b = sh.body;
     const uint32_t task = sh.task, phase = sh.phase, tile = sh.tile;
+    int bucket = kProfVadd;
 
     if (b.type == kTaskVadd) {
       const int64_t lo = (int64_t)tile * b.vadd_tile;
@@ -366,25 +381,28 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
       const float* B = reinterpret_cast<const float*>(b.b);
       float* C = reinterpret_cast<float*>(b.c);
       if constexpr (PATH == kPathFma) {
+        bucket = kProfGemm;
         const int tm = (int)(tile / b.tiles_n), tn = (int)(tile % b.tiles_n);
         fma_tile(A, B, C, b.m, (int)b.n, b.k, tm, tn, reinterpret_cast<FmaSmem*>(big));
       } else {
         if (phase == kPhaseSplit) {
+          bucket = kProfSplit;
           const uint32_t tiles_a = (uint32_t)((b.m + kSplitRows - 1) / kSplitRows);
           if (tile < tiles_a) {
             split_a_tile(A, reinterpret_cast<__nv_bfloat16*>(b.scratch), b.m, b.k, (int)b.kp,
-                         (int)(tile * kSplitRows));
+                         (int)(tile * kSplitRows), kSplitRows);
           } else {
             split_b_tile(B, reinterpret_cast<__nv_bfloat16*>(b.scratch_b), b.n, b.k, (int)b.kp,
-                         (int64_t)(tile - tiles_a) * kSplitRows);
+                         (int64_t)(tile - tiles_a) * kSplitRows, kSplitRows);
           }
           fence_proxy_async_global();
         } else {
+          bucket = kProfGemm;
           const int tm = (int)(tile / b.tiles_n), tn = (int)(tile % b.tiles_n);
           const DevTask* dt = &p.tasks[task];
           tc_tile(&dt->body.tmA, &dt->body.tmB, C, b.m, b.n, b.k, tm, tn, big, &sh.tc, it, tile_no,
                   p.wait_timeout_ns, b.nsplit ? &dt->split_done : nullptr, b.nsplit, &sh.abort,
-                  &sh.fail_where, true);
+                  &sh.fail_where, true, &sh.prof[kProfSplitWait]);
         }
       }
     }
@@ -395,6 +413,8 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
       break;
     }
     if (tid == 0) {
+      sh.prof[bucket] += globaltimer() - t_tile;
+      sh.prof[kProfTiles] += 1;
       DevTask* dt = &p.tasks[task];
       if (phase == kPhaseSplit) atomicAdd(&dt->split_done, 1u);
       const uint32_t d = atomicAdd(&dt->tiles_done, 1u);
@@ -410,10 +430,20 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
     tc_teardown(&sh.tc);
   }
   if (tid == 0) {
+    for (int i = 0; i < 8; ++i)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), (unsigned long long)sh.prof[i]);
     __threadfence();
     const uint32_t n = atomicAdd(&p.ctrl->exit_count, 1u);
     if (n + 1 == gridDim.x) {
-      // Every CTA has left: reset the per-launch words for the next launch.
+      // Every CTA has left: publish this launch's timeline and phase
+      // counters, then reset the per-launch words for the next launch.
+      HostShared* hs = p.host_shared;
+      st_relaxed_sys64(&hs->k_start, atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->t_start), 0ull));
+      st_relaxed_sys64(&hs->k_last_done,
+                       atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->t_last_done), 0ull));
+      for (int i = 0; i < 8; ++i)
+        st_relaxed_sys64(&hs->k_prof[i], atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), 0ull));
+      st_relaxed_sys64(&hs->k_exit, globaltimer());
       atomicExch(&p.ctrl->exit_count, 0u);
       atomicExch(&p.ctrl->drained, 0u);
       atomicExch(&p.ctrl->ingest_lock, 0u);

@@ -273,7 +273,9 @@ class Manager:
     def stats(self) -> dict:
         s = GvmStats()
         check(lib().gvm_stats_get(self.handle, byref(s)), "gvm_stats_get")
-        return {name: getattr(s, name) for name, _ in GvmStats._fields_}
+        out = {name: getattr(s, name) for name, _ in GvmStats._fields_}
+        out["launch_phase"] = list(s.launch_phase)
+        return out
 
     def shutdown(self) -> None:
         if self.handle is not None:
