@@ -268,6 +268,29 @@ GVM_API uint64_t gvm_sgemm_scratch_bytes(int32_t m, int32_t n, int32_t k, int32_
 GVM_API int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m, int32_t n, int32_t k,
                   int32_t path, void* scratch, uint64_t scratch_bytes, void* stream);
 
+/* C = A B on the split3 path without any scratch from the caller. The paper
+   has no counterpart: this entry point exists for callers that cannot
+   allocate device memory -- a plain C program with no device allocator of its
+   own, a framework whose pool already owns all device memory, a
+   latency-critical loop where allocating is not allowed. It never calls
+   cudaMalloc, cudaFree or any allocating routine.
+
+   Scratch: a fixed 32 MiB array in the library's device image, held by every
+   GPU that loads the library until the process exits. That bounds the shape:
+   4 * (m + n) * kp bytes (kp = k rounded up to 8) must fit, e.g. up to
+   m = n = k = 2048; larger shapes return GVM_ENOMEM and launch nothing.
+   The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress, with that device current) and caches it; make that
+   first call before any stream capture.
+
+   Every call shares the one array, and the array keeps the previous call's
+   contents (each call rewrites every byte it reads, so nothing needs
+   clearing). Calls whose kernels overlap on the GPU -- for example on two
+   streams at once -- race on the array: order them on one stream.
+   Arguments, layout and errors are otherwise those of gvm_sgemm_f32. */
+GVM_API int gvm_sgemm_f32_noalloc(const float* A, const float* B, float* C, int32_t m, int32_t n, int32_t k,
+                                  void* stream);
+
 /* Reads and clears the error status of the standalone kernels: 0 when every
    bounded wait since the last call finished in time; otherwise the low byte
    is the status and the next byte names the wait. Synchronous. */

@@ -118,6 +118,7 @@ PROTOTYPES = {
         [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_uint64, c_void_p],
     ),
     "gvm_kernel_status": (c_int, [POINTER(c_uint32)]),
+    "gvm_sgemm_f32_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p]),
 }
 
 _lib = None
