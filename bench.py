@@ -231,8 +231,10 @@ def build_tasks(w, inputs, resident, bufs):
     return arrays
 
 
-def run_step(mgr, ranks, arrays, pool):
-    """Every rank submits its batch (one thread per rank), flush, sync all."""
+def run_step(mgr, ranks, arrays, pool, record=True):
+    """Every rank submits its batch (one thread per rank), flush, sync all.
+    With ``record``, CUDA events on the scheduler stream bracket the flush's
+    launch (barrier mode only: a resident scheduler never completes)."""
     def submit(r):
         first, cnt = ranks[r].submit_many(arrays[r])
         return first + cnt - 1
@@ -241,11 +243,13 @@ def run_step(mgr, ranks, arrays, pool):
     ev0 = ev1 = None
     import torch
 
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(mgr.sched_stream)
+    if record:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(mgr.sched_stream)
     mgr.flush()
-    ev1.record(mgr.sched_stream)
+    if record:
+        ev1.record(mgr.sched_stream)
     list(pool.map(lambda r: ranks[r].sync(lasts[r]), range(len(ranks))))
     return ev0, ev1, lasts
 
@@ -304,35 +308,51 @@ def gpu_arm(args, w, desc, rank, world):
     sampler = ClockSampler(dev)
 
     # ---- device-resident value
+    cont = args.mode == "continuous"
+
+    def device_sync():
+        # A resident (continuous-mode) scheduler never finishes before
+        # shutdown, so only barrier mode may synchronise the whole device.
+        if not cont:
+            torch.cuda.synchronize()
+
     for _ in range(args.warmup):
-        run_step(mgr, ranks, res_arrays, pool)
-    torch.cuda.synchronize()
+        run_step(mgr, ranks, res_arrays, pool, record=not cont)
+    device_sync()
     if world > 1:
         torch.distributed.barrier()
     sampler.start()
     t_step = []
     t_kernel = []
-    st0 = torch.cuda.Event(enable_timing=True)
-    st1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    st0.record(mgr.sched_stream)
-    events = []
-    for _ in range(args.steps):
-        e_step0 = torch.cuda.Event(enable_timing=True)
-        e_step0.record(mgr.sched_stream)
-        ev0, ev1, lasts = run_step(mgr, ranks, res_arrays, pool)
-        e_step1 = torch.cuda.Event(enable_timing=True)
-        e_step1.record(mgr.sched_stream)
-        events.append((e_step0, ev0, ev1, e_step1))
-    st1.record(mgr.sched_stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
+    if not cont:
+        st0 = torch.cuda.Event(enable_timing=True)
+        st1 = torch.cuda.Event(enable_timing=True)
+        st0.record(mgr.sched_stream)
+        events = []
+        for _ in range(args.steps):
+            e_step0 = torch.cuda.Event(enable_timing=True)
+            e_step0.record(mgr.sched_stream)
+            ev0, ev1, lasts = run_step(mgr, ranks, res_arrays, pool)
+            e_step1 = torch.cuda.Event(enable_timing=True)
+            e_step1.record(mgr.sched_stream)
+            events.append((e_step0, ev0, ev1, e_step1))
+        st1.record(mgr.sched_stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        for e_step0, ev0, ev1, e_step1 in events:
+            t_step.append(e_step0.elapsed_time(e_step1) / 1e3)
+            t_kernel.append(ev0.elapsed_time(ev1) / 1e3)
+        total_s = st0.elapsed_time(st1) / 1e3
+    else:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            _, _, lasts = run_step(mgr, ranks, res_arrays, pool, record=False)
+            t_step.append(time.perf_counter() - t0)
+        wall = time.perf_counter() - wall0
+        t_kernel = t_step
+        total_s = wall
     sampler.stop()
-    for e_step0, ev0, ev1, e_step1 in events:
-        t_step.append(e_step0.elapsed_time(e_step1) / 1e3)
-        t_kernel.append(ev0.elapsed_time(ev1) / 1e3)
-    total_s = st0.elapsed_time(st1) / 1e3
     # device-side service latency of the last step's tasks
     lat = []
     for r, rk in enumerate(ranks):
@@ -361,14 +381,14 @@ def gpu_arm(args, w, desc, rank, world):
     e2e = None
     if not args.skip_e2e:
         for _ in range(max(1, args.warmup)):
-            run_step(mgr, ranks, host_arrays, pool)
-        torch.cuda.synchronize()
+            run_step(mgr, ranks, host_arrays, pool, record=not cont)
+        device_sync()
         if world > 1:
             torch.distributed.barrier()
         e_steps = max(3, args.steps // 2)
         h0 = time.perf_counter()
         for _ in range(e_steps):
-            run_step(mgr, ranks, host_arrays, pool)
+            run_step(mgr, ranks, host_arrays, pool, record=not cont)
         h_s = time.perf_counter() - h0
         if world > 1:
             t = torch.tensor([h_s], device="cuda")
@@ -459,7 +479,7 @@ def gpu_arm(args, w, desc, rank, world):
         "roofline": roof,
         "sched_timeline_last_launch": timeline,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps if not cont else 1,
         "clocks": clocks,
         "parity_spot_rel_err": max(spot) if spot else None,
         "manager_stats": {k: stats_after_value[k] for k in ("launches", "staged_peak", "device_status")},

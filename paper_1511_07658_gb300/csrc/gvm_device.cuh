@@ -216,10 +216,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
 
 // ---------------------------------------------------------------- vector add
 
-// c[i] = a[i] + b[i] for lo <= i < hi, by all threads of the CTA.
+// c[i] = a[i] + b[i] for lo <= i < hi, by threads tid = 0 .. nthr-1 of the
+// CTA (the scheduler leaves warp 0 out to find the next tile meanwhile).
 __device__ __forceinline__ void vadd_range(const float* __restrict__ a, const float* __restrict__ b,
-                                           float* __restrict__ c, int64_t lo, int64_t hi) {
-  const int tid = threadIdx.x;
+                                           float* __restrict__ c, int64_t lo, int64_t hi, int tid, int nthr) {
   const bool vec = ((reinterpret_cast<uintptr_t>(a + lo) | reinterpret_cast<uintptr_t>(b + lo) |
                      reinterpret_cast<uintptr_t>(c + lo)) &
                     15) == 0;
@@ -231,12 +231,12 @@ __device__ __forceinline__ void vadd_range(const float* __restrict__ a, const fl
     float4* c4 = reinterpret_cast<float4*>(c + lo);
     constexpr int U = 4;
     int64_t i = tid;
-    for (; i + (U - 1) * kThreads < nv; i += U * kThreads) {
+    for (; i + (int64_t)(U - 1) * nthr < nv; i += (int64_t)U * nthr) {
       float4 x[U], y[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        x[u] = __ldcs(a4 + i + u * kThreads);
-        y[u] = __ldcs(b4 + i + u * kThreads);
+        x[u] = __ldcs(a4 + i + u * nthr);
+        y[u] = __ldcs(b4 + i + u * nthr);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -245,10 +245,10 @@ __device__ __forceinline__ void vadd_range(const float* __restrict__ a, const fl
         z.y = __fadd_rn(x[u].y, y[u].y);
         z.z = __fadd_rn(x[u].z, y[u].z);
         z.w = __fadd_rn(x[u].w, y[u].w);
-        __stcs(c4 + i + u * kThreads, z);
+        __stcs(c4 + i + u * nthr, z);
       }
     }
-    for (; i < nv; i += kThreads) {
+    for (; i < nv; i += nthr) {
       const float4 x = __ldcs(a4 + i), y = __ldcs(b4 + i);
       float4 z;
       z.x = __fadd_rn(x.x, y.x);
@@ -259,7 +259,7 @@ __device__ __forceinline__ void vadd_range(const float* __restrict__ a, const fl
     }
     done = lo + (nv << 2);
   }
-  for (int64_t i = done + tid; i < hi; i += kThreads) c[i] = __fadd_rn(a[i], b[i]);
+  for (int64_t i = done + tid; i < hi; i += nthr) c[i] = __fadd_rn(a[i], b[i]);
 }
 
 // ---------------------------------------------------------------- FMA SGEMM
@@ -382,22 +382,22 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo
 
 // Rows [r0, r0 + rows) of A (m x k, row-major) into the hi plane
 // (planes + row * kp) and the lo plane (+ m * kp). Columns k .. kp-1 get 0.
-// Each thread keeps kSplitUnroll groups of 8 elements in flight, so that a
-// CTA has ~32 KB of loads outstanding (the pass is bound by memory latency
-// otherwise).
+// Threads tid = 0 .. nthr-1 take groups of 8 elements; each keeps
+// kSplitUnroll groups in flight, so that a CTA has ~32 KB of loads
+// outstanding (the pass is bound by memory latency otherwise).
 constexpr int kSplitUnroll = 4;
 
 __device__ __forceinline__ void split_a_tile(const float* __restrict__ A, __nv_bfloat16* __restrict__ planes,
-                                             int m, int k, int kp, int r0, int rows) {
+                                             int m, int k, int kp, int r0, int rows, int tid, int nthr) {
   const int groups = kp >> 3;
   rows = min(rows, m - r0);
   const bool vec = ((k & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
   const int64_t total = (int64_t)rows * groups;
-  for (int64_t gb = 0; gb < total; gb += (int64_t)kThreads * kSplitUnroll) {
+  for (int64_t gb = 0; gb < total; gb += (int64_t)nthr * kSplitUnroll) {
     float v[kSplitUnroll][8];
 #pragma unroll
     for (int u = 0; u < kSplitUnroll; ++u) {
-      const int64_t g = gb + threadIdx.x + (int64_t)u * kThreads;
+      const int64_t g = gb + tid + (int64_t)u * nthr;
       if (g >= total) continue;
       const int r = r0 + (int)(g / groups);
       const int kk = (int)(g % groups) * 8;
@@ -414,7 +414,7 @@ __device__ __forceinline__ void split_a_tile(const float* __restrict__ A, __nv_b
     }
 #pragma unroll
     for (int u = 0; u < kSplitUnroll; ++u) {
-      const int64_t g = gb + threadIdx.x + (int64_t)u * kThreads;
+      const int64_t g = gb + tid + (int64_t)u * nthr;
       if (g >= total) continue;
       const int r = r0 + (int)(g / groups);
       const int kk = (int)(g % groups) * 8;
@@ -427,33 +427,37 @@ __device__ __forceinline__ void split_a_tile(const float* __restrict__ A, __nv_b
 }
 
 // Columns [c0, c0 + cols) of B (k x n, row-major) into rows of the
-// transposed planes: hi at planes + col * kp, lo at + n * kp. Threads are
-// laid out (column, k-group) so that every load instruction of a warp reads
-// 32 consecutive floats of one row of B; each thread keeps kSplitUnroll
-// groups of 8 loads in flight.
+// transposed planes: hi at planes + col * kp, lo at + n * kp. Work items are
+// (32 columns, 8 rows of B); warp w of the nthr/32 warps takes items w, w +
+// nwarps, ... so every load instruction reads 32 consecutive floats of one
+// row of B, and each lane keeps kSplitUnroll items (32 loads) in flight.
 __device__ __forceinline__ void split_b_tile(const float* __restrict__ B, __nv_bfloat16* __restrict__ planes,
-                                             int64_t n, int k, int kp, int64_t c0, int cols) {
+                                             int64_t n, int k, int kp, int64_t c0, int cols, int tid, int nthr) {
   cols = (int)min((int64_t)cols, n - c0);
-  const int width = cols <= 32 ? 32 : (cols <= 64 ? 64 : 128);  // threads per k-group
-  const int lane_c = threadIdx.x % width;
-  const int grp = threadIdx.x / width;
-  const int ngrp = kThreads / width;
-  if (lane_c >= cols) return;
-  const int64_t col = c0 + lane_c;
-  const int step = 8 * ngrp;
-  for (int kb = grp * 8; kb < kp; kb += step * kSplitUnroll) {
+  const int lane = tid & 31, w = tid >> 5, nw = nthr >> 5;
+  const int cgroups = (cols + 31) >> 5, kgroups = kp >> 3;
+  const int items = cgroups * kgroups;
+  for (int ib = w; ib < items; ib += nw * kSplitUnroll) {
     float v[kSplitUnroll][8];
 #pragma unroll
     for (int u = 0; u < kSplitUnroll; ++u) {
-      const int kk = kb + u * step;
+      const int item = ib + u * nw;
+      const int cg = item % cgroups, kg = item / cgroups;
+      const int c = cg * 32 + lane;
+      const int kk = kg * 8;
+      const bool live = item < items && c < cols;
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        v[u][i] = (kk + i < k) ? __ldcs(B + (int64_t)(kk + i) * n + col) : 0.f;
+        v[u][i] = (live && kk + i < k) ? __ldcs(B + (int64_t)(kk + i) * n + c0 + c) : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < kSplitUnroll; ++u) {
-      const int kk = kb + u * step;
-      if (kk >= kp) continue;
+      const int item = ib + u * nw;
+      const int cg = item % cgroups, kg = item / cgroups;
+      const int c = cg * 32 + lane;
+      if (item >= items || c >= cols) continue;
+      const int64_t col = c0 + c;
+      const int kk = kg * 8;
       uint4 hi, lo;
       split8(v[u], hi, lo);
       st_cg_v4(planes + col * kp + kk, hi);

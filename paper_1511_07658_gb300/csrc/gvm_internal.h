@@ -136,22 +136,30 @@ struct alignas(256) DevCtrl {
   uint32_t exit_count;
   uint32_t abort;
   uint64_t published;     // entries written to the publication queue
-  uint64_t cursor;        // first entry that may still have unclaimed tiles
+  uint64_t cursor;        // entries whose tiles have all been handed out (lower bound)
   uint32_t drained;       // drain mode: every published descriptor has been taken
   uint32_t pad0;
   uint64_t quiet_until;   // globaltimer before which look-ahead ingest is skipped
   uint64_t t_start;       // this launch: first CTA start (0 = unset)
   uint64_t t_last_done;   // this launch: last task completion
   uint64_t prof[8];       // this launch: summed CTA time per phase (see kProf*)
-  uint32_t pad[32];
+  uint64_t published_tiles;  // tiles of all published entries (one global tile space)
+  uint64_t next_tile;        // next tile index to hand out (may run ahead: a reservation)
+  uint32_t pad[28];
 };
 static_assert(sizeof(DevCtrl) == 256, "DevCtrl layout");
 
-// Publication-queue entry: task index (rank * depth + slot) and phase.
+// Publication-queue entry: one phase of one task, covering tiles
+// [base, base + cnt) of the global tile space.
 struct PubEntry {
-  uint32_t task;
-  uint32_t phase;
+  uint64_t base;   // first global tile index
+  uint64_t seq;    // entry index (checks that the ring slot was not reused)
+  uint32_t task;   // rank * depth + slot
+  uint32_t phase;  // kPhaseSplit or kPhaseMain
+  uint32_t cnt;    // tiles in this entry
+  uint32_t pad;
 };
+static_assert(sizeof(PubEntry) == 32, "PubEntry layout");
 
 // Everything the scheduler kernel needs, passed by value.
 struct SchedParams {

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(kThreads) vadd_kernel(const float* a, const fl
                                                         int64_t chunk) {
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   if (lo >= n) return;
-  vadd_range(a, b, c, lo, min(n, lo + chunk));
+  vadd_range(a, b, c, lo, min(n, lo + chunk), threadIdx.x, kThreads);
 }
 
 __global__ void __launch_bounds__(kThreads, 2) fma_sgemm_kernel(const float* A, const float* B, float* C, int m,
@@ -37,9 +37,10 @@ __global__ void __launch_bounds__(kThreads) split_kernel(const float* A, const f
   const int tiles_a = (m + kSplitRowsAlone - 1) / kSplitRowsAlone;
   const int t = blockIdx.x;
   if (t < tiles_a) {
-    split_a_tile(A, pa, m, k, kp, t * kSplitRowsAlone, kSplitRowsAlone);
+    split_a_tile(A, pa, m, k, kp, t * kSplitRowsAlone, kSplitRowsAlone, threadIdx.x, kThreads);
   } else {
-    split_b_tile(B, pb, n, k, kp, (int64_t)(t - tiles_a) * kSplitRowsAlone, kSplitRowsAlone);
+    split_b_tile(B, pb, n, k, kp, (int64_t)(t - tiles_a) * kSplitRowsAlone, kSplitRowsAlone, threadIdx.x,
+                 kThreads);
   }
 }
 

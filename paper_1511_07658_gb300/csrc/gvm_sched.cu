@@ -31,21 +31,23 @@
 
 namespace gvm {
 
+// Two tile slots: the CTA runs the tile in one while warp 0 claims the next
+// into the other. go: 1 = a tile is there, 0 = exit, 2 = nothing claimed yet.
 struct alignas(128) SchedShared {
-  TaskBody body;  // copy of the claimed task's body
-  uint32_t go;
-  uint32_t task;
-  uint32_t phase;
-  uint32_t tile;
+  TaskBody body[2];  // copies of the claimed tasks' bodies
+  uint32_t go[2];
+  uint32_t task[2];
+  uint32_t phase[2];
+  uint32_t tile[2];
   uint32_t abort;
   uint32_t fail_where;
-  uint32_t pad[2];
   uint64_t prof[8];  // this CTA's phase counters (kProf*), written by thread 0 only
+  uint64_t claim[3];  // Claim state (see acquire), owned by warp 0
   TcShared tc;
 };
 
 constexpr uint32_t kMaxQuantum = 8;
-constexpr uint64_t kLookahead = 16;  // ingest ahead when this few queue entries remain
+constexpr uint64_t kLookaheadTiles = 512;  // ingest ahead when this few published tiles remain
 constexpr uint64_t kQuietNs = 20000; // skip look-ahead ingest this long after an empty pass
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
@@ -94,7 +96,8 @@ struct IngestOut {
 };
 
 // Warp 0 of one CTA: move ready descriptors from the host rings into the
-// device table and the publication queue. All lanes call.
+// device table and append their queue entries, each covering a contiguous
+// range of the global tile space. All lanes call.
 __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
   const int lane = threadIdx.x & 31;
   IngestOut out{0, 0, 0};
@@ -107,18 +110,21 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
   }
   __threadfence();
   const uint64_t pub0 = ld_relaxed_gpu64(&p.ctrl->published);
-  const uint64_t cur = ld_relaxed_gpu64(&p.ctrl->cursor);
+  const uint64_t tiles0 = ld_relaxed_gpu64(&p.ctrl->published_tiles);
+  const uint64_t consumed = ld_relaxed_gpu64(&p.ctrl->cursor);
   const uint32_t rr = ld_relaxed_gpu(&p.ctrl->rr);
   const uint64_t now = globaltimer();
-  uint64_t pub = pub0;
+  uint64_t pub = pub0, ptiles = tiles0;
   uint32_t pending = 0;
   bool bad = false;
 
   for (uint32_t g = 0; g < p.ranks; g += 32) {
-    const uint32_t used = (uint32_t)(pub - cur);
-    const uint32_t space = used < p.qcap ? p.qcap - used : 0u;
+    // Keep at most half the ring between the hand-out frontier and the
+    // newest entry, so that an entry is read long before its slot is reused.
+    const uint64_t used = pub - consumed;
+    const uint32_t space = used < p.qcap / 2 ? (uint32_t)(p.qcap / 2 - used) : 0u;
     uint32_t quantum = min(p.quantum, kMaxQuantum);
-    // Each task takes at most two queue entries; keep this pass within the free space.
+    // Each task takes at most two queue entries.
     const uint32_t lanes = min(32u, p.ranks - g);
     if (2u * lanes * quantum > space) quantum = space / (2u * lanes);
 
@@ -138,16 +144,14 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
       }
     }
 
-    uint32_t tidx[kMaxQuantum];
-    uint32_t kinds = 0;  // bit 2i: has split entry, bit 2i+1: has main entry
-    uint32_t nsplit_e = 0, nmain_e = 0;
+    uint32_t tidx[kMaxQuantum], tsplit[kMaxQuantum], tmain[kMaxQuantum];
+    uint32_t nsplit_e = 0, nmain_e = 0, split_tiles = 0, main_tiles = 0;
     for (uint32_t i = 0; i < take; ++i) {
       const uint32_t s = t + i;
       const uint32_t idx = r * p.depth + (s & (p.depth - 1));
       tidx[i] = idx;
+      tsplit[i] = tmain[i] = 0;
       DevTask* dt = &p.tasks[idx];
-      atomicExch(&dt->claimed[0], kClaimLocked);
-      atomicExch(&dt->claimed[1], kClaimLocked);
       const uint4* src = reinterpret_cast<const uint4*>(&p.host_desc[idx]);
       uint4* dst = reinterpret_cast<uint4*>(&dt->body);
 #pragma unroll
@@ -175,51 +179,57 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
         complete_task(p, idx, tag, flags, now);
         continue;
       }
-      if (nsplit > 0) {
-        kinds |= 1u << (2 * i);
+      tsplit[i] = nsplit;
+      tmain[i] = ntiles - nsplit;
+      if (nsplit) {
         ++nsplit_e;
+        split_tiles += nsplit;
       }
       if (ntiles > nsplit) {
-        kinds |= 1u << (2 * i + 1);
         ++nmain_e;
+        main_tiles += ntiles - nsplit;
       }
     }
-    const uint32_t incl_s = warp_incl_scan(nsplit_e);
-    const uint32_t incl_m = warp_incl_scan(nmain_e);
-    const uint32_t tot_s = __shfl_sync(0xffffffffu, incl_s, 31);
-    const uint32_t tot_m = __shfl_sync(0xffffffffu, incl_m, 31);
-    uint64_t ps = pub + incl_s - nsplit_e;
-    uint64_t pm = pub + tot_s + incl_m - nmain_e;
+    // Split entries of this pass first, then main entries, each group in lane
+    // order: the split3 pre-pass of a task is handed out well ahead of its GEMM.
+    const uint32_t ie_s = warp_incl_scan(nsplit_e), ie_m = warp_incl_scan(nmain_e);
+    const uint32_t it_s = warp_incl_scan(split_tiles), it_m = warp_incl_scan(main_tiles);
+    const uint32_t te_s = __shfl_sync(0xffffffffu, ie_s, 31), te_m = __shfl_sync(0xffffffffu, ie_m, 31);
+    const uint32_t tt_s = __shfl_sync(0xffffffffu, it_s, 31), tt_m = __shfl_sync(0xffffffffu, it_m, 31);
+    uint64_t es = pub + ie_s - nsplit_e, em = pub + te_s + ie_m - nmain_e;
+    uint64_t bs = ptiles + it_s - split_tiles, bm = ptiles + tt_s + it_m - main_tiles;
     for (uint32_t i = 0; i < take; ++i) {
-      if (kinds & (1u << (2 * i))) {
-        PubEntry e{tidx[i], kPhaseSplit};
-        p.pubq[ps++ & (p.qcap - 1)] = e;
+      if (tsplit[i]) {
+        PubEntry e{bs, es, tidx[i], kPhaseSplit, tsplit[i], 0};
+        p.pubq[es & (p.qcap - 1)] = e;
+        ++es;
+        bs += tsplit[i];
       }
-      if (kinds & (1u << (2 * i + 1))) {
-        PubEntry e{tidx[i], kPhaseMain};
-        p.pubq[pm++ & (p.qcap - 1)] = e;
-      }
-    }
-    __threadfence();
-    fence_tensormap_release();
-    for (uint32_t i = 0; i < take; ++i) {
-      if (kinds & (3u << (2 * i))) {
-        atomicExch(&p.tasks[tidx[i]].claimed[0], 0u);
-        atomicExch(&p.tasks[tidx[i]].claimed[1], 0u);
+      if (tmain[i]) {
+        PubEntry e{bm, em, tidx[i], kPhaseMain, tmain[i], 0};
+        p.pubq[em & (p.qcap - 1)] = e;
+        ++em;
+        bm += tmain[i];
       }
     }
     if (valid && take > 0) *reinterpret_cast<volatile uint32_t*>(&p.tail[r]) = t + take;
     pending += avail - take;
-    pub += tot_s + tot_m;
+    pub += te_s + te_m;
+    ptiles += tt_s + tt_m;
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) pending += __shfl_xor_sync(0xffffffffu, pending, d);
   const uint32_t any_bad = __any_sync(0xffffffffu, bad);
   __threadfence();
+  fence_tensormap_release();
+  __syncwarp();
   if (lane == 0) {
     if (pending == 0 && pub == pub0)
       *reinterpret_cast<volatile uint64_t*>(&p.ctrl->quiet_until) = now + kQuietNs;
-    if (pub != pub0) st_release_gpu64(&p.ctrl->published, pub);
+    if (pub != pub0) {
+      st_release_gpu64(&p.ctrl->published, pub);
+      st_release_gpu64(&p.ctrl->published_tiles, ptiles);
+    }
     *reinterpret_cast<volatile uint32_t*>(&p.ctrl->rr) = (rr + 1) % p.ranks;
     __threadfence();
     atomicExch(&p.ctrl->ingest_lock, 0u);
@@ -242,63 +252,95 @@ __device__ __forceinline__ uint64_t bcast64(uint64_t v) {
   return ((uint64_t)hi << 32) | lo;
 }
 
+// A CTA's claim state, kept in shared memory across calls: a tile index
+// handed out by next_tile that may lie beyond the published tiles (then the
+// CTA waits for it, ingesting meanwhile), and where its entry search resumes.
+struct Claim {
+  uint64_t resv;     // reserved tile index
+  uint64_t hint;     // queue entry to start the next search at
+  uint32_t has_resv;
+  uint32_t pad;
+};
+
 // Warp 0: find the next tile to run. Returns 1 with (task, phase, tile) set,
-// or 0 when the kernel should exit. Every decision is taken on values lane 0
-// read and broadcast, so the warp never diverges across the shuffles.
-__device__ int acquire(const SchedParams& p, uint32_t& task, uint32_t& phase, uint32_t& tile,
-                       uint64_t& idle_since, uint64_t* prof) {
+// 0 when the kernel should exit, and (only when !blocking) 2 when the
+// reserved tile is not published yet. Decisions use values lane 0 read and
+// broadcast, so the warp never diverges across the shuffles.
+//
+// Claiming is one atomicAdd on next_tile per tile: there is no per-entry
+// counter for all CTAs to contend on. A tile beyond published_tiles is a
+// reservation; tiles are published in increasing order, so it becomes valid
+// without further claims.
+__device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t& phase, uint32_t& tile,
+                       uint64_t* prof, bool blocking) {
   const int lane = threadIdx.x & 31;
   uint64_t stall_since = 0;
   while (true) {
     uint32_t abort = 0, drained = 0;
-    uint64_t cur = 0, pub = 0, now = 0, quiet = 0;
+    uint64_t pt = 0, now = 0, quiet = 0, x = 0;
     if (lane == 0) {
       abort = ld_relaxed_gpu(&p.ctrl->abort);
       drained = ld_relaxed_gpu(&p.ctrl->drained);
-      cur = ld_relaxed_gpu64(&p.ctrl->cursor);
-      pub = ld_acquire_gpu64(&p.ctrl->published);
+      if (!cl->has_resv) {
+        cl->resv = atomicAdd(reinterpret_cast<unsigned long long*>(&p.ctrl->next_tile), 1ull);
+        cl->has_resv = 1;
+      }
+      x = cl->resv;
+      pt = ld_acquire_gpu64(&p.ctrl->published_tiles);
       quiet = ld_relaxed_gpu64(&p.ctrl->quiet_until);
       now = globaltimer();
     }
     if (bcast(abort)) return 0;
     drained = bcast(drained);
-    cur = bcast64(cur);
-    pub = bcast64(pub);
+    x = bcast64(x);
+    pt = bcast64(pt);
     now = bcast64(now);
     quiet = bcast64(quiet);
-    if (cur < pub) {
-      // Keep the queue ahead of the CTAs, unless a recent pass found the rings empty.
-      if (pub - cur <= kLookahead && now >= quiet) (void)ingest(p, prof);
-      uint32_t x = 0, etask = 0, ephase = 0, cnt = 0;
+    if (x < pt) {
+      // Keep the queue ahead of the CTAs.
+      if (pt - x <= kLookaheadTiles && now >= quiet) (void)ingest(p, prof);
+      uint32_t etask = 0, ephase = 0, off = 0, ok = 1;
       if (lane == 0) {
-        const uint64_t raw = ld_relaxed_gpu64(reinterpret_cast<const uint64_t*>(&p.pubq[cur & (p.qcap - 1)]));
-        etask = (uint32_t)raw;
-        ephase = (uint32_t)(raw >> 32) & 1u;
-        x = atomicAdd(&p.tasks[etask].claimed[ephase], 1u);
-        __threadfence();
-        const TaskBody* b = &p.tasks[etask].body;
-        const uint32_t ntiles = ld_relaxed_gpu(&b->ntiles);
-        const uint32_t nsplit = ld_relaxed_gpu(&b->nsplit);
-        cnt = (ephase == kPhaseSplit) ? nsplit : ntiles - nsplit;
-        if (x >= cnt)
-          atomicMax(reinterpret_cast<unsigned long long*>(&p.ctrl->cursor), (unsigned long long)(cur + 1));
+        uint64_t e = cl->hint;
+        const uint64_t lo = ld_relaxed_gpu64(&p.ctrl->cursor);
+        if (e < lo) e = lo;
+        while (true) {
+          const PubEntry* pe = &p.pubq[e & (p.qcap - 1)];
+          const uint64_t seq = ld_relaxed_gpu64(&pe->seq);
+          const uint64_t base = ld_relaxed_gpu64(&pe->base);
+          const uint32_t cnt = ld_relaxed_gpu(&pe->cnt);
+          if (seq != e) {  // the slot was overwritten: the ring bound was broken
+            ok = 0;
+            break;
+          }
+          if (x < base + cnt) {
+            etask = ld_relaxed_gpu(&pe->task);
+            ephase = ld_relaxed_gpu(&pe->phase) & 1u;
+            off = (uint32_t)(x - base);
+            if (x + 1 == base + cnt)
+              atomicMax(reinterpret_cast<unsigned long long*>(&p.ctrl->cursor), (unsigned long long)(e + 1));
+            break;
+          }
+          ++e;
+        }
+        cl->hint = e;
+        cl->has_resv = 0;
       }
-      x = bcast(x);
-      cnt = bcast(cnt);
-      if (x < cnt) {
-        task = bcast(etask);
-        phase = bcast(ephase);
-        tile = x;
-        idle_since = 0;
-        return 1;
+      if (!bcast(ok)) {
+        if (lane == 0) report_error(p, kStatusBadTask, kWhereQueueFull, (uint32_t)x);
+        __syncwarp();
+        return 0;
       }
-      continue;
+      task = bcast(etask);
+      phase = bcast(ephase);
+      tile = bcast(off);
+      return 1;
     }
+    // The reserved tile is not published yet.
     if (p.drain && drained) return 0;
     const IngestOut r = ingest(p, prof);
     if (r.published) {
       stall_since = 0;
-      idle_since = 0;
       continue;
     }
     if (!r.locked_out) {
@@ -312,7 +354,7 @@ __device__ int acquire(const SchedParams& p, uint32_t& task, uint32_t& phase, ui
         uint32_t stop = 0;
         if (lane == 0) stop = ld_acquire_sys(&p.host_shared->stop);
         if (bcast(stop)) return 0;
-      } else {
+      } else if (blocking) {
         if (stall_since == 0) stall_since = now;
         else if (now - stall_since > p.wait_timeout_ns) {
           if (lane == 0) report_error(p, kStatusTimeout, kWhereReadyWait, r.pending);
@@ -321,6 +363,10 @@ __device__ int acquire(const SchedParams& p, uint32_t& task, uint32_t& phase, ui
         }
       }
     }
+    // Nothing to run yet. A look-ahead claim (made while the CTA still works
+    // on its current tile) must not wait: the current tile's completion is
+    // published only after it returns. The reservation is kept.
+    if (!blocking) return 2;
     __nanosleep(r.locked_out ? 200u : (uint32_t)p.idle_poll_ns);
   }
 }
@@ -345,37 +391,55 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
   } else {
     __syncthreads();
   }
-  uint64_t idle_since = 0;
+  Claim* cl = reinterpret_cast<Claim*>(sh.claim);
+  if (tid == 0) {
+    cl->has_resv = 0;
+    cl->hint = ld_relaxed_gpu64(&p.ctrl->cursor);
+  }
+  __syncthreads();
 
-  while (true) {
-    if (warp == 0) {
-      const uint64_t t_acq = globaltimer();
-      uint32_t task = 0, phase = 0, tile = 0;
-      const int got = acquire(p, task, phase, tile, idle_since, sh.prof);
-      if (lane == 0) {
-        sh.go = (uint32_t)got;
-        sh.task = task;
-        sh.phase = phase;
-        sh.tile = tile;
-      }
-      if (got && lane < (int)(sizeof(TaskBody) / 16)) {
-        const uint4 v = ld_cg_v4(reinterpret_cast<const uint4*>(&p.tasks[task].body) + lane);
-        reinterpret_cast<uint4*>(&sh.body)[lane] = v;
-      }
-      if (lane == 0) sh.prof[kProfAcquire] += globaltimer() - t_acq;
+  // Warp 0: claim a tile into slot s (blocking: wait for work; otherwise
+  // return at once with go = 2 when nothing is claimable).
+  auto claim = [&](int slot, bool blocking) {
+    const uint64_t t_acq = globaltimer();
+    uint32_t task = 0, phase = 0, tile = 0;
+    const int got = acquire(p, cl, task, phase, tile, sh.prof, blocking);
+    if (lane == 0) {
+      sh.go[slot] = (uint32_t)got;
+      sh.task[slot] = task;
+      sh.phase[slot] = phase;
+      sh.tile[slot] = tile;
     }
-    __syncthreads();
-    if (!sh.go || sh.abort) break;
+    if (got == 1 && lane < (int)(sizeof(TaskBody) / 16)) {
+      const uint4 v = ld_cg_v4(reinterpret_cast<const uint4*>(&p.tasks[task].body) + lane);
+      reinterpret_cast<uint4*>(&sh.body[slot])[lane] = v;
+    }
+    __syncwarp();
+    if (lane == 0) sh.prof[kProfAcquire] += globaltimer() - t_acq;
+  };
+
+  if (warp == 0) claim(0, true);
+  __syncthreads();
+  int cur = 0;
+  while (true) {
+    if (sh.go[cur] != 1 || sh.abort) break;
+    const int nxt = cur ^ 1;
     const uint64_t t_tile = tid == 0 ? globaltimer() : 0;
-    const TaskBody& b = sh.body;
-    const uint32_t task = sh.task, phase = sh.phase, tile = sh.tile;
+    const TaskBody& b = sh.body[cur];
+    const uint32_t task = sh.task[cur], phase = sh.phase[cur], tile = sh.tile[cur];
     int bucket = kProfVadd;
+    bool early = false;  // warp 0 claims the next tile while this one runs
 
     if (b.type == kTaskVadd) {
       const int64_t lo = (int64_t)tile * b.vadd_tile;
       const int64_t hi = min(b.n, lo + b.vadd_tile);
-      vadd_range(reinterpret_cast<const float*>(b.a), reinterpret_cast<const float*>(b.b),
-                 reinterpret_cast<float*>(b.c), lo, hi);
+      if (warp == 0) {
+        claim(nxt, false);
+      } else {
+        vadd_range(reinterpret_cast<const float*>(b.a), reinterpret_cast<const float*>(b.b),
+                   reinterpret_cast<float*>(b.c), lo, hi, tid - 32, kThreads - 32);
+      }
+      early = true;
     } else {
       const float* A = reinterpret_cast<const float*>(b.a);
       const float* B = reinterpret_cast<const float*>(b.b);
@@ -387,15 +451,20 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
       } else {
         if (phase == kPhaseSplit) {
           bucket = kProfSplit;
-          const uint32_t tiles_a = (uint32_t)((b.m + kSplitRows - 1) / kSplitRows);
-          if (tile < tiles_a) {
-            split_a_tile(A, reinterpret_cast<__nv_bfloat16*>(b.scratch), b.m, b.k, (int)b.kp,
-                         (int)(tile * kSplitRows), kSplitRows);
+          if (warp == 0) {
+            claim(nxt, false);
           } else {
-            split_b_tile(B, reinterpret_cast<__nv_bfloat16*>(b.scratch_b), b.n, b.k, (int)b.kp,
-                         (int64_t)(tile - tiles_a) * kSplitRows, kSplitRows);
+            const uint32_t tiles_a = (uint32_t)((b.m + kSplitRows - 1) / kSplitRows);
+            if (tile < tiles_a) {
+              split_a_tile(A, reinterpret_cast<__nv_bfloat16*>(b.scratch), b.m, b.k, (int)b.kp,
+                           (int)(tile * kSplitRows), kSplitRows, tid - 32, kThreads - 32);
+            } else {
+              split_b_tile(B, reinterpret_cast<__nv_bfloat16*>(b.scratch_b), b.n, b.k, (int)b.kp,
+                           (int64_t)(tile - tiles_a) * kSplitRows, kSplitRows, tid - 32, kThreads - 32);
+            }
+            fence_proxy_async_global();
           }
-          fence_proxy_async_global();
+          early = true;
         } else {
           bucket = kProfGemm;
           const int tm = (int)(tile / b.tiles_n), tn = (int)(tile % b.tiles_n);
@@ -403,9 +472,14 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
           tc_tile(&dt->body.tmA, &dt->body.tmB, C, b.m, b.n, b.k, tm, tn, big, &sh.tc, it, tile_no,
                   p.wait_timeout_ns, b.nsplit ? &dt->split_done : nullptr, b.nsplit, &sh.abort,
                   &sh.fail_where, true, &sh.prof[kProfSplitWait]);
+          // The producer has issued every load of this tile; it claims the
+          // next tile while the MMA and epilogue warps finish.
+          if (warp == 0) claim(nxt, false);
+          early = true;
         }
       }
     }
+    if (!early && warp == 0 && lane == 0) sh.go[nxt] = 2;
     __threadfence();
     __syncthreads();
     if (sh.abort) {
@@ -424,6 +498,13 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
         complete_task(p, task, b.tag, b.flags, t_in);
       }
     }
+    if (sh.go[nxt] == 2) {
+      // Nothing was claimable while the tile ran: wait for work now that its
+      // completion is published.
+      if (warp == 0) claim(nxt, true);
+      __syncthreads();
+    }
+    cur = nxt;
   }
 
   if constexpr (PATH == kPathSplit3) {
@@ -444,6 +525,9 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
       for (int i = 0; i < 8; ++i)
         st_relaxed_sys64(&hs->k_prof[i], atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), 0ull));
       st_relaxed_sys64(&hs->k_exit, globaltimer());
+      // Reservations beyond the published tiles died with their CTAs.
+      atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->next_tile),
+                 (unsigned long long)ld_relaxed_gpu64(&p.ctrl->published_tiles));
       atomicExch(&p.ctrl->exit_count, 0u);
       atomicExch(&p.ctrl->drained, 0u);
       atomicExch(&p.ctrl->ingest_lock, 0u);
