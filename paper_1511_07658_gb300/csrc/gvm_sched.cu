@@ -39,6 +39,7 @@ struct alignas(128) SchedShared {
   uint32_t task[2];
   uint32_t phase[2];
   uint32_t tile[2];
+  uint32_t need[2];  // per iteration parity: a blocking claim must follow the tile
   uint32_t abort;
   uint32_t fail_where;
   uint64_t prof[8];  // this CTA's phase counters (kProf*), written by thread 0 only
@@ -479,7 +480,14 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
         }
       }
     }
-    if (!early && warp == 0 && lane == 0) sh.go[nxt] = 2;
+    // need[cur]: the look-ahead claim found nothing, so warp 0 must claim
+    // (blocking) after this tile. Written before the barrier and not touched
+    // again until two tiles later, so every thread reads the same value (the
+    // blocking claim itself rewrites go[nxt] while others may still look).
+    if (warp == 0 && lane == 0) {
+      if (!early) sh.go[nxt] = 2;
+      sh.need[cur] = sh.go[nxt] == 2 ? 1u : 0u;
+    }
     __threadfence();
     __syncthreads();
     if (sh.abort) {
@@ -498,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
         complete_task(p, task, b.tag, b.flags, t_in);
       }
     }
-    if (sh.go[nxt] == 2) {
+    if (sh.need[cur]) {
       // Nothing was claimable while the tile ran: wait for work now that its
       // completion is published.
       if (warp == 0) claim(nxt, true);
