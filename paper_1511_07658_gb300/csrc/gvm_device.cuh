@@ -600,28 +600,28 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* tmA, const CUtensorMa
       }
     } else {
       tc_fence_after();
-      const int row = tm * kTcM + q * 32 + lane;
-      const bool cvec = ((n & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
-      float* crow = C + (int64_t)row * n;
+      // TMEM gives each thread one row; a 32 x 32 block goes through a
+      // warp-private shared-memory tile (row pitch 33 words: no bank
+      // conflicts either way) so that every store of the warp writes 32
+      // consecutive floats of one row of C. The pipeline stages are free:
+      // every MMA of this tile has completed.
+      float* stage = reinterpret_cast<float*>(stages) + q * (32 * 33);
+      const int row0 = tm * kTcM + q * 32;
 #pragma unroll 1
       for (int ch = 0; ch < kTcN / 32; ++ch) {
         uint32_t r[32];
         tmem_ld_32x32b_x32(ts->tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32), r);
         tmem_ld_wait();
-        const int64_t c0 = (int64_t)tn * kTcN + ch * 32;
-        if (row < m) {
-          if (cvec && c0 + 32 <= n) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              *reinterpret_cast<float4*>(crow + c0 + 4 * j) =
-                  make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                              __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (c0 + j < n) crow[c0 + j] = __uint_as_float(r[j]);
-          }
+        for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int64_t c = (int64_t)tn * kTcN + ch * 32 + lane;
+        if (c < n) {
+          const int rows = min(32, m - row0);
+#pragma unroll 4
+          for (int i = 0; i < rows; ++i) C[(int64_t)(row0 + i) * n + c] = stage[i * 33 + lane];
         }
+        __syncwarp();
       }
     }
     tc_fence_before();

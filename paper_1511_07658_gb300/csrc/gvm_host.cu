@@ -236,6 +236,35 @@ int push_flushed(gvm_rank* r) {
   return push_out_ops(r, f);
 }
 
+// Bounded wait for the scheduler stream (wait_timeout_ns plus a grace
+// period). On timeout the device control block is read back on a separate
+// stream and traced, and GVM_ETIMEDOUT is returned.
+int wait_scheduler(gvm_ctx* ctx) {
+  const uint64_t t0 = now_ns();
+  while (true) {
+    const cudaError_t e = cudaStreamQuery(ctx->sched);
+    if (e == cudaSuccess) return GVM_OK;
+    if (e != cudaErrorNotReady) return GVM_EDEVICE;
+    if (now_ns() - t0 > ctx->cfg.wait_timeout_ns + kHostGraceNs) break;
+    std::this_thread::yield();
+  }
+  DevCtrl c;
+  memset(&c, 0, sizeof(c));
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess) {
+    if (cudaMemcpyAsync(&c, ctx->params.ctrl, sizeof(c), cudaMemcpyDeviceToHost, s) == cudaSuccess)
+      cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  fprintf(stderr,
+          "[gvm] scheduler did not stop: lock=%u abort=%u exit_count=%u drained=%u published=%llu "
+          "tiles=%llu next_tile=%llu consumed=%llu status=%u\n",
+          c.ingest_lock, c.abort, c.exit_count, c.drained, (unsigned long long)c.published,
+          (unsigned long long)c.published_tiles, (unsigned long long)c.next_tile, (unsigned long long)c.cursor,
+          ld_acq(&ctx->shared->status));
+  return GVM_ETIMEDOUT;
+}
+
 bool is_pinned(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -673,8 +702,10 @@ int gvm_flush(gvm_ctx* ctx) {
 int gvm_wait_idle(gvm_ctx* ctx) {
   if (!ctx) return GVM_EINVAL;
   bind_device(ctx);
-  cudaError_t e = cudaStreamSynchronize(ctx->sched);
-  if (e != cudaSuccess) return GVM_EDEVICE;
+  if (ctx->cfg.mode == GVM_MODE_BARRIER) {  // a resident scheduler only stops at shutdown
+    const int rc = wait_scheduler(ctx);
+    if (rc != GVM_OK) return rc;
+  }
   for (auto& rk : ctx->ranks) {
     if (cudaStreamSynchronize(rk->in_stream) != cudaSuccess) return GVM_EDEVICE;
     if (cudaStreamSynchronize(rk->out_stream) != cudaSuccess) return GVM_EDEVICE;
@@ -742,8 +773,14 @@ int gvm_shutdown(gvm_ctx* ctx) {
     std::lock_guard<std::mutex> g(rk->mu);
     if (rc == GVM_OK && push_out_ops(rk.get(), rk->next_seq) != GVM_OK) rc = GVM_EDEVICE;
   }
-  GVM_TRACE("shutdown: output ops pushed, syncing scheduler stream");
-  if (cudaStreamSynchronize(ctx->sched) != cudaSuccess) rc = GVM_EDEVICE;
+  GVM_TRACE("shutdown: output ops pushed, waiting for the scheduler");
+  const int wrc = wait_scheduler(ctx);
+  if (wrc == GVM_ETIMEDOUT) {
+    // The scheduler did not stop within the bound: leave the rings allocated
+    // (the kernel may still read them) and report.
+    return GVM_ETIMEDOUT;
+  }
+  if (wrc != GVM_OK) rc = wrc;
   const bool device_ok = ld_acq(&ctx->shared->status) == 0;
   GVM_TRACE("shutdown: scheduler idle, device_ok=%d", (int)device_ok);
   const DriverApi* api = driver_api();

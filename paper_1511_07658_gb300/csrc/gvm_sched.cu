@@ -281,7 +281,7 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
     uint64_t pt = 0, now = 0, quiet = 0, x = 0;
     if (lane == 0) {
       abort = ld_relaxed_gpu(&p.ctrl->abort);
-      drained = ld_relaxed_gpu(&p.ctrl->drained);
+      drained = ld_acquire_gpu(&p.ctrl->drained);
       if (!cl->has_resv) {
         cl->resv = atomicAdd(reinterpret_cast<unsigned long long*>(&p.ctrl->next_tile), 1ull);
         cl->has_resv = 1;
@@ -337,8 +337,20 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
       tile = bcast(off);
       return 1;
     }
-    // The reserved tile is not published yet.
-    if (p.drain && drained) return 0;
+    // The reserved tile is not published yet. Before leaving, look at the
+    // published tiles once more: another CTA's last ingest pass may have
+    // published the reserved tile since pt was read, and a tile whose owner
+    // leaves would never run. Once the rings are drained (or stop is set with
+    // nothing pending) no further tile is published, so this read is final.
+    auto reserved_published = [&]() -> bool {
+      uint64_t pt2 = 0;
+      if (lane == 0) pt2 = ld_acquire_gpu64(&p.ctrl->published_tiles);
+      return x < bcast64(pt2);
+    };
+    if (p.drain && drained) {
+      if (reserved_published()) continue;
+      return 0;
+    }
     const IngestOut r = ingest(p, prof);
     if (r.published) {
       stall_since = 0;
@@ -350,11 +362,15 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
         if (p.drain) {
           if (lane == 0) atomicExch(&p.ctrl->drained, 1u);
           __syncwarp();
+          if (reserved_published()) continue;
           return 0;
         }
         uint32_t stop = 0;
         if (lane == 0) stop = ld_acquire_sys(&p.host_shared->stop);
-        if (bcast(stop)) return 0;
+        if (bcast(stop)) {
+          if (reserved_published()) continue;
+          return 0;
+        }
       } else if (blocking) {
         if (stall_since == 0) stall_since = now;
         else if (now - stall_since > p.wait_timeout_ns) {
