@@ -62,7 +62,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gvm", "reference"], default="gvm")
-    p.add_argument("--workload", choices=["sgemm512", "vadd_tiny"], default="sgemm512")
+    p.add_argument("--workload", choices=["sgemm512", "vadd_tiny", "serving"], default="sgemm512")
+    p.add_argument("--serving-tasks", type=int, default=0, help="serving workload: total tasks (default 4096)")
     p.add_argument("--path", choices=["split3", "fma"], default="split3")
     p.add_argument("--mode", choices=["barrier", "continuous"], default="barrier")
     p.add_argument("--skip-e2e", action="store_true")
@@ -628,6 +629,133 @@ def plain_per_rank(w):
     }
 
 
+# --------------------------------------------------------------- serving loop
+
+
+def serving_arm(args):
+    """Open-loop serving: 16 ranks, 4096 tasks, Poisson arrivals with a mean
+    gap of 20 us per rank, half vector adds (n = floor(2^(16+8u))) and half
+    square SGEMMs (side from {256, 512, 1024, 2048}), admission capped at
+    32 GiB of device buffers. The manager runs in continuous mode: tasks are
+    admitted as ring slots and staging space free up while others run.
+
+    Latency of a task = the moment its rank observes completion minus its
+    scheduled arrival time (so a rank that falls behind does not hide queueing
+    delay). Operands: per size, one seeded input set shared by every task of
+    that size (the latency and throughput do not depend on values; parity of
+    the mix is covered by the GPU tests); outputs go to per-rank pinned
+    buffers, one per in-flight slot.
+    """
+    import torch
+
+    import paper_1511_07658_gb300 as g
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = synth.serving_mix(ranks=16, total=args.serving_tasks or 4096)
+    R = w.ranks
+    depth = 8
+    vmax = max(t.n for t in w.tasks if t.kind == synth.TASK_VADD)
+    a, b = synth.vadd_inputs(4242, vmax)
+    va, vb = torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()
+    sides = sorted({t.m for t in w.tasks if t.kind == synth.TASK_SGEMM})
+    gin = {}
+    for sd in sides:
+        A, B = synth.sgemm_inputs(9000 + sd, sd, sd, sd)
+        gin[sd] = (torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory())
+    out_elems = max(vmax, max(sd * sd for sd in sides))
+    outs = [[torch.empty(out_elems).pin_memory() for _ in range(depth)] for _ in range(R)]
+    smax = max(sd for sd in sides)
+    per_task = max(12 * vmax, 12 * smax * smax + g.sgemm_scratch_bytes(smax, smax, smax, args.path)) + (1 << 20)
+    mgr = g.Manager(R, ring_depth=depth, mode="continuous", sgemm_path=args.path,
+                    slice_bytes=per_task * 2 + (64 << 20), admission_cap_bytes=32 << 30,
+                    ingest_quantum=args.quantum)
+    ranks = [mgr.attach(r) for r in range(R)]
+    by_rank = w.by_rank()
+    lat = [[] for _ in range(R)]
+    done_at = [0.0] * R
+    bytes_moved = [0] * R
+    start = time.perf_counter() + 0.05
+
+    def run_rank(r):
+        rk = ranks[r]
+        inflight = []  # (seq, arrival, slot)
+        free = list(range(depth))
+
+        def reap(block):
+            while inflight:
+                seq, arr, slot = inflight[0]
+                if block:
+                    rk.sync(seq)
+                elif not rk.poll(seq):
+                    return
+                lat[r].append(time.perf_counter() - arr)
+                free.append(slot)
+                inflight.pop(0)
+                if block:
+                    return
+
+        for spec in by_rank[r]:
+            arrival = start + spec.arrival_s
+            while True:
+                reap(False)
+                if time.perf_counter() >= arrival and free:
+                    break
+                if not free and inflight:
+                    reap(True)
+            slot = free.pop()
+            t = g.GvmTask()
+            if spec.kind == synth.TASK_VADD:
+                t.type, t.n = g.GVM_TASK_VADD, spec.n
+                t.a, t.b, t.c = va.data_ptr(), vb.data_ptr(), outs[r][slot].data_ptr()
+                bytes_moved[r] += 12 * spec.n
+            else:
+                A, B = gin[spec.m]
+                t.type, t.m, t.n, t.k = g.GVM_TASK_SGEMM, spec.m, spec.n, spec.k
+                t.a, t.b, t.c = A.data_ptr(), B.data_ptr(), outs[r][slot].data_ptr()
+                bytes_moved[r] += 12 * spec.m * spec.m
+            while True:
+                seq = c_uint64_holder()
+                rc = g.lib().gvm_submit(rk.handle, ctypes.byref(t), ctypes.byref(seq))
+                if rc == g.GVM_EAGAIN:
+                    reap(True) if inflight else time.sleep(0)
+                    continue
+                g._abi.check(rc, "gvm_submit")
+                break
+            inflight.append((seq.value, arrival, slot))
+        while inflight:
+            reap(True)
+        done_at[r] = time.perf_counter()
+
+    with ThreadPoolExecutor(max_workers=R) as ex:
+        list(ex.map(run_rank, range(R)))
+    span = max(done_at) - start
+    all_lat = sorted(x for l in lat for x in l)
+    st = mgr.stats()
+    mgr.shutdown()
+    total = len(w.tasks)
+    return {
+        "metric": METRIC + " (serving loop)",
+        "value": total / span,
+        "unit": "tasks/s",
+        "n_gpus": 1,
+        "higher_is_better": True,
+        "dtype": "bf16x3->f32" if args.path == "split3" else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"serving mix: 16 ranks, {total} tasks, Poisson 20 us mean gap per rank, "
+                   "50/50 vector add n~2^(16+8u) / square SGEMM {256,512,1024,2048}, cap 32 GiB",
+                   "mode": "continuous", "sgemm_path": args.path, "ring_depth": depth},
+        "latency_us": {"p50": 1e6 * percentile(all_lat, 50), "p99": 1e6 * percentile(all_lat, 99),
+                       "p999": 1e6 * percentile(all_lat, 99.9), "kind": "scheduled arrival -> completion seen by the rank"},
+        "host_link_gbs": sum(bytes_moved) / span / 1e9,
+        "staged_peak_bytes": st["staged_peak"],
+        "device_status": st["device_status"],
+    }
+
+
+class c_uint64_holder(ctypes.c_uint64):
+    pass
+
+
 # --------------------------------------------------------------- model check
 
 
@@ -722,6 +850,13 @@ def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.workload == "serving":
+        if args.impl == "reference" or rank != 0:
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the serving loop has no CPU reference arm"}))
+            return
+        print(json.dumps(serving_arm(args)))
+        return
     w, desc = workload(args.workload, args.ranks, args.per_rank)
     if args.impl == "reference":
         if rank != 0:

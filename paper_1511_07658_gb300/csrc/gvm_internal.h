@@ -145,7 +145,8 @@ struct alignas(256) DevCtrl {
   uint64_t prof[8];       // this launch: summed CTA time per phase (see kProf*)
   uint64_t published_tiles;  // tiles of all published entries (one global tile space)
   uint64_t next_tile;        // next tile index to hand out (may run ahead: a reservation)
-  uint32_t pad[28];
+  uint64_t first_entry;      // entries published before the current launch began
+  uint32_t pad[26];
 };
 static_assert(sizeof(DevCtrl) == 256, "DevCtrl layout");
 
@@ -195,7 +196,7 @@ inline CtrlLayout ctrl_layout(uint32_t ranks, uint32_t depth) {
   CtrlLayout L;
   uint64_t slots = (uint64_t)ranks * depth;
   uint32_t q = 1;
-  while (q < 4 * slots || q < 256) q <<= 1;
+  while (q < 4 * slots || q < 4096) q <<= 1;
   L.qcap = q;
   uint64_t off = sizeof(DevCtrl);
   L.off_tail = off;   off = align_up(off + 4ull * ranks, 256);

@@ -11,12 +11,16 @@
 // stream per process, without a kernel launch per task.
 //
 // Work flow per CTA:
-//   claim:   entry e at the publication-queue cursor; atomically take the next
-//            tile of e's task and phase; advance the cursor when e is used up.
-//   ingest:  when nothing is claimable, one CTA (holding a lock) copies ready
-//            descriptors from the host rings into the device task table and
-//            appends queue entries (split phases of a pass before main phases,
-//            so the split3 pre-pass of a task runs well ahead of its GEMM).
+//   claim:   every queue entry covers a contiguous range of one global tile
+//            space; a CTA takes the next tile index with one atomicAdd on
+//            next_tile and finds its entry by a short forward search. An
+//            index beyond the published tiles is a reservation the CTA waits
+//            for (ingesting meanwhile). Warp 0 claims the next tile while the
+//            other warps run the current one.
+//   ingest:  one CTA at a time (holding a lock) copies ready descriptors from
+//            the host rings into the device task table and appends queue
+//            entries (split phases of a pass before main phases, so the
+//            split3 pre-pass of a task runs well ahead of its GEMM).
 //   finish:  the CTA that completes a task's last tile publishes completion:
 //            the host completion word (resident tasks) or the device done word
 //            on which the rank's output-copy stream waits (host-buffer tasks).
@@ -300,32 +304,51 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
     if (x < pt) {
       // Keep the queue ahead of the CTAs.
       if (pt - x <= kLookaheadTiles && now >= quiet) (void)ingest(p, prof);
+      // Find the entry holding tile x: the last entry with base <= x. Entries
+      // are published in tile order, and x only grows from one claim of a CTA
+      // to the next, so the search starts at the entry of this CTA's previous
+      // tile; the warp checks 32 entries per step.
       uint32_t etask = 0, ephase = 0, off = 0, ok = 1;
-      if (lane == 0) {
-        uint64_t e = cl->hint;
-        const uint64_t lo = ld_relaxed_gpu64(&p.ctrl->cursor);
-        if (e < lo) e = lo;
-        while (true) {
-          const PubEntry* pe = &p.pubq[e & (p.qcap - 1)];
-          const uint64_t seq = ld_relaxed_gpu64(&pe->seq);
-          const uint64_t base = ld_relaxed_gpu64(&pe->base);
-          const uint32_t cnt = ld_relaxed_gpu(&pe->cnt);
-          if (seq != e) {  // the slot was overwritten: the ring bound was broken
-            ok = 0;
-            break;
-          }
-          if (x < base + cnt) {
-            etask = ld_relaxed_gpu(&pe->task);
-            ephase = ld_relaxed_gpu(&pe->phase) & 1u;
-            off = (uint32_t)(x - base);
-            if (x + 1 == base + cnt)
-              atomicMax(reinterpret_cast<unsigned long long*>(&p.ctrl->cursor), (unsigned long long)(e + 1));
-            break;
-          }
-          ++e;
+      uint64_t e0 = 0;
+      if (lane == 0) e0 = cl->hint;
+      e0 = bcast64(e0);
+      while (true) {
+        const uint64_t e = e0 + (uint64_t)lane;
+        const PubEntry* pe = &p.pubq[e & (p.qcap - 1)];
+        const uint64_t seq = ld_relaxed_gpu64(&pe->seq);
+        const uint64_t base = ld_relaxed_gpu64(&pe->base);
+        const bool le = (seq == e) && base <= x;
+        const uint32_t m = __ballot_sync(0xffffffffu, le);
+        if (m == 0) {  // not even the first entry starts at or before x
+          ok = 0;
+          break;
         }
-        cl->hint = e;
-        cl->has_resv = 0;
+        const int last = 31 - __clz(m);
+        if (last == 31 && (m & 1u)) {  // the whole window precedes x: move on
+          e0 += 31;
+          continue;
+        }
+        const uint32_t cnt = ld_relaxed_gpu(&pe->cnt);
+        const uint32_t tk = ld_relaxed_gpu(&pe->task);
+        const uint32_t ph = ld_relaxed_gpu(&pe->phase);
+        const uint64_t hit_base = __shfl_sync(0xffffffffu, base, last);
+        const uint32_t hit_cnt = __shfl_sync(0xffffffffu, cnt, last);
+        etask = __shfl_sync(0xffffffffu, tk, last);
+        ephase = __shfl_sync(0xffffffffu, ph, last) & 1u;
+        if (x >= hit_base + hit_cnt) {  // a hole in the tile space: the ring bound was broken
+          ok = 0;
+          break;
+        }
+        off = (uint32_t)(x - hit_base);
+        if (lane == 0) {
+          const uint64_t ehit = e0 + (uint64_t)last;
+          if (x + 1 == hit_base + hit_cnt)
+            atomicMax(reinterpret_cast<unsigned long long*>(&p.ctrl->cursor), (unsigned long long)(ehit + 1));
+          cl->hint = ehit;
+          cl->has_resv = 0;
+        }
+        __syncwarp();
+        break;
       }
       if (!bcast(ok)) {
         if (lane == 0) report_error(p, kStatusBadTask, kWhereQueueFull, (uint32_t)x);
@@ -411,7 +434,9 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
   Claim* cl = reinterpret_cast<Claim*>(sh.claim);
   if (tid == 0) {
     cl->has_resv = 0;
-    cl->hint = ld_relaxed_gpu64(&p.ctrl->cursor);
+    // Tiles handed out by this launch lie in entries published after it began
+    // (a CTA may start after others of the launch have already published).
+    cl->hint = ld_relaxed_gpu64(&p.ctrl->first_entry);
   }
   __syncthreads();
 
@@ -549,9 +574,12 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
       for (int i = 0; i < 8; ++i)
         st_relaxed_sys64(&hs->k_prof[i], atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), 0ull));
       st_relaxed_sys64(&hs->k_exit, globaltimer());
-      // Reservations beyond the published tiles died with their CTAs.
+      // Reservations beyond the published tiles died with their CTAs; the
+      // next launch hands out tiles of entries published from here on.
       atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->next_tile),
                  (unsigned long long)ld_relaxed_gpu64(&p.ctrl->published_tiles));
+      atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->first_entry),
+                 (unsigned long long)ld_relaxed_gpu64(&p.ctrl->published));
       atomicExch(&p.ctrl->exit_count, 0u);
       atomicExch(&p.ctrl->drained, 0u);
       atomicExch(&p.ctrl->ingest_lock, 0u);

@@ -145,7 +145,11 @@ class Rank:
 
     # -- completion -------------------------------------------------------
     def sync(self, seq: int) -> None:
-        check(lib().gvm_sync(self.handle, seq), "gvm_sync")
+        rc = lib().gvm_sync(self.handle, seq)
+        if rc == _abi.GVM_EDEVICE and self.mgr.handle is not None:
+            st = self.mgr.stats()
+            check(rc, f"gvm_sync (device status {st['device_status']}, where {st['device_where']})")
+        check(rc, "gvm_sync")
 
     def poll(self, seq: int) -> bool:
         return check(lib().gvm_poll(self.handle, seq), "gvm_poll") == 1
