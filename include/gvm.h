@@ -66,6 +66,9 @@ extern "C" {
 #define GVM_SGEMM_FMA 0    /* binary32 fused multiply-add on the CUDA cores */
 #define GVM_SGEMM_SPLIT3 1 /* A = Ah + Al, B = Bh + Bl in bf16; C = AhBh + AhBl + AlBh on
                               tcgen05 tensor cores with binary32 accumulation in TMEM */
+#define GVM_SGEMM_SPLIT3_FUSED 2 /* the same split3 arithmetic (bit-identical results), with
+                              the split done while operands are staged into shared memory:
+                              no pre-pass and no scratch. gvm_sgemm_f32 only */
 
 /* ---- manager modes ------------------------------------------------------ */
 #define GVM_MODE_BARRIER 0    /* Section 5 request barrier: gvm_flush runs the scheduler

@@ -8,6 +8,7 @@
 
 #include "gvm.h"
 #include "gvm_device.cuh"
+#include "gvm_fused.cuh"
 #include "gvm_runtime.h"
 
 namespace gvm {
@@ -60,6 +61,53 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_tile(&tmA, &tmB, C, m, n, k, blockIdx.y, blockIdx.x, big, &ts, it, tile_no, timeout_ns, nullptr, 0,
           &abort_flag, &fail_where, false);
   tc_teardown(&ts);
+  if (threadIdx.x == 0 && abort_flag) atomicExch(&g_kernel_status, kStatusTimeout | (fail_where << 8));
+}
+
+// Fused split3 GEMM over all tiles of one product: a persistent grid, CTA i
+// takes tiles i, i + grid, ... (row-major over the tile grid). Every role
+// walks the same tile sequence; the control warp has nothing to do here.
+__global__ void __launch_bounds__(kFzThreads, 1)
+    fz_sgemm_kernel(const float* A, const float* B, float* C, int m, int n, int k, uint64_t timeout_ns) {
+  __shared__ FzShared fs;
+  __shared__ uint32_t abort_flag, fail_where;
+  extern __shared__ uint8_t dyn_smem[];
+  uint8_t* big = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    fail_where = 0;
+  }
+  fz_init(&fs);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_n = (n + kTcN - 1) / kTcN;
+  const int ntiles = ((m + kTcM - 1) / kTcM) * tiles_n;
+  const uint32_t nkb = (uint32_t)((k + kTcBK - 1) / kTcBK);
+  uint32_t it = 0, tile_no = 0;
+  if (warp < kFzConvWarps) {
+    FzTile prev{};
+    bool have_prev = false, ok = true;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
+      ok = fz_convert(t, big, &fs, it, timeout_ns, &abort_flag, &fail_where, nullptr);
+      if (ok && have_prev) ok = fz_epilogue(prev, &fs, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
+      prev = t;
+      have_prev = true;
+      it += nkb;
+      ++tile_no;
+    }
+    if (ok && have_prev) fz_epilogue(prev, &fs, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
+  } else if (warp == kFzMmaWarp) {
+    if (lane == 0) {
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
+        if (!fz_mma(t, big, &fs, it, tile_no, timeout_ns, &abort_flag, &fail_where, nullptr)) break;
+        it += nkb;
+        ++tile_no;
+      }
+    }
+    __syncwarp();
+  }
+  fz_teardown(&fs);
   if (threadIdx.x == 0 && abort_flag) atomicExch(&g_kernel_status, kStatusTimeout | (fail_where << 8));
 }
 
@@ -158,6 +206,7 @@ extern "C" uint64_t gvm_sgemm_scratch_bytes(int32_t m, int32_t n, int32_t k, int
 
 static bool fma_attr_set = false;
 static bool tc_attr_set = false;
+static bool fz_attr_set = false;
 
 extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m, int32_t n, int32_t k,
                              int32_t path, void* scratch, uint64_t scratch_bytes, void* stream) {
@@ -174,6 +223,21 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
     }
     dim3 grid((n + kFmaTile - 1) / kFmaTile, (m + kFmaTile - 1) / kFmaTile);
     fma_sgemm_kernel<<<grid, kThreads, smem, s>>>(A, B, C, m, n, k);
+    return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
+  }
+  if (path == GVM_SGEMM_SPLIT3_FUSED) {
+    const size_t smem = (size_t)kTcStages * kTcStageBytes + 1024;
+    if (!fz_attr_set) {
+      if (cudaFuncSetAttribute(fz_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+        return GVM_EDEVICE;
+      fz_attr_set = true;
+    }
+    const int sms = sm_count();
+    if (sms <= 0) return GVM_ENODEV;
+    const int64_t ntiles = (int64_t)((m + kTcM - 1) / kTcM) * ((n + kTcN - 1) / kTcN);
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    fz_sgemm_kernel<<<grid, kFzThreads, smem, s>>>(A, B, C, m, n, k, kStandaloneTimeoutNs);
     return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
   }
   if (path != GVM_SGEMM_SPLIT3) return GVM_EINVAL;

@@ -1,7 +1,7 @@
 """Kernel-level timings of the task kernels alone (no manager).
 
     python -m paper_1511_07658_gb300.kbench            # all
-    python -m paper_1511_07658_gb300.kbench 2048       # split3 SGEMM, one size
+    python -m paper_1511_07658_gb300.kbench 2048       # split3 SGEMM (both forms), one size
     python -m paper_1511_07658_gb300.kbench vadd       # vector add, 2^26 elements
     python -m paper_1511_07658_gb300.kbench link       # host-link copy rates
 
@@ -32,7 +32,7 @@ def _time(fn, reps=10):
     return e0.elapsed_time(e1) / reps / 1e3
 
 
-def sgemm(side: int, paths=("split3", "fma")) -> None:
+def sgemm(side: int, paths=("split3", "split3_fused", "fma")) -> None:
     A = torch.randn(side, side, device="cuda")
     B = torch.randn(side, side, device="cuda")
     C = torch.empty(side, side, device="cuda")
@@ -86,7 +86,7 @@ def main(argv) -> None:
     elif what == "link":
         link()
     elif what.isdigit():
-        sgemm(int(what), paths=("split3",))
+        sgemm(int(what), paths=("split3", "split3_fused"))
     else:
         for side in (512, 2048, 4096):
             sgemm(side)

@@ -19,6 +19,7 @@ from ._abi import (
     GVM_MODE_CONTINUOUS,
     GVM_SGEMM_FMA,
     GVM_SGEMM_SPLIT3,
+    GVM_SGEMM_SPLIT3_FUSED,
     GVM_TASK_RESIDENT,
     GVM_TASK_SGEMM,
     GVM_TASK_VADD,
@@ -29,7 +30,7 @@ from ._abi import (
     lib,
 )
 
-_PATHS = {"fma": GVM_SGEMM_FMA, "split3": GVM_SGEMM_SPLIT3}
+_PATHS = {"fma": GVM_SGEMM_FMA, "split3": GVM_SGEMM_SPLIT3, "split3_fused": GVM_SGEMM_SPLIT3_FUSED}
 _MODES = {"barrier": GVM_MODE_BARRIER, "continuous": GVM_MODE_CONTINUOUS}
 
 

@@ -85,7 +85,7 @@ def run_sgemm(gvm, A, B, path):
     return tC.cpu().numpy()
 
 
-@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_fused"])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_sgemm_normal_inputs(gvm, path, shape):
     m, n, k = shape
@@ -98,7 +98,7 @@ def test_sgemm_normal_inputs(gvm, path, shape):
     assert kernel_status() == 0
 
 
-@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_fused"])
 @pytest.mark.parametrize("shape", [(9, 11, 64), (130, 260, 100), (256, 256, 256)])
 def test_sgemm_integer_exact(gvm, path, shape):
     # |x| <= 16 and K <= 256: every product and partial sum is an integer
@@ -126,3 +126,24 @@ def test_fma_identity_exact(gvm):
     A, _ = synth.sgemm_inputs(78, 100, 60, 60)
     C = run_sgemm(gvm, A, np.eye(60, dtype=np.float32), "fma")
     assert np.array_equal(C, A)
+
+
+@pytest.mark.parametrize(
+    "shape",
+    [(128, 256, 32), (257, 130, 67), (512, 512, 512), (129, 257, 513), (300, 1001, 77),
+     (130, 260, 100), (1000, 520, 2052), (4096, 2048, 96), (2500, 3000, 40)],
+)
+def test_split3_fused_equals_prepass(gvm, shape):
+    # Same split rule, same products in the same order per 16-wide k slice,
+    # same tile shape: the fused staging must give the pre-pass result bit for
+    # bit. The large shapes give several tiles per CTA (both accumulators and
+    # the stage ring wrap), the odd ones ragged tiles and rows aligned to 4,
+    # 8 or 16 bytes only (each load width of the converters).
+    m, n, k = shape
+    A, B = synth.sgemm_inputs(synth.task_seed(7, m % 1000), m, n, k)
+    C1 = run_sgemm(gvm, A, B, "split3")
+    C2 = run_sgemm(gvm, A, B, "split3_fused")
+    assert np.array_equal(bits(C1), bits(C2)), shape
+    from paper_1511_07658_gb300.manager import kernel_status
+
+    assert kernel_status() == 0
