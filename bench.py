@@ -372,8 +372,8 @@ def gpu_arm(args, w, desc, rank, world):
     timeline = {
         "start_to_last_done_us": (st["launch_last_done_ns"] - st["launch_start_ns"]) / 1e3,
         "last_done_to_exit_us": (st["launch_exit_ns"] - st["launch_last_done_ns"]) / 1e3,
-        "cta_ms": {"acquire": ph[0] / 1e6, "ingest": ph[1] / 1e6, "split": ph[2] / 1e6, "gemm": ph[3] / 1e6,
-                   "gemm_split_wait": ph[4] / 1e6, "vadd": ph[5] / 1e6},
+        "cta_ms": {"acquire": ph[0] / 1e6, "ingest": ph[1] / 1e6, "stage_wait": ph[2] / 1e6, "gemm": ph[3] / 1e6,
+                   "mma_wait": ph[4] / 1e6, "vadd": ph[5] / 1e6},
         "tiles": ph[6],
         "ingest_passes": ph[7],
     }
@@ -445,8 +445,9 @@ def gpu_arm(args, w, desc, rank, world):
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "unit": "GB/s", "peak_basis": f"HBM copy {pk['hbm_gbs']} GB/s ({pk_kind})"}
         achieved = byts / kmean / 1e9
-    key = f"sched_kernel/{args.path}/{args.workload}"
-    roof.update({"kernel": f"gvm::sched_kernel<{args.path}>", "achieved": achieved, "peak": peak,
+    kname = "sched_fused_kernel" if args.path == "split3" else "sched_fma_kernel"
+    key = f"{kname}/{args.workload}"
+    roof.update({"kernel": f"gvm::{kname}", "achieved": achieved, "peak": peak,
                  "frac": achieved / peak, "traffic": ncu_traffic(key), "launch_ms": kmean * 1e3})
     clocks = sampler.summary()
     cfg = {

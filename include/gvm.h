@@ -65,10 +65,13 @@ extern "C" {
 /* ---- SGEMM arithmetic --------------------------------------------------- */
 #define GVM_SGEMM_FMA 0    /* binary32 fused multiply-add on the CUDA cores */
 #define GVM_SGEMM_SPLIT3 1 /* A = Ah + Al, B = Bh + Bl in bf16; C = AhBh + AhBl + AlBh on
-                              tcgen05 tensor cores with binary32 accumulation in TMEM */
-#define GVM_SGEMM_SPLIT3_FUSED 2 /* the same split3 arithmetic (bit-identical results), with
-                              the split done while operands are staged into shared memory:
-                              no pre-pass and no scratch. gvm_sgemm_f32 only */
+                              tcgen05 tensor cores with binary32 accumulation in TMEM.
+                              The manager splits while staging operands into shared
+                              memory (no scratch); gvm_sgemm_f32 runs a split pre-pass
+                              into caller scratch, then TMA-fed GEMM tiles */
+#define GVM_SGEMM_SPLIT3_FUSED 2 /* gvm_sgemm_f32 only: the manager's form of split3 (split
+                              during staging, no scratch); bit-identical to
+                              GVM_SGEMM_SPLIT3 */
 
 /* ---- manager modes ------------------------------------------------------ */
 #define GVM_MODE_BARRIER 0    /* Section 5 request barrier: gvm_flush runs the scheduler
@@ -93,7 +96,7 @@ typedef struct gvm_config {
   uint64_t arena_bytes;
   uint64_t resident_bytes; /* bytes at the start of each slice addressed by the offsets
                               of GVM_TASK_RESIDENT tasks; the rest of the slice is the
-                              rank's staging ring (copied inputs, outputs, scratch) */
+                              rank's staging ring (copied inputs and outputs) */
   void* ctrl;             /* caller-owned device memory for control words and the
                              device task table, >= gvm_ctrl_bytes(cfg), 256-aligned */
   uint64_t ctrl_bytes;

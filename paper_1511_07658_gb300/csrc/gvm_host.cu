@@ -6,7 +6,7 @@
 //   - a ring of task descriptors in pinned host memory, read by the
 //     scheduler kernel (the paper's request queue);
 //   - a slice of the caller's device arena: a resident region addressed by
-//     task offsets and a staging ring for copied operands and scratch (the
+//     task offsets and a staging ring for copied operands (the
 //     paper's per-process memory objects, so ranks never share buffers);
 //   - an input stream and an output stream (the paper's one stream per
 //     process): input copies then a ready word; a wait on the task's done
@@ -463,7 +463,7 @@ int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
   const bool split3 = ctx->path == kPathSplit3;
 
   // ---- shape and operand checks
-  uint64_t bytes_a = 0, bytes_b = 0, bytes_c = 0, bytes_s = 0;
+  uint64_t bytes_a = 0, bytes_b = 0, bytes_c = 0;
   if (t->type == GVM_TASK_VADD) {
     if (t->n < 0 || t->n > (int64_t(1) << 34)) return GVM_EINVAL;
     bytes_a = bytes_b = bytes_c = 4ull * (uint64_t)t->n;
@@ -472,7 +472,6 @@ int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
     bytes_a = 4ull * (uint64_t)t->m * (uint64_t)t->k;
     bytes_b = 4ull * (uint64_t)t->k * (uint64_t)t->n;
     bytes_c = 4ull * (uint64_t)t->m * (uint64_t)t->n;
-    if (split3) bytes_s = split_scratch_bytes(t->m, t->n, t->k);
   } else {
     return GVM_EINVAL;
   }
@@ -495,11 +494,11 @@ int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
   const uint64_t seq = r->next_seq;
   if (seq - r->synced >= D) return GVM_EAGAIN;
 
-  // ---- staging: copied operands (host mode) and split3 scratch
+  // ---- staging: copied operands (host mode)
   const uint64_t sa = resident ? 0 : align_up(bytes_a, 256);
   const uint64_t sb = resident ? 0 : align_up(bytes_b, 256);
   const uint64_t sc = resident ? 0 : align_up(bytes_c, 256);
-  const uint64_t need = sa + sb + sc + bytes_s;
+  const uint64_t need = sa + sb + sc;
   if (need > r->ring_bytes) return GVM_ENOMEM;
   const uint64_t cap = ctx->cfg.admission_cap_bytes;
   if (cap && need > cap) return GVM_ENOMEM;
@@ -554,22 +553,12 @@ int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
     body.k = t->k;
     body.n = t->n;
     if (split3) {
-      const uint64_t scr = base + sa + sb + sc;
+      // Fused split3 tiles (the bf16 split happens in the tile itself).
       body.flags |= kFlagSplit3;
-      body.kp = split_kp(t->k);
-      body.scratch = scr;
-      body.scratch_b = scr + split_a_bytes(t->m, t->k);
       body.tiles_m = (uint32_t)((t->m + kTcM - 1) / kTcM);
       body.tiles_n = (uint32_t)((t->n + kTcN - 1) / kTcN);
-      body.nsplit = (uint32_t)((t->m + kSplitRows - 1) / kSplitRows + (t->n + kSplitRows - 1) / kSplitRows);
-      body.ntiles = body.nsplit + body.tiles_m * body.tiles_n;
-      if (encode_split_maps(reinterpret_cast<void*>(scr), t->m, t->n, t->k, &body.tmA, &body.tmB) !=
-          CUDA_SUCCESS) {
-        r->ring_head -= held;  // undo the reservation (nothing was published)
-        ctx->staged.fetch_sub(held);
-        si.bytes = 0;
-        return GVM_EDEVICE;
-      }
+      body.nsplit = 0;
+      body.ntiles = body.tiles_m * body.tiles_n;
     } else {
       body.tiles_m = (uint32_t)((t->m + kFmaTile - 1) / kFmaTile);
       body.tiles_n = (uint32_t)((t->n + kFmaTile - 1) / kFmaTile);

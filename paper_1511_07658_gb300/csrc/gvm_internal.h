@@ -44,6 +44,8 @@ enum : uint32_t {
   kWhereEmptyBarrier = 4,
   kWhereAccumBarrier = 5,
   kWhereQueueFull = 6,
+  kWhereItemWait = 7,   // a warp waiting for its CTA's next claimed tile
+  kWhereItemRing = 8,   // the claiming warp waiting for a free item slot
 };
 
 constexpr uint32_t kClaimLocked = 0x40000000u;  // claim counter while a slot is rewritten
@@ -119,11 +121,11 @@ struct alignas(64) HostShared {
 
 // Per-launch phase counters (nanoseconds of CTA time summed over CTAs, and counts).
 enum : int {
-  kProfAcquire = 0,    // warp 0 finding the next tile (claims, ingest, idle polling)
+  kProfAcquire = 0,    // the claiming warp finding the next tile (claims, ingest, idle polling)
   kProfIngest = 1,     // inside ingest passes that published work
-  kProfSplit = 2,      // split3 pre-pass tiles
-  kProfGemm = 3,       // GEMM tiles (FMA or tensor core), waits included
-  kProfSplitWait = 4,  // GEMM producer waiting for its task's split pass
+  kProfStageWait = 2,  // split3: converters waiting for a free pipeline stage (MMA-bound time)
+  kProfGemm = 3,       // GEMM tiles (FMA; split3: converter time, staging + epilogue)
+  kProfMmaWait = 4,    // split3: the MMA warp waiting for a staged k-step (staging-bound time)
   kProfVadd = 5,       // vector-add tiles
   kProfTiles = 6,      // tiles run
   kProfIngests = 7,    // ingest passes that published work

@@ -31,12 +31,14 @@
 // idle_poll_ns between polls); in barrier (drain) mode it exits once every
 // descriptor published before its launch has been taken.
 #include "gvm_device.cuh"
+#include "gvm_fused.cuh"
 #include "gvm_runtime.h"
 
 namespace gvm {
 
-// Two tile slots: the CTA runs the tile in one while warp 0 claims the next
-// into the other. go: 1 = a tile is there, 0 = exit, 2 = nothing claimed yet.
+// FMA path: two tile slots; the CTA runs the tile in one while warp 0 claims
+// the next into the other. go: 1 = a tile is there, 0 = exit, 2 = nothing
+// claimed yet.
 struct alignas(128) SchedShared {
   TaskBody body[2];  // copies of the claimed tasks' bodies
   uint32_t go[2];
@@ -47,8 +49,7 @@ struct alignas(128) SchedShared {
   uint32_t abort;
   uint32_t fail_where;
   uint64_t prof[8];  // this CTA's phase counters (kProf*), written by thread 0 only
-  uint64_t claim[3];  // Claim state (see acquire), owned by warp 0
-  TcShared tc;
+  uint64_t claim[4];  // Claim state (see acquire), owned by warp 0
 };
 
 constexpr uint32_t kMaxQuantum = 8;
@@ -263,26 +264,32 @@ __device__ __forceinline__ uint64_t bcast64(uint64_t v) {
 struct Claim {
   uint64_t resv;     // reserved tile index
   uint64_t hint;     // queue entry to start the next search at
+  uint64_t stall_since;  // when published descriptors started waiting for their inputs (0: not waiting)
   uint32_t has_resv;
   uint32_t pad;
 };
 
-// Warp 0: find the next tile to run. Returns 1 with (task, phase, tile) set,
-// 0 when the kernel should exit, and (only when !blocking) 2 when the
-// reserved tile is not published yet. Decisions use values lane 0 read and
-// broadcast, so the warp never diverges across the shuffles.
+// One warp: find the next tile to run. Returns 1 with (task, phase, tile) set,
+// 0 when the kernel should exit, and 2 when the reserved tile is not
+// published yet and either !blocking or a blocking call has found nothing for
+// idle_return_ns (0: never). Decisions use values lane 0 read and broadcast,
+// so the warp never diverges across the shuffles.
 //
 // Claiming is one atomicAdd on next_tile per tile: there is no per-entry
 // counter for all CTAs to contend on. A tile beyond published_tiles is a
 // reservation; tiles are published in increasing order, so it becomes valid
 // without further claims.
 __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t& phase, uint32_t& tile,
-                       uint64_t* prof, bool blocking) {
+                       uint64_t* prof, bool blocking, uint64_t idle_return_ns = 0) {
   const int lane = threadIdx.x & 31;
-  uint64_t stall_since = 0;
+  uint64_t entered = 0;
+  auto set_stall = [&](uint64_t v) {
+    if (lane == 0) cl->stall_since = v;
+    __syncwarp();
+  };
   while (true) {
     uint32_t abort = 0, drained = 0;
-    uint64_t pt = 0, now = 0, quiet = 0, x = 0;
+    uint64_t pt = 0, npub = 0, now = 0, quiet = 0, x = 0;
     if (lane == 0) {
       abort = ld_relaxed_gpu(&p.ctrl->abort);
       drained = ld_acquire_gpu(&p.ctrl->drained);
@@ -292,13 +299,19 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
       }
       x = cl->resv;
       pt = ld_acquire_gpu64(&p.ctrl->published_tiles);
+      // Entries below `published` are complete: an ingest pass releases
+      // `published` (before published_tiles) only after writing them. An
+      // entry beyond it may be half written (new seq, old count).
+      npub = ld_acquire_gpu64(&p.ctrl->published);
       quiet = ld_relaxed_gpu64(&p.ctrl->quiet_until);
       now = globaltimer();
     }
     if (bcast(abort)) return 0;
     drained = bcast(drained);
+    if (entered == 0) entered = bcast64(now);
     x = bcast64(x);
     pt = bcast64(pt);
+    npub = bcast64(npub);
     now = bcast64(now);
     quiet = bcast64(quiet);
     if (x < pt) {
@@ -317,7 +330,7 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
         const PubEntry* pe = &p.pubq[e & (p.qcap - 1)];
         const uint64_t seq = ld_relaxed_gpu64(&pe->seq);
         const uint64_t base = ld_relaxed_gpu64(&pe->base);
-        const bool le = (seq == e) && base <= x;
+        const bool le = (e < npub) && (seq == e) && base <= x;
         const uint32_t m = __ballot_sync(0xffffffffu, le);
         if (m == 0) {  // not even the first entry starts at or before x
           ok = 0;
@@ -346,6 +359,7 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
             atomicMax(reinterpret_cast<unsigned long long*>(&p.ctrl->cursor), (unsigned long long)(ehit + 1));
           cl->hint = ehit;
           cl->has_resv = 0;
+          cl->stall_since = 0;
         }
         __syncwarp();
         break;
@@ -376,12 +390,12 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
     }
     const IngestOut r = ingest(p, prof);
     if (r.published) {
-      stall_since = 0;
+      set_stall(0);
       continue;
     }
     if (!r.locked_out) {
       if (r.pending == 0) {
-        stall_since = 0;
+        set_stall(0);
         if (p.drain) {
           if (lane == 0) atomicExch(&p.ctrl->drained, 1u);
           __syncwarp();
@@ -395,8 +409,13 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
           return 0;
         }
       } else if (blocking) {
-        if (stall_since == 0) stall_since = now;
-        else if (now - stall_since > p.wait_timeout_ns) {
+        uint64_t since = 0;
+        if (lane == 0) {
+          if (cl->stall_since == 0) cl->stall_since = now;
+          since = cl->stall_since;
+        }
+        since = bcast64(since);
+        if (now - since > p.wait_timeout_ns) {
           if (lane == 0) report_error(p, kStatusTimeout, kWhereReadyWait, r.pending);
           __syncwarp();
           return 0;
@@ -407,33 +426,75 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
     // on its current tile) must not wait: the current tile's completion is
     // published only after it returns. The reservation is kept.
     if (!blocking) return 2;
+    if (idle_return_ns != 0 && now - entered > idle_return_ns) return 2;
     __nanosleep(r.locked_out ? 200u : (uint32_t)p.idle_poll_ns);
   }
 }
 
-template <int PATH>
-__global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kernel(const SchedParams p) {
+// Kernel entry bookkeeping: the launch's start time is the earliest CTA's.
+__device__ void sched_enter(const SchedParams& p) {
+  const unsigned long long t0 = globaltimer();
+  unsigned long long* ts = reinterpret_cast<unsigned long long*>(&p.ctrl->t_start);
+  if (atomicCAS(ts, 0ull, t0) != 0ull) atomicMin(ts, t0);
+}
+
+// Thread 0 of a CTA that is done: adds its phase counters; the last CTA of the
+// launch publishes the launch's timeline and counters and resets the
+// per-launch words for the next launch.
+__device__ void sched_exit(const SchedParams& p, const uint64_t* prof) {
+  for (int i = 0; i < 8; ++i)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), (unsigned long long)prof[i]);
+  __threadfence();
+  const uint32_t n = atomicAdd(&p.ctrl->exit_count, 1u);
+  if (n + 1 != gridDim.x) return;
+  HostShared* hs = p.host_shared;
+  st_relaxed_sys64(&hs->k_start, atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->t_start), 0ull));
+  st_relaxed_sys64(&hs->k_last_done,
+                   atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->t_last_done), 0ull));
+  for (int i = 0; i < 8; ++i)
+    st_relaxed_sys64(&hs->k_prof[i], atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), 0ull));
+  st_relaxed_sys64(&hs->k_exit, globaltimer());
+  // Reservations beyond the published tiles died with their CTAs; the next
+  // launch hands out tiles of entries published from here on.
+  atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->next_tile),
+             (unsigned long long)ld_relaxed_gpu64(&p.ctrl->published_tiles));
+  atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->first_entry),
+             (unsigned long long)ld_relaxed_gpu64(&p.ctrl->published));
+  atomicExch(&p.ctrl->exit_count, 0u);
+  atomicExch(&p.ctrl->drained, 0u);
+  atomicExch(&p.ctrl->ingest_lock, 0u);
+  __threadfence_system();
+  st_release_sys(&p.host_shared->exit_gen, p.launch_gen);
+}
+
+// One tile of a task has finished (its results are visible device-wide):
+// count it, and complete the task after its last tile.
+__device__ void finish_tile(const SchedParams& p, uint32_t task, uint32_t ntiles, uint32_t tag, uint32_t flags) {
+  DevTask* dt = &p.tasks[task];
+  const uint32_t d = atomicAdd(&dt->tiles_done, 1u);
+  if (d + 1 == ntiles) {
+    __threadfence();
+    const uint64_t t_in = *reinterpret_cast<volatile uint64_t*>(&dt->t_ingest);
+    complete_task(p, task, tag, flags, t_in);
+  }
+}
+
+// ------------------------------------------------------------ FMA scheduler
+
+__global__ void __launch_bounds__(kThreads, 2) sched_fma_kernel(const SchedParams p) {
   __shared__ SchedShared sh;
   extern __shared__ uint8_t dyn_smem[];
-  uint8_t* big = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     sh.abort = 0;
     sh.fail_where = 0;
     for (int i = 0; i < 8; ++i) sh.prof[i] = 0;
-    const unsigned long long t0 = globaltimer();
-    unsigned long long* ts = reinterpret_cast<unsigned long long*>(&p.ctrl->t_start);
-    if (atomicCAS(ts, 0ull, t0) != 0ull) atomicMin(ts, t0);
-  }
-  uint32_t it = 0, tile_no = 0;
-  if constexpr (PATH == kPathSplit3) {
-    tc_init(&sh.tc);
-  } else {
-    __syncthreads();
+    sched_enter(p);
   }
   Claim* cl = reinterpret_cast<Claim*>(sh.claim);
   if (tid == 0) {
     cl->has_resv = 0;
+    cl->stall_since = 0;
     // Tiles handed out by this launch lie in entries published after it began
     // (a CTA may start after others of the launch have already published).
     cl->hint = ld_relaxed_gpu64(&p.ctrl->first_entry);
@@ -468,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
     const int nxt = cur ^ 1;
     const uint64_t t_tile = tid == 0 ? globaltimer() : 0;
     const TaskBody& b = sh.body[cur];
-    const uint32_t task = sh.task[cur], phase = sh.phase[cur], tile = sh.tile[cur];
+    const uint32_t task = sh.task[cur], tile = sh.tile[cur];
     int bucket = kProfVadd;
     bool early = false;  // warp 0 claims the next tile while this one runs
 
@@ -483,43 +544,10 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
       }
       early = true;
     } else {
-      const float* A = reinterpret_cast<const float*>(b.a);
-      const float* B = reinterpret_cast<const float*>(b.b);
-      float* C = reinterpret_cast<float*>(b.c);
-      if constexpr (PATH == kPathFma) {
-        bucket = kProfGemm;
-        const int tm = (int)(tile / b.tiles_n), tn = (int)(tile % b.tiles_n);
-        fma_tile(A, B, C, b.m, (int)b.n, b.k, tm, tn, reinterpret_cast<FmaSmem*>(big));
-      } else {
-        if (phase == kPhaseSplit) {
-          bucket = kProfSplit;
-          if (warp == 0) {
-            claim(nxt, false);
-          } else {
-            const uint32_t tiles_a = (uint32_t)((b.m + kSplitRows - 1) / kSplitRows);
-            if (tile < tiles_a) {
-              split_a_tile(A, reinterpret_cast<__nv_bfloat16*>(b.scratch), b.m, b.k, (int)b.kp,
-                           (int)(tile * kSplitRows), kSplitRows, tid - 32, kThreads - 32);
-            } else {
-              split_b_tile(B, reinterpret_cast<__nv_bfloat16*>(b.scratch_b), b.n, b.k, (int)b.kp,
-                           (int64_t)(tile - tiles_a) * kSplitRows, kSplitRows, tid - 32, kThreads - 32);
-            }
-            fence_proxy_async_global();
-          }
-          early = true;
-        } else {
-          bucket = kProfGemm;
-          const int tm = (int)(tile / b.tiles_n), tn = (int)(tile % b.tiles_n);
-          const DevTask* dt = &p.tasks[task];
-          tc_tile(&dt->body.tmA, &dt->body.tmB, C, b.m, b.n, b.k, tm, tn, big, &sh.tc, it, tile_no,
-                  p.wait_timeout_ns, b.nsplit ? &dt->split_done : nullptr, b.nsplit, &sh.abort,
-                  &sh.fail_where, true, &sh.prof[kProfSplitWait]);
-          // The producer has issued every load of this tile; it claims the
-          // next tile while the MMA and epilogue warps finish.
-          if (warp == 0) claim(nxt, false);
-          early = true;
-        }
-      }
+      bucket = kProfGemm;
+      const int tm = (int)(tile / b.tiles_n), tn = (int)(tile % b.tiles_n);
+      fma_tile(reinterpret_cast<const float*>(b.a), reinterpret_cast<const float*>(b.b),
+               reinterpret_cast<float*>(b.c), b.m, (int)b.n, b.k, tm, tn, reinterpret_cast<FmaSmem*>(dyn_smem));
     }
     // need[cur]: the look-ahead claim found nothing, so warp 0 must claim
     // (blocking) after this tile. Written before the barrier and not touched
@@ -538,14 +566,7 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
     if (tid == 0) {
       sh.prof[bucket] += globaltimer() - t_tile;
       sh.prof[kProfTiles] += 1;
-      DevTask* dt = &p.tasks[task];
-      if (phase == kPhaseSplit) atomicAdd(&dt->split_done, 1u);
-      const uint32_t d = atomicAdd(&dt->tiles_done, 1u);
-      if (d + 1 == b.ntiles) {
-        __threadfence();
-        const uint64_t t_in = *reinterpret_cast<volatile uint64_t*>(&dt->t_ingest);
-        complete_task(p, task, b.tag, b.flags, t_in);
-      }
+      finish_tile(p, task, b.ntiles, b.tag, b.flags);
     }
     if (sh.need[cur]) {
       // Nothing was claimable while the tile ran: wait for work now that its
@@ -555,51 +576,274 @@ __global__ void __launch_bounds__(kThreads, PATH == kPathFma ? 2 : 1) sched_kern
     }
     cur = nxt;
   }
+  __syncthreads();
+  if (tid == 0) sched_exit(p, sh.prof);
+}
 
-  if constexpr (PATH == kPathSplit3) {
-    tc_teardown(&sh.tc);
-  }
-  if (tid == 0) {
-    for (int i = 0; i < 8; ++i)
-      atomicAdd(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), (unsigned long long)sh.prof[i]);
-    __threadfence();
-    const uint32_t n = atomicAdd(&p.ctrl->exit_count, 1u);
-    if (n + 1 == gridDim.x) {
-      // Every CTA has left: publish this launch's timeline and phase
-      // counters, then reset the per-launch words for the next launch.
-      HostShared* hs = p.host_shared;
-      st_relaxed_sys64(&hs->k_start, atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->t_start), 0ull));
-      st_relaxed_sys64(&hs->k_last_done,
-                       atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->t_last_done), 0ull));
-      for (int i = 0; i < 8; ++i)
-        st_relaxed_sys64(&hs->k_prof[i], atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), 0ull));
-      st_relaxed_sys64(&hs->k_exit, globaltimer());
-      // Reservations beyond the published tiles died with their CTAs; the
-      // next launch hands out tiles of entries published from here on.
-      atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->next_tile),
-                 (unsigned long long)ld_relaxed_gpu64(&p.ctrl->published_tiles));
-      atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->first_entry),
-                 (unsigned long long)ld_relaxed_gpu64(&p.ctrl->published));
-      atomicExch(&p.ctrl->exit_count, 0u);
-      atomicExch(&p.ctrl->drained, 0u);
-      atomicExch(&p.ctrl->ingest_lock, 0u);
-      __threadfence_system();
-      st_release_sys(&p.host_shared->exit_gen, p.launch_gen);
+// ---------------------------------------------------------- split3 scheduler
+//
+// Roles (see gvm_fused.cuh): warp kFzCtlWarp claims tiles and passes them to
+// the other warps through a ring of kFzItems items in shared memory; the MMA
+// warp and the converter warps each walk the ring in order. GEMM tiles run
+// through the fused split3 pipeline (the epilogue of a tile overlaps the
+// MMAs of the next); vector-add tiles run on the converter warps. No warp
+// waits for another warp's tile to finish except through the pipeline's own
+// barriers, so the next tile's claim, staging and MMAs overlap this one's.
+
+constexpr int kFzItems = 4;
+constexpr uint32_t kItemExit = 0, kItemNop = 3;  // besides kTaskVadd, kTaskSgemm
+constexpr int kFinSlots = 16;  // per-item finish counters (items in flight < 16)
+
+struct FzItem {
+  uint32_t kind;  // kItemExit, kTaskVadd, kTaskSgemm or kItemNop
+  uint32_t task;
+  uint32_t tile;
+  uint32_t tag;
+  uint32_t flags;
+  uint32_t ntiles;
+  uint32_t tiles_n;
+  int32_t m;
+  int32_t k;
+  uint32_t pad;
+  int64_t n;
+  int64_t vadd_tile;
+  uint64_t a, b, c;
+};
+
+struct alignas(128) FusedShared {
+  FzShared fz;
+  uint64_t item_full[kFzItems];   // control -> consumers (1 arrival)
+  uint64_t item_empty[kFzItems];  // consumers -> control (converter warps + MMA warp)
+  FzItem items[kFzItems];
+  uint32_t fin[kFinSlots];        // converter warps done with item (seq % kFinSlots)
+  FzItem pend[kFzConvWarps][2];   // per converter warp: GEMM tiles by tile_no & 1 (staged, not yet drained)
+  uint32_t abort;
+  uint32_t fail_where;
+  uint64_t prof[8];   // kProf* counters; each slot written by one thread only
+  uint64_t claim[4];  // Claim state, owned by the control warp
+};
+
+// Records a failure seen by this CTA: the CTA flag stops its other warps'
+// waits, report_error stops the other CTAs and tells the host.
+__device__ void cta_fail(const SchedParams& p, FusedShared& sh, uint32_t where, uint32_t info) {
+  sh.fail_where = where;
+  sh.abort = 1;
+  report_error(p, kStatusTimeout, where, info);
+}
+
+// A converter warp has written its share of item `seq` (a vector-add range or
+// a drained accumulator). The last of the kFzConvWarps warps completes the
+// tile. Lanes fence their own stores before lane 0 counts the warp.
+__device__ void conv_item_done(const SchedParams& p, FusedShared& sh, uint32_t seq, uint32_t task,
+                               uint32_t ntiles, uint32_t tag, uint32_t flags) {
+  __threadfence();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    uint32_t* f = &sh.fin[seq % kFinSlots];
+    if (atomicAdd(f, 1u) == kFzConvWarps - 1) {
+      *f = 0;
+      __threadfence();
+      finish_tile(p, task, ntiles, tag, flags);
     }
   }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedParams p) {
+  __shared__ FusedShared sh;
+  extern __shared__ uint8_t dyn_smem[];
+  uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  Claim* cl = reinterpret_cast<Claim*>(sh.claim);
+  if (tid == 0) {
+    sh.abort = 0;
+    sh.fail_where = 0;
+    for (int i = 0; i < 8; ++i) sh.prof[i] = 0;
+    for (int i = 0; i < kFinSlots; ++i) sh.fin[i] = 0;
+    for (int i = 0; i < kFzItems; ++i) {
+      mbar_init(&sh.item_full[i], 1);
+      mbar_init(&sh.item_empty[i], kFzConvWarps + 1);
+    }
+    cl->has_resv = 0;
+    cl->stall_since = 0;
+    cl->hint = ld_relaxed_gpu64(&p.ctrl->first_entry);
+    sched_enter(p);
+  }
+  fz_init(&sh.fz);  // initialises the pipeline barriers, fences all inits, allocates TMEM
+
+  if (warp == kFzCtlWarp) {
+    // ---- control: claim tiles into the item ring.
+    for (uint32_t seq = 0;; ++seq) {
+      const uint32_t slot = seq % kFzItems, ph = (seq / kFzItems) & 1u;
+      uint32_t ok = 1;
+      if (lane == 0) ok = mbar_wait(&sh.item_empty[slot], ph ^ 1u, p.wait_timeout_ns, &sh.abort) ? 1u : 0u;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0 && !sh.abort) cta_fail(p, sh, kWhereItemRing, seq);
+        break;
+      }
+      const uint64_t t0 = globaltimer();
+      uint32_t task = 0, phase = 0, tile = 0;
+      // An idle control warp posts a no-op item now and then, so that the
+      // other warps' waits for items stay bounded.
+      const int got = sh.abort ? 0 : acquire(p, cl, task, phase, tile, sh.prof, true, p.wait_timeout_ns / 4);
+      if (lane == 0) {
+        FzItem& it = sh.items[slot];
+        it.kind = got == 1 ? 0u : (got == 2 ? kItemNop : kItemExit);
+        if (got == 1) {
+          const TaskBody* b = &p.tasks[task].body;
+          it.kind = __ldcg(&b->type);
+          it.task = task;
+          it.tile = tile;
+          it.tag = __ldcg(&b->tag);
+          it.flags = __ldcg(&b->flags);
+          it.ntiles = __ldcg(&b->ntiles);
+          it.tiles_n = __ldcg(&b->tiles_n);
+          it.m = __ldcg(&b->m);
+          it.k = __ldcg(&b->k);
+          it.n = __ldcg(&b->n);
+          it.vadd_tile = __ldcg(&b->vadd_tile);
+          it.a = __ldcg(&b->a);
+          it.b = __ldcg(&b->b);
+          it.c = __ldcg(&b->c);
+        }
+        sh.prof[kProfAcquire] += globaltimer() - t0;
+        mbar_arrive(&sh.item_full[slot]);
+      }
+      __syncwarp();
+      if (got == 0) break;
+    }
+  } else if (warp == kFzMmaWarp) {
+    // ---- MMA issue: GEMM items only; every item is read and released.
+    uint32_t it_k = 0, tile_no = 0;
+    for (uint32_t seq = 0;; ++seq) {
+      const uint32_t slot = seq % kFzItems, ph = (seq / kFzItems) & 1u;
+      if (!mbar_wait(&sh.item_full[slot], ph, p.wait_timeout_ns, &sh.abort)) {
+        if (lane == 0 && !sh.abort) cta_fail(p, sh, kWhereItemWait, seq);
+        break;
+      }
+      const FzItem& item = sh.items[slot];
+      const uint32_t kind = item.kind;
+      FzTile t{reinterpret_cast<const float*>(item.a), reinterpret_cast<const float*>(item.b),
+               reinterpret_cast<float*>(item.c), item.n, item.m, item.k, 0, 0};
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
+      if (kind == kItemExit) break;
+      if (kind != kTaskSgemm) continue;
+      uint32_t ok = 1;
+      if (lane == 0)
+        ok = fz_mma(t, stages, &sh.fz, it_k, tile_no, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+                    &sh.prof[kProfMmaWait])
+                 ? 1u
+                 : 0u;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0) report_error(p, kStatusTimeout, sh.fail_where, seq);
+        break;
+      }
+      it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
+      ++tile_no;
+    }
+  } else {
+    // ---- converters: stage GEMM tiles, drain the previous tile's
+    // accumulator after staging the next one, run vector-add tiles.
+    uint32_t it_k = 0, tile_no = 0;
+    bool have_prev = false;
+    // GEMM tile number i of this CTA is kept (by lane 0) in pend[warp][i & 1]
+    // until its accumulator is drained, out of the registers the staging
+    // loop needs.
+    auto tile_of = [](const FzItem& item) {
+      return FzTile{reinterpret_cast<const float*>(item.a), reinterpret_cast<const float*>(item.b),
+                    reinterpret_cast<float*>(item.c), item.n, item.m, item.k,
+                    (int)(item.tile / item.tiles_n), (int)(item.tile % item.tiles_n)};
+    };
+    auto drain_prev = [&]() -> bool {
+      const FzItem& prev = sh.pend[warp][(tile_no - 1) & 1u];
+      if (!fz_epilogue(tile_of(prev), &sh.fz, tile_no - 1, p.wait_timeout_ns, &sh.abort, &sh.fail_where))
+        return false;
+      conv_item_done(p, sh, prev.pad, prev.task, prev.ntiles, prev.tag, prev.flags);
+      have_prev = false;
+      return true;
+    };
+    for (uint32_t seq = 0;; ++seq) {
+      const uint32_t slot = seq % kFzItems, ph = (seq / kFzItems) & 1u;
+      if (!mbar_wait(&sh.item_full[slot], ph, p.wait_timeout_ns, &sh.abort)) {
+        if (lane == 0 && !sh.abort) cta_fail(p, sh, kWhereItemWait, seq);
+        break;
+      }
+      const FzItem& item = sh.items[slot];
+      const uint32_t kind = item.kind;
+      if (kind == kItemExit || kind == kItemNop) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
+        if (kind == kItemExit) break;
+        continue;
+      }
+      const uint64_t t0 = tid == 0 ? globaltimer() : 0;
+      bool ok = true;
+      if (kind == kTaskSgemm) {
+        const FzTile t = tile_of(item);
+        __syncwarp();
+        if (lane == 0) {
+          FzItem& keep = sh.pend[warp][tile_no & 1u];
+          keep = item;
+          keep.pad = seq;  // the item's sequence number names its finish counter
+          mbar_arrive(&sh.item_empty[slot]);
+        }
+        __syncwarp();
+        ok = fz_convert(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+                        tid == 0 ? &sh.prof[kProfStageWait] : nullptr);
+        it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
+        // The previous tile's accumulator is drained after this tile is staged.
+        if (ok && have_prev) ok = drain_prev();
+        have_prev = true;
+        ++tile_no;
+        if (tid == 0) sh.prof[kProfGemm] += globaltimer() - t0;
+      } else {
+        const uint32_t task = item.task, ntiles = item.ntiles, tag = item.tag, flags = item.flags;
+        const int64_t lo = (int64_t)item.tile * item.vadd_tile;
+        const int64_t hi = min(item.n, lo + item.vadd_tile);
+        const float* a = reinterpret_cast<const float*>(item.a);
+        const float* b = reinterpret_cast<const float*>(item.b);
+        float* c = reinterpret_cast<float*>(item.c);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
+        if (have_prev) ok = drain_prev();
+        if (ok) {
+          vadd_range(a, b, c, lo, hi, tid, kFzConvThreads);
+          conv_item_done(p, sh, seq, task, ntiles, tag, flags);
+        }
+        if (tid == 0) sh.prof[kProfVadd] += globaltimer() - t0;
+      }
+      if (tid == 0) sh.prof[kProfTiles] += 1;
+      if (!ok) {
+        if (lane == 0) report_error(p, kStatusTimeout, sh.fail_where, seq);
+        break;
+      }
+    }
+    if (have_prev && !sh.abort) {
+      if (!drain_prev() && lane == 0) report_error(p, kStatusTimeout, sh.fail_where, 0);
+    }
+  }
+  fz_teardown(&sh.fz);
+  if (tid == 0) sched_exit(p, sh.prof);
 }
 
 static size_t dyn_smem_bytes(int path) {
   return (path == kPathSplit3 ? (size_t)kTcStages * kTcStageBytes : sizeof(FmaSmem)) + 1024;
 }
 
+static const void* sched_fn(int path) {
+  return path == kPathSplit3 ? (const void*)sched_fused_kernel : (const void*)sched_fma_kernel;
+}
+
+static int sched_threads(int path) { return path == kPathSplit3 ? kFzThreads : kThreads; }
+
 cudaError_t scheduler_setup(int path, int* blocks_per_sm, size_t* smem_bytes) {
   const size_t smem = dyn_smem_bytes(path);
-  const void* fn = path == kPathSplit3 ? (const void*)sched_kernel<kPathSplit3> : (const void*)sched_kernel<kPathFma>;
+  const void* fn = sched_fn(path);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sched_threads(path), smem);
   if (e != cudaSuccess) return e;
   *blocks_per_sm = nb;
   *smem_bytes = smem;
@@ -608,9 +852,9 @@ cudaError_t scheduler_setup(int path, int* blocks_per_sm, size_t* smem_bytes) {
 
 cudaError_t launch_scheduler(int path, const SchedParams& p, int grid, size_t smem, cudaStream_t stream) {
   if (path == kPathSplit3) {
-    sched_kernel<kPathSplit3><<<grid, kThreads, smem, stream>>>(p);
+    sched_fused_kernel<<<grid, kFzThreads, smem, stream>>>(p);
   } else {
-    sched_kernel<kPathFma><<<grid, kThreads, smem, stream>>>(p);
+    sched_fma_kernel<<<grid, kThreads, smem, stream>>>(p);
   }
   return cudaGetLastError();
 }
