@@ -240,7 +240,9 @@ def run_step(mgr, ranks, arrays, pool, record=True):
         first, cnt = ranks[r].submit_many(arrays[r])
         return first + cnt - 1
 
+    h0 = time.perf_counter()
     lasts = list(pool.map(submit, range(len(ranks))))
+    h1 = time.perf_counter()
     ev0 = ev1 = None
     import torch
 
@@ -251,8 +253,14 @@ def run_step(mgr, ranks, arrays, pool, record=True):
     mgr.flush()
     if record:
         ev1.record(mgr.sched_stream)
+    h2 = time.perf_counter()
     list(pool.map(lambda r: ranks[r].sync(lasts[r]), range(len(ranks))))
+    h3 = time.perf_counter()
+    HOST_TIMES.append((h1 - h0, h2 - h1, h3 - h2))
     return ev0, ev1, lasts
+
+
+HOST_TIMES = []  # per step: (submit, flush, sync) host seconds
 
 
 def gpu_arm(args, w, desc, rank, world):
@@ -373,10 +381,17 @@ def gpu_arm(args, w, desc, rank, world):
         "start_to_last_done_us": (st["launch_last_done_ns"] - st["launch_start_ns"]) / 1e3,
         "last_done_to_exit_us": (st["launch_exit_ns"] - st["launch_last_done_ns"]) / 1e3,
         "cta_ms": {"acquire": ph[0] / 1e6, "ingest": ph[1] / 1e6, "stage_wait": ph[2] / 1e6, "gemm": ph[3] / 1e6,
-                   "mma_wait": ph[4] / 1e6, "vadd": ph[5] / 1e6},
+                   "mma_wait": ph[4] / 1e6, "vadd": ph[5] / 1e6, "epilogue": ph[8] / 1e6},
         "tiles": ph[6],
         "ingest_passes": ph[7],
     }
+    if HOST_TIMES:
+        last = HOST_TIMES[-args.steps:]
+        timeline["host_ms_per_step"] = {
+            "submit": 1e3 * statistics.mean(h[0] for h in last),
+            "flush": 1e3 * statistics.mean(h[1] for h in last),
+            "sync": 1e3 * statistics.mean(h[2] for h in last),
+        }
 
     # ---- end to end (host buffers, copies inside the timed region)
     e2e = None

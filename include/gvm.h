@@ -149,12 +149,15 @@ typedef struct gvm_stats {
   uint64_t launch_start_ns;     /* last scheduler launch that exited: first CTA start, */
   uint64_t launch_last_done_ns; /* its last task completion and its last CTA exit */
   uint64_t launch_exit_ns;      /* (device %globaltimer, ns; 0 before any exit) */
-  uint64_t launch_phase[8];     /* that launch's CTA time per phase, summed over CTAs (ns):
+  uint64_t launch_phase[12];    /* that launch's CTA time per phase, summed over CTAs (ns):
                                    [0] finding work (claims, ingest, idle polling),
-                                   [1] ingest passes that published work, [2] split3
-                                   pre-pass tiles, [3] GEMM tiles, [4] GEMM tiles waiting
-                                   for their split pass, [5] vector-add tiles; then counts:
-                                   [6] tiles run, [7] ingest passes that published work */
+                                   [1] ingest passes that published work, [2] split3:
+                                   staging warps waiting for a free stage, [3] GEMM tiles
+                                   (split3: staging warps' time incl. [8]), [4] split3: MMA
+                                   warp waiting for a staged k-step, [5] vector-add tiles;
+                                   counts: [6] tiles run, [7] ingest passes that published
+                                   work; [8] split3: draining accumulators into C;
+                                   [9..11] 0 */
 } gvm_stats;
 
 typedef struct gvm_ctx gvm_ctx;

@@ -81,7 +81,7 @@ class GvmStats(ctypes.Structure):
         ("launch_start_ns", c_uint64),
         ("launch_last_done_ns", c_uint64),
         ("launch_exit_ns", c_uint64),
-        ("launch_phase", c_uint64 * 8),
+        ("launch_phase", c_uint64 * 12),
     ]
 
 

@@ -211,29 +211,37 @@ __device__ __forceinline__ void fz_load_b(const FzTile& t, int kb, int w, int la
 // as an item is split and stored, its registers take the item's next load,
 // so a thread has its share of operands in flight nearly all the time
 // (the stage ring alone cannot cover the load latency at this rate).
-// Returns false when a wait ran out (*cta_abort set).
-__device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzShared* fs, uint32_t it,
-                                           uint64_t timeout_ns, volatile uint32_t* cta_abort,
-                                           uint32_t* fail_where, uint64_t* wait_acc) {
+// kFast: an interior tile, k a multiple of kTcBK and 32-byte aligned rows;
+// every item is one 32-byte load at a fixed offset from two per-thread bases.
+// Otherwise each load checks its bounds and picks the widest access the
+// alignment allows. Returns false when a wait ran out (*cta_abort set).
+template <bool kFast>
+__device__ __forceinline__ bool fz_convert_loop(const FzTile& t, uint32_t base, FzShared* fs, uint32_t it,
+                                                int avec, int bvec, uint64_t timeout_ns,
+                                                volatile uint32_t* cta_abort, uint32_t* fail_where,
+                                                uint64_t* wait_acc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int par = warp / kFzGroupWarps, w = warp % kFzGroupWarps;
   const int nkb = (t.k + kTcBK - 1) / kTcBK;
-  // Widest load every item of the tile allows: 2 = 32 bytes, 1 = 16 bytes, 0 = scalar.
-  const int avec = ((t.k & 7) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 31) == 0)   ? 2
-                   : ((t.k & 3) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 15) == 0) ? 1
-                                                                                      : 0;
-  const int bvec = ((t.n & 7) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 31) == 0)   ? 2
-                   : ((t.n & 3) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 15) == 0) ? 1
-                                                                                      : 0;
-  const uint32_t base = smem_u32(stages);
   // First k-step of this tile with the group's parity.
   const int kb0 = (int)((it + (uint32_t)par) & 1u);
   if (kb0 >= nkb) return true;
+  const float* pa = t.A + (int64_t)(t.tm * kTcM + 8 * w + (lane >> 2)) * t.k + 8 * (lane & 3);
+  const float* pb = t.B + (int64_t)(lane >> 2) * t.n + (int64_t)t.tn * kTcN + 64 * w + 8 * (lane & 3);
+  const int64_t a_row32 = 32 * (int64_t)t.k, b_row8 = 8 * t.n, b_step = (int64_t)kTcBK * t.n;
+  auto load_a = [&](int kb, int j, float (&v)[8]) {
+    if (kFast) ld_cg_v8(pa + kb * kTcBK + j * a_row32, v);
+    else fz_load_a(t, kb, w, lane, j, avec, v);
+  };
+  auto load_b = [&](int kb, int j, float (&v)[8]) {
+    if (kFast) ld_cg_v8(pb + kb * b_step + (j >> 1) * b_row8 + 32 * (j & 1), v);
+    else fz_load_b(t, kb, w, lane, j, bvec, v);
+  };
   float va[4][8], vb[8][8];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) fz_load_a(t, kb0, w, lane, j, avec, va[j]);
+  for (int j = 0; j < 4; ++j) load_a(kb0, j, va[j]);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) fz_load_b(t, kb0, w, lane, j, bvec, vb[j]);
+  for (int j = 0; j < 8; ++j) load_b(kb0, j, vb[j]);
   const uint32_t a_off = (uint32_t)(8 * w) * 64u + swz64((uint32_t)(lane >> 2), (uint32_t)(lane & 3));
   const uint32_t b_off = swz64((uint32_t)(lane >> 2), (uint32_t)(lane & 3));
   for (int kb = kb0; kb < nkb; kb += 2) {
@@ -259,7 +267,7 @@ __device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzS
       split8_x2(va[j], hi, lo);
       st_shared_v4(st + kTcAOff + off, hi);
       st_shared_v4(st + kTcAlOff + off, lo);
-      if (more) fz_load_a(t, kb + 2, w, lane, j, avec, va[j]);
+      if (more) load_a(kb + 2, j, va[j]);
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -268,7 +276,7 @@ __device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzS
       split8_x2(vb[j], hi, lo);
       st_shared_v4(st + kTcBOff + off, hi);
       st_shared_v4(st + kTcBlOff + off, lo);
-      if (more) fz_load_b(t, kb + 2, w, lane, j, bvec, vb[j]);
+      if (more) load_b(kb + 2, j, vb[j]);
     }
     fence_proxy_async_shared();
     __syncwarp();
@@ -277,10 +285,36 @@ __device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzS
   return true;
 }
 
+__device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzShared* fs, uint32_t it,
+                                           uint64_t timeout_ns, volatile uint32_t* cta_abort,
+                                           uint32_t* fail_where, uint64_t* wait_acc) {
+  // Widest load every item of the tile allows: 2 = 32 bytes, 1 = 16 bytes, 0 = scalar.
+  const int avec = ((t.k & 7) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 31) == 0)   ? 2
+                   : ((t.k & 3) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 15) == 0) ? 1
+                                                                                      : 0;
+  const int bvec = ((t.n & 7) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 31) == 0)   ? 2
+                   : ((t.n & 3) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 15) == 0) ? 1
+                                                                                      : 0;
+  const bool fast = avec == 2 && bvec == 2 && (t.k % kTcBK) == 0 && (t.tm + 1) * kTcM <= t.m &&
+                    (int64_t)(t.tn + 1) * kTcN <= t.n;
+  const uint32_t base = smem_u32(stages);
+  return fast ? fz_convert_loop<true>(t, base, fs, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc)
+              : fz_convert_loop<false>(t, base, fs, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc);
+}
+
+// 32-byte store of 8 floats; the address must be 32-byte aligned.
+__device__ __forceinline__ void st_v8(float* p, const uint32_t* r) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(r[0]), "r"(r[1]), "r"(r[2]),
+               "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+
 // Converter warps: drain accumulator (tile_no & 1) of tile t into C. Warp w
 // reads TMEM lanes 32 (w & 3) .. +31 (rows of the tile) and columns
-// 128 (w >> 2) .. +127; each thread stores one row's 32 consecutive floats per
-// chunk (8 x 16-byte stores when n allows). Then frees the accumulator.
+// 128 (w >> 2) .. +127, 32 columns at a time; TMEM hands each thread one
+// row, which it stores as whole 32-byte sectors (16-byte or single stores
+// when n does not allow). No shared memory: the operand loads keep all of L1
+// for their requests in flight. Then frees the accumulator.
 __device__ __forceinline__ bool fz_epilogue(const FzTile& t, FzShared* fs, uint32_t tile_no, uint64_t timeout_ns,
                                             volatile uint32_t* cta_abort, uint32_t* fail_where) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -295,7 +329,8 @@ __device__ __forceinline__ bool fz_epilogue(const FzTile& t, FzShared* fs, uint3
   tc_fence_after();
   const int q = warp & 3, cq = warp >> 2;
   const int row = t.tm * kTcM + q * 32 + lane;
-  const bool vec = ((t.n & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.C) & 15) == 0);
+  const uintptr_t ca = reinterpret_cast<uintptr_t>(t.C);
+  const int vec = ((t.n & 7) == 0 && (ca & 31) == 0) ? 2 : ((t.n & 3) == 0 && (ca & 15) == 0) ? 1 : 0;
 #pragma unroll 1
   for (int ch = 0; ch < 4; ++ch) {
     const int chunk = cq * 4 + ch;
@@ -305,11 +340,13 @@ __device__ __forceinline__ bool fz_epilogue(const FzTile& t, FzShared* fs, uint3
     const int64_t c0 = (int64_t)t.tn * kTcN + chunk * 32;
     if (row < t.m && c0 < t.n) {
       float* dst = t.C + (int64_t)row * t.n + c0;
-      if (vec && c0 + 32 <= t.n) {
+      if (vec == 2 && c0 + 32 <= t.n) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) st_v8(dst + 8 * j, r + 8 * j);
+      } else if (vec == 1 && c0 + 32 <= t.n) {
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          reinterpret_cast<float4*>(dst)[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                                          __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          reinterpret_cast<uint4*>(dst)[j] = make_uint4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j)

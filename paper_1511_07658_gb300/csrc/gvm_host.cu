@@ -816,7 +816,8 @@ int gvm_stats_get(gvm_ctx* ctx, gvm_stats* out) {
   out->launch_start_ns = __atomic_load_n(&ctx->shared->k_start, __ATOMIC_ACQUIRE);
   out->launch_last_done_ns = __atomic_load_n(&ctx->shared->k_last_done, __ATOMIC_ACQUIRE);
   out->launch_exit_ns = __atomic_load_n(&ctx->shared->k_exit, __ATOMIC_ACQUIRE);
-  for (int i = 0; i < 8; ++i) out->launch_phase[i] = __atomic_load_n(&ctx->shared->k_prof[i], __ATOMIC_ACQUIRE);
+  for (int i = 0; i < kProfSlots; ++i)
+    out->launch_phase[i] = __atomic_load_n(&ctx->shared->k_prof[i], __ATOMIC_ACQUIRE);
   return GVM_OK;
 }
 

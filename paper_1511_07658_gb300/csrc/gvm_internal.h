@@ -18,6 +18,7 @@ constexpr int kTcStages = 4;          // TMA -> MMA pipeline depth
 constexpr int kSplitRows = 128;       // rows of A (or columns of B) per split tile
 constexpr int64_t kVaddTileMin = 16384;
 constexpr int64_t kVaddTileMax = 1 << 20;
+constexpr int kProfSlots = 12;        // per-launch phase counters (see kProf*)
 
 // Bytes of one pipeline stage: A hi, A lo (kTcM x kTcBK) and B^T hi, lo (kTcN x kTcBK).
 constexpr uint32_t kTcStageBytes = (2u * kTcM + 2u * kTcN) * kTcBK * 2u;
@@ -116,7 +117,7 @@ struct alignas(64) HostShared {
   uint64_t k_start;      // first CTA started
   uint64_t k_last_done;  // last task completion
   uint64_t k_exit;       // last CTA left
-  uint64_t k_prof[8];    // per-phase CTA time summed over CTAs (kProf* order)
+  uint64_t k_prof[kProfSlots];  // per-phase CTA time summed over CTAs (kProf* order)
 };
 
 // Per-launch phase counters (nanoseconds of CTA time summed over CTAs, and counts).
@@ -129,6 +130,7 @@ enum : int {
   kProfVadd = 5,       // vector-add tiles
   kProfTiles = 6,      // tiles run
   kProfIngests = 7,    // ingest passes that published work
+  kProfEpilogue = 8,   // split3: converter time draining accumulators into C (part of kProfGemm)
 };
 
 // Device control block (front of the caller's ctrl buffer).
@@ -144,11 +146,11 @@ struct alignas(256) DevCtrl {
   uint64_t quiet_until;   // globaltimer before which look-ahead ingest is skipped
   uint64_t t_start;       // this launch: first CTA start (0 = unset)
   uint64_t t_last_done;   // this launch: last task completion
-  uint64_t prof[8];       // this launch: summed CTA time per phase (see kProf*)
+  uint64_t prof[kProfSlots];  // this launch: summed CTA time per phase (see kProf*)
   uint64_t published_tiles;  // tiles of all published entries (one global tile space)
   uint64_t next_tile;        // next tile index to hand out (may run ahead: a reservation)
   uint64_t first_entry;      // entries published before the current launch began
-  uint32_t pad[26];
+  uint32_t pad[18];
 };
 static_assert(sizeof(DevCtrl) == 256, "DevCtrl layout");
 

@@ -48,7 +48,7 @@ struct alignas(128) SchedShared {
   uint32_t need[2];  // per iteration parity: a blocking claim must follow the tile
   uint32_t abort;
   uint32_t fail_where;
-  uint64_t prof[8];  // this CTA's phase counters (kProf*), written by thread 0 only
+  uint64_t prof[kProfSlots];  // this CTA's phase counters (kProf*), written by thread 0 only
   uint64_t claim[4];  // Claim state (see acquire), owned by warp 0
 };
 
@@ -442,7 +442,7 @@ __device__ void sched_enter(const SchedParams& p) {
 // launch publishes the launch's timeline and counters and resets the
 // per-launch words for the next launch.
 __device__ void sched_exit(const SchedParams& p, const uint64_t* prof) {
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < kProfSlots; ++i)
     atomicAdd(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), (unsigned long long)prof[i]);
   __threadfence();
   const uint32_t n = atomicAdd(&p.ctrl->exit_count, 1u);
@@ -451,7 +451,7 @@ __device__ void sched_exit(const SchedParams& p, const uint64_t* prof) {
   st_relaxed_sys64(&hs->k_start, atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->t_start), 0ull));
   st_relaxed_sys64(&hs->k_last_done,
                    atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->t_last_done), 0ull));
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < kProfSlots; ++i)
     st_relaxed_sys64(&hs->k_prof[i], atomicExch(reinterpret_cast<unsigned long long*>(&p.ctrl->prof[i]), 0ull));
   st_relaxed_sys64(&hs->k_exit, globaltimer());
   // Reservations beyond the published tiles died with their CTAs; the next
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 2) sched_fma_kernel(const SchedParam
   if (tid == 0) {
     sh.abort = 0;
     sh.fail_where = 0;
-    for (int i = 0; i < 8; ++i) sh.prof[i] = 0;
+    for (int i = 0; i < kProfSlots; ++i) sh.prof[i] = 0;
     sched_enter(p);
   }
   Claim* cl = reinterpret_cast<Claim*>(sh.claim);
@@ -594,6 +594,14 @@ constexpr int kFzItems = 4;
 constexpr uint32_t kItemExit = 0, kItemNop = 3;  // besides kTaskVadd, kTaskSgemm
 constexpr int kFinSlots = 16;  // per-item finish counters (items in flight < 16)
 
+// A staged GEMM tile whose accumulator is not drained yet.
+struct FzPend {
+  uint64_t c;
+  int64_t n;
+  int32_t m;
+  uint32_t tile, tiles_n, task, ntiles, tag, flags, seq;
+};
+
 struct FzItem {
   uint32_t kind;  // kItemExit, kTaskVadd, kTaskSgemm or kItemNop
   uint32_t task;
@@ -616,10 +624,10 @@ struct alignas(128) FusedShared {
   uint64_t item_empty[kFzItems];  // consumers -> control (converter warps + MMA warp)
   FzItem items[kFzItems];
   uint32_t fin[kFinSlots];        // converter warps done with item (seq % kFinSlots)
-  FzItem pend[kFzConvWarps][2];   // per converter warp: GEMM tiles by tile_no & 1 (staged, not yet drained)
+  FzPend pend[kFzConvWarps][3];   // per converter warp: GEMM tiles by tile number % 3 (staged, not yet counted)
   uint32_t abort;
   uint32_t fail_where;
-  uint64_t prof[8];   // kProf* counters; each slot written by one thread only
+  uint64_t prof[kProfSlots];  // kProf* counters; each slot written by one thread only
   uint64_t claim[4];  // Claim state, owned by the control warp
 };
 
@@ -658,7 +666,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
   if (tid == 0) {
     sh.abort = 0;
     sh.fail_where = 0;
-    for (int i = 0; i < 8; ++i) sh.prof[i] = 0;
+    for (int i = 0; i < kProfSlots; ++i) sh.prof[i] = 0;
     for (int i = 0; i < kFinSlots; ++i) sh.fin[i] = 0;
     for (int i = 0; i < kFzItems; ++i) {
       mbar_init(&sh.item_full[i], 1);
@@ -743,30 +751,58 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
       ++tile_no;
     }
   } else {
-    // ---- converters: stage GEMM tiles, drain the previous tile's
-    // accumulator after staging the next one, run vector-add tiles.
+    // ---- converters: stage GEMM tiles; after staging tile T, count tile
+    // T-2 as finished (its stores were issued a tile ago, so the fence that
+    // orders them before the count hardly waits) and drain tile T-1's
+    // accumulator into C. Vector-add tiles, no-op items, the exit and an
+    // empty item ring flush both steps first, so that no completion waits
+    // for later work.
     uint32_t it_k = 0, tile_no = 0;
-    bool have_prev = false;
-    // GEMM tile number i of this CTA is kept (by lane 0) in pend[warp][i & 1]
-    // until its accumulator is drained, out of the registers the staging
-    // loop needs.
+    bool has_drain = false, has_done = false;  // tile tile_no-1 to drain; tile done_no to count
+    uint32_t done_no = 0;
+    // GEMM tile number i of this CTA is kept (by lane 0) in pend[warp][i % 3]
+    // until it is counted, out of the registers the staging loop needs.
     auto tile_of = [](const FzItem& item) {
       return FzTile{reinterpret_cast<const float*>(item.a), reinterpret_cast<const float*>(item.b),
                     reinterpret_cast<float*>(item.c), item.n, item.m, item.k,
                     (int)(item.tile / item.tiles_n), (int)(item.tile % item.tiles_n)};
     };
-    auto drain_prev = [&]() -> bool {
-      const FzItem& prev = sh.pend[warp][(tile_no - 1) & 1u];
-      if (!fz_epilogue(tile_of(prev), &sh.fz, tile_no - 1, p.wait_timeout_ns, &sh.abort, &sh.fail_where))
-        return false;
-      conv_item_done(p, sh, prev.pad, prev.task, prev.ntiles, prev.tag, prev.flags);
-      have_prev = false;
+    auto count_done = [&]() {
+      if (!has_done) return;
+      const FzPend& d = sh.pend[warp][done_no % 3u];
+      conv_item_done(p, sh, d.seq, d.task, d.ntiles, d.tag, d.flags);
+      has_done = false;
+    };
+    auto drain = [&]() -> bool {
+      if (!has_drain) return true;
+      const uint64_t t0 = tid == 0 ? globaltimer() : 0;
+      const uint32_t no = tile_no - 1;
+      const FzPend& d = sh.pend[warp][no % 3u];
+      const FzTile pt{nullptr, nullptr, reinterpret_cast<float*>(d.c), d.n, d.m, 0, (int)(d.tile / d.tiles_n),
+                      (int)(d.tile % d.tiles_n)};
+      if (!fz_epilogue(pt, &sh.fz, no, p.wait_timeout_ns, &sh.abort, &sh.fail_where)) return false;
+      has_drain = false;
+      has_done = true;
+      done_no = no;
+      if (tid == 0) sh.prof[kProfEpilogue] += globaltimer() - t0;
       return true;
     };
+    auto flush = [&]() -> bool {
+      count_done();
+      if (!drain()) return false;
+      count_done();
+      return true;
+    };
+    bool ok = true;
     for (uint32_t seq = 0;; ++seq) {
       const uint32_t slot = seq % kFzItems, ph = (seq / kFzItems) & 1u;
+      if ((has_drain || has_done) && !mbar_try_wait(&sh.item_full[slot], ph)) {
+        ok = flush();  // nothing queued: finish what is pending before waiting
+        if (!ok) break;
+      }
       if (!mbar_wait(&sh.item_full[slot], ph, p.wait_timeout_ns, &sh.abort)) {
         if (lane == 0 && !sh.abort) cta_fail(p, sh, kWhereItemWait, seq);
+        ok = false;
         break;
       }
       const FzItem& item = sh.items[slot];
@@ -775,26 +811,29 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
         if (kind == kItemExit) break;
+        ok = flush();
+        if (!ok) break;
         continue;
       }
       const uint64_t t0 = tid == 0 ? globaltimer() : 0;
-      bool ok = true;
       if (kind == kTaskSgemm) {
         const FzTile t = tile_of(item);
         __syncwarp();
         if (lane == 0) {
-          FzItem& keep = sh.pend[warp][tile_no & 1u];
-          keep = item;
-          keep.pad = seq;  // the item's sequence number names its finish counter
+          // The item's sequence number names its finish counter.
+          sh.pend[warp][tile_no % 3u] = FzPend{item.c, item.n, item.m, item.tile, item.tiles_n,
+                                               item.task, item.ntiles, item.tag, item.flags, seq};
           mbar_arrive(&sh.item_empty[slot]);
         }
         __syncwarp();
         ok = fz_convert(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
                         tid == 0 ? &sh.prof[kProfStageWait] : nullptr);
         it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
-        // The previous tile's accumulator is drained after this tile is staged.
-        if (ok && have_prev) ok = drain_prev();
-        have_prev = true;
+        if (ok) {
+          count_done();
+          ok = drain();
+        }
+        has_drain = true;
         ++tile_no;
         if (tid == 0) sh.prof[kProfGemm] += globaltimer() - t0;
       } else {
@@ -806,7 +845,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
         float* c = reinterpret_cast<float*>(item.c);
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
-        if (have_prev) ok = drain_prev();
+        ok = flush();
         if (ok) {
           vadd_range(a, b, c, lo, hi, tid, kFzConvThreads);
           conv_item_done(p, sh, seq, task, ntiles, tag, flags);
@@ -814,14 +853,10 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
         if (tid == 0) sh.prof[kProfVadd] += globaltimer() - t0;
       }
       if (tid == 0) sh.prof[kProfTiles] += 1;
-      if (!ok) {
-        if (lane == 0) report_error(p, kStatusTimeout, sh.fail_where, seq);
-        break;
-      }
+      if (!ok) break;
     }
-    if (have_prev && !sh.abort) {
-      if (!drain_prev() && lane == 0) report_error(p, kStatusTimeout, sh.fail_where, 0);
-    }
+    if (ok && !sh.abort) ok = flush();
+    if (!ok && lane == 0) report_error(p, kStatusTimeout, sh.fail_where, 0);
   }
   fz_teardown(&sh.fz);
   if (tid == 0) sched_exit(p, sh.prof);
