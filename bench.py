@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--plain", action="store_true", help="also time the plain one-context-per-rank form")
     p.add_argument("--model", action="store_true", help="also check timings against Eqs. 1, 2 and 7")
     p.add_argument("--quantum", type=int, default=8)
+    p.add_argument("--harness", choices=["native", "python"], default="native",
+                   help="rank threads: native (gvm_spmd_run) or Python threads calling the API")
     p.add_argument("--ranks", type=int, default=0, help="smaller case for profiling (not a bench line)")
     p.add_argument("--per-rank", type=int, default=0, help="smaller case for profiling (not a bench line)")
     return p.parse_args()
@@ -325,8 +327,28 @@ def gpu_arm(args, w, desc, rank, world):
         if not cont:
             torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        run_step(mgr, ranks, res_arrays, pool, record=not cont)
+    native = args.harness == "native"
+
+    def native_steps(arrays, steps):
+        # One native thread per rank (gvm_spmd_run). The resident scheduler of
+        # continuous mode holds the scheduler stream, so no events there.
+        if cont:
+            n = len(ranks)
+            hs = (ctypes.c_void_p * n)(*[r.handle for r in ranks])
+            tp = (ctypes.POINTER(g.GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(g.GvmTask)) for a in arrays])
+            cnt = (ctypes.c_uint32 * n)(*[len(a) for a in arrays])
+            host = (ctypes.c_double * max(steps, 1))()
+            rc = g._abi.lib().gvm_spmd_run(mgr.handle, hs, tp, cnt, n, steps, None, None, host)
+            g._abi.check(rc, "gvm_spmd_run")
+            return [h / 1e3 for h in list(host)[:steps]], [h / 1e3 for h in list(host)[:steps]]
+        dev, launch, _ = mgr.spmd_run(ranks, arrays, steps)
+        return [d / 1e3 for d in dev], [x / 1e3 for x in launch]
+
+    if native:
+        native_steps(res_arrays, args.warmup)
+    else:
+        for _ in range(args.warmup):
+            run_step(mgr, ranks, res_arrays, pool, record=not cont)
     device_sync()
     if world > 1:
         torch.distributed.barrier()
@@ -334,7 +356,22 @@ def gpu_arm(args, w, desc, rank, world):
     t_step = []
     t_kernel = []
     wall0 = time.perf_counter()
-    if not cont:
+    if native:
+        if not cont:
+            st0 = torch.cuda.Event(enable_timing=True)
+            st1 = torch.cuda.Event(enable_timing=True)
+            st0.record(mgr.sched_stream)
+        t_step, t_kernel = native_steps(res_arrays, args.steps)
+        # Sequence numbers are per rank, from 0: warm-up steps, then timed ones.
+        lasts = [(args.warmup + args.steps) * len(res_arrays[r]) - 1 for r in range(R)]
+        if not cont:
+            st1.record(mgr.sched_stream)
+            torch.cuda.synchronize()
+            total_s = st0.elapsed_time(st1) / 1e3
+        else:
+            total_s = time.perf_counter() - wall0
+        wall = time.perf_counter() - wall0
+    elif not cont:
         st0 = torch.cuda.Event(enable_timing=True)
         st1 = torch.cuda.Event(enable_timing=True)
         st0.record(mgr.sched_stream)
@@ -396,15 +433,21 @@ def gpu_arm(args, w, desc, rank, world):
     # ---- end to end (host buffers, copies inside the timed region)
     e2e = None
     if not args.skip_e2e:
-        for _ in range(max(1, args.warmup)):
-            run_step(mgr, ranks, host_arrays, pool, record=not cont)
+        if native:
+            native_steps(host_arrays, max(1, args.warmup))
+        else:
+            for _ in range(max(1, args.warmup)):
+                run_step(mgr, ranks, host_arrays, pool, record=not cont)
         device_sync()
         if world > 1:
             torch.distributed.barrier()
         e_steps = max(3, args.steps // 2)
         h0 = time.perf_counter()
-        for _ in range(e_steps):
-            run_step(mgr, ranks, host_arrays, pool, record=not cont)
+        if native:
+            native_steps(host_arrays, e_steps)
+        else:
+            for _ in range(e_steps):
+                run_step(mgr, ranks, host_arrays, pool, record=not cont)
         h_s = time.perf_counter() - h0
         if world > 1:
             t = torch.tensor([h_s], device="cuda")
@@ -474,7 +517,8 @@ def gpu_arm(args, w, desc, rank, world):
         "operands": "resident in HBM for value; pinned host buffers for e2e",
         "l2": "inputs larger than L2 (2 GiB of operands per step)" if args.workload == "sgemm512"
         else "inputs smaller than L2; latency-bound",
-        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU, 16 SPMD ranks as host threads",
+        "parallelism": f"replicas x{world}" if world > 1 else f"1 GPU, {R} SPMD ranks as host threads",
+        "rank_threads": "native (gvm_spmd_run)" if args.harness == "native" else "Python threads",
     }
     out = {
         "metric": METRIC,

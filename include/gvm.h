@@ -253,6 +253,26 @@ GVM_API int gvm_stats_get(gvm_ctx* ctx, gvm_stats* out);
    once the task is complete and until its ring slot is reused. */
 GVM_API int gvm_task_times(gvm_rank* rank, uint64_t seq, uint64_t* t_ingest_ns, uint64_t* t_done_ns);
 
+/* ---- SPMD harness --------------------------------------------------------
+   Runs `steps` steps of the paper's SPMD pattern (Section 6: every process
+   issues its task, the manager runs them together, every process collects its
+   result) with one native thread per rank, so that a benchmark measures the
+   manager rather than an interpreter's threads. ranks[r] must be attached;
+   tasks[r][0 .. counts[r]-1] is rank r's batch, submitted in order every step
+   (counts[r] <= ring_depth). A step: all threads submit their batches
+   (gvm_submit_many, waiting out GVM_EAGAIN), meet, thread 0 calls gvm_flush
+   (barrier mode), each thread syncs its last task, all meet again. In barrier
+   mode a batch must fit the rank's ring and staging space at once. Timing
+   (each array may be NULL): step_ms_device[i] is CUDA-event time on the
+   scheduler stream from before the first submit of step i to after its last
+   sync; launch_ms_device[i] the same around step i's gvm_flush (its
+   scheduler launch; 0 in continuous mode); step_ms_host[i] the step on the
+   host clock. Returns GVM_OK or the first error any rank saw (the remaining
+   steps are skipped). */
+GVM_API int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks,
+                         const uint32_t* counts, int32_t nranks, int32_t steps, float* step_ms_device,
+                         float* launch_ms_device, double* step_ms_host);
+
 GVM_API const char* gvm_strerror(int code);
 
 /* ---- the task kernels alone -------------------------------------------- */

@@ -4,7 +4,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
-from ctypes import POINTER, c_char_p, c_int, c_int32, c_int64, c_uint32, c_uint64, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int32, c_int64, c_uint32, c_uint64, c_void_p
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 _DEFAULT_LIB = os.path.join(HERE, "_build", "libgvm.so")
@@ -111,6 +111,11 @@ PROTOTYPES = {
     "gvm_shutdown": (c_int, [c_void_p]),
     "gvm_stats_get": (c_int, [c_void_p, POINTER(GvmStats)]),
     "gvm_task_times": (c_int, [c_void_p, c_uint64, POINTER(c_uint64), POINTER(c_uint64)]),
+    "gvm_spmd_run": (
+        c_int,
+        [c_void_p, POINTER(c_void_p), POINTER(POINTER(GvmTask)), POINTER(c_uint32), c_int32, c_int32,
+         POINTER(c_float), POINTER(c_float), POINTER(c_double)],
+    ),
     "gvm_strerror": (c_char_p, [c_int]),
     "gvm_vadd_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "gvm_sgemm_scratch_bytes": (c_uint64, [c_int32, c_int32, c_int32, c_int32]),

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgvm.so")
-SOURCES = ["gvm_host.cu", "gvm_sched.cu", "gvm_kernels.cu", "gvm_noalloc.cu"]
+SOURCES = ["gvm_host.cu", "gvm_sched.cu", "gvm_kernels.cu", "gvm_noalloc.cu", "gvm_spmd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = [
     "-O3",

@@ -60,6 +60,7 @@ bool debug_on() {
   } while (0)
 
 // gvm_sync gives the device this long beyond its own wait limit to report.
+constexpr uint64_t kStreamQueryNs = 2000000;  // gvm_sync: driver status check period (2 ms)
 constexpr uint64_t kHostGraceNs = 1000ull * 1000 * 1000;
 
 inline uint64_t now_ns() {
@@ -645,7 +646,7 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
   bind_device(ctx);
   if (push_flushed(r) != GVM_OK) return GVM_EDEVICE;
   uint64_t last = r->synced;
-  uint64_t t_prog = now_ns();
+  uint64_t t_prog = now_ns(), t_query = t_prog;
   uint32_t spins = 0;
   while (true) {
     reap(r);
@@ -658,9 +659,15 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
     } else if (now - t_prog > ctx->cfg.wait_timeout_ns + kHostGraceNs) {
       return GVM_ETIMEDOUT;
     }
-    if ((++spins & 63) == 0) {
+    // A kernel that died without writing its status word shows up in the
+    // stream's state; ask the driver rarely (every rank may be waiting here,
+    // and driver calls from many threads serialise).
+    if (now - t_query > kStreamQueryNs) {
+      t_query = now;
       cudaError_t e = cudaStreamQuery(ctx->sched);
       if (e != cudaSuccess && e != cudaErrorNotReady) return GVM_EDEVICE;
+    }
+    if ((++spins & 63) == 0) {
       g.unlock();
       std::this_thread::yield();
       g.lock();

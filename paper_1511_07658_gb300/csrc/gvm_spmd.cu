@@ -1,0 +1,155 @@
+// Native SPMD harness (gvm_spmd_run): one thread per rank runs the paper's
+// per-process loop -- submit the task, wait at the request barrier, collect
+// the result (Section 6) -- through the public API only, so that measured
+// step times contain the manager's work and not an interpreter's.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <thread>
+#include <vector>
+
+#include "gvm.h"
+
+namespace {
+
+// Reusable barrier for a fixed number of threads (generation counting; waits
+// yield so that more threads than cores still make progress).
+class SpinBarrier {
+ public:
+  explicit SpinBarrier(int n) : n_(n) {}
+  void wait() {
+    const uint32_t gen = gen_.load(std::memory_order_acquire);
+    if (count_.fetch_add(1, std::memory_order_acq_rel) + 1 == n_) {
+      count_.store(0, std::memory_order_relaxed);
+      gen_.fetch_add(1, std::memory_order_acq_rel);
+      return;
+    }
+    uint32_t spins = 0;
+    while (gen_.load(std::memory_order_acquire) == gen) {
+      if (++spins > 64) std::this_thread::yield();
+    }
+  }
+
+ private:
+  const int n_;
+  std::atomic<int> count_{0};
+  std::atomic<uint32_t> gen_{0};
+};
+
+// Submits the whole batch, syncing the rank's oldest outstanding task when
+// the ring or the staging space is full. Returns the last sequence number
+// through *last.
+int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* last) {
+  uint32_t done = 0;
+  uint64_t first_of_step = 0;
+  bool have_first = false;
+  while (done < count) {
+    uint64_t first = 0;
+    const int rc = gvm_submit_many(r, tasks + done, count - done, &first);
+    if (rc < 0) return rc;
+    if (rc > 0) {
+      if (!have_first) {
+        first_of_step = first;
+        have_first = true;
+      }
+      done += (uint32_t)rc;
+      *last = first + (uint64_t)rc - 1;
+      continue;
+    }
+    // Nothing admitted: the ring is full of this step's earlier tasks.
+    if (!have_first) return GVM_EAGAIN;
+    const int s = gvm_sync(r, first_of_step);
+    if (s != GVM_OK) return s;
+    ++first_of_step;
+  }
+  return GVM_OK;
+}
+
+}  // namespace
+
+extern "C" int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks,
+                            const uint32_t* counts, int32_t nranks, int32_t steps, float* step_ms_device,
+                            float* launch_ms_device, double* step_ms_host) {
+  if (!ctx || !ranks || !tasks || !counts || nranks <= 0 || steps < 0) return GVM_EINVAL;
+  for (int r = 0; r < nranks; ++r)
+    if (!ranks[r] || (counts[r] && !tasks[r])) return GVM_EINVAL;
+  cudaStream_t sched = static_cast<cudaStream_t>(gvm_stream(ctx, -1));
+  int dev = 0;
+  if (!sched || cudaGetDevice(&dev) != cudaSuccess) return GVM_EINVAL;
+  // Events per step: step start, step end, before and after the flush.
+  std::vector<cudaEvent_t> ev;
+  if (step_ms_device || launch_ms_device) {
+    ev.resize(4 * (size_t)steps);
+    for (auto& e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        for (auto& x : ev)
+          if (x) cudaEventDestroy(x);
+        return GVM_EDEVICE;
+      }
+  }
+  SpinBarrier bar(nranks);
+  std::atomic<int> err{GVM_OK};
+  std::vector<std::chrono::steady_clock::time_point> t0(steps), t1(steps);
+  auto body = [&](int r) {
+    cudaSetDevice(dev);
+    for (int i = 0; i < steps; ++i) {
+      if (r == 0) {
+        t0[i] = std::chrono::steady_clock::now();
+        if (!ev.empty() && cudaEventRecord(ev[4 * i], sched) != cudaSuccess) err.store(GVM_EDEVICE);
+      }
+      bar.wait();
+      uint64_t last = 0;
+      int rc = err.load() == GVM_OK && counts[r] ? submit_batch(ranks[r], tasks[r], counts[r], &last) : GVM_OK;
+      if (rc != GVM_OK) {
+        int ok = GVM_OK;
+        err.compare_exchange_strong(ok, rc);
+      }
+      bar.wait();
+      if (r == 0 && err.load() == GVM_OK) {
+        if (!ev.empty()) cudaEventRecord(ev[4 * i + 2], sched);
+        rc = gvm_flush(ctx);
+        if (!ev.empty()) cudaEventRecord(ev[4 * i + 3], sched);
+        if (rc != GVM_OK) {
+          int ok = GVM_OK;
+          err.compare_exchange_strong(ok, rc);
+        }
+      }
+      bar.wait();
+      if (err.load() == GVM_OK && counts[r]) {
+        rc = gvm_sync(ranks[r], last);
+        if (rc != GVM_OK) {
+          int ok = GVM_OK;
+          err.compare_exchange_strong(ok, rc);
+        }
+      }
+      bar.wait();
+      if (r == 0) {
+        if (!ev.empty() && cudaEventRecord(ev[4 * i + 1], sched) != cudaSuccess) err.store(GVM_EDEVICE);
+        t1[i] = std::chrono::steady_clock::now();
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  th.reserve(nranks - 1);
+  for (int r = 1; r < nranks; ++r) th.emplace_back(body, r);
+  body(0);
+  for (auto& t : th) t.join();
+  int rc = err.load();
+  if (!ev.empty()) {
+    if (rc == GVM_OK && steps > 0 && cudaEventSynchronize(ev[4 * (steps - 1) + 1]) != cudaSuccess)
+      rc = GVM_EDEVICE;
+    for (int i = 0; rc == GVM_OK && i < steps; ++i) {
+      if (step_ms_device && cudaEventElapsedTime(&step_ms_device[i], ev[4 * i], ev[4 * i + 1]) != cudaSuccess)
+        rc = GVM_EDEVICE;
+      if (launch_ms_device &&
+          cudaEventElapsedTime(&launch_ms_device[i], ev[4 * i + 2], ev[4 * i + 3]) != cudaSuccess)
+        rc = GVM_EDEVICE;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  if (step_ms_host)
+    for (int i = 0; i < steps; ++i)
+      step_ms_host[i] = std::chrono::duration<double, std::milli>(t1[i] - t0[i]).count();
+  return rc;
+}

@@ -282,6 +282,22 @@ class Manager:
         out["launch_phase"] = list(s.launch_phase)
         return out
 
+    def spmd_run(self, ranks, task_arrays, steps: int) -> tuple[list[float], list[float], list[float]]:
+        """Runs ``steps`` SPMD steps natively (gvm_spmd_run): one thread per
+        rank submits ``task_arrays[i]`` (a ctypes array of GvmTask) for
+        ``ranks[i]``, then flush and sync. Returns per-step times in ms:
+        (step, scheduler launch) by CUDA events on the scheduler stream, and
+        the step on the host clock."""
+        n = len(ranks)
+        hs = (c_void_p * n)(*[r.handle for r in ranks])
+        tp = (ctypes.POINTER(GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(GvmTask)) for a in task_arrays])
+        cnt = (c_uint32 * n)(*[len(a) for a in task_arrays])
+        dev = (ctypes.c_float * max(steps, 1))()
+        launch = (ctypes.c_float * max(steps, 1))()
+        host = (ctypes.c_double * max(steps, 1))()
+        check(lib().gvm_spmd_run(self.handle, hs, tp, cnt, n, steps, dev, launch, host), "gvm_spmd_run")
+        return list(dev)[:steps], list(launch)[:steps], list(host)[:steps]
+
     def shutdown(self) -> None:
         if self.handle is not None:
             rc = lib().gvm_shutdown(self.handle)
