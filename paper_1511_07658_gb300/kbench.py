@@ -76,6 +76,37 @@ def link() -> None:
     print(f"H2D 4 x 64 MiB on 4 streams: {n / t / 1e9:.1f} GB/s", flush=True)
     t = _time(lambda: fan(True))
     print(f"H2D + D2H 2 + 2 x 64 MiB: {n / t / 1e9:.1f} GB/s total", flush=True)
+    # Many small copies, as the manager issues them: 16 streams (one per rank),
+    # each copying 64 chunks; H2D alone, then with D2H of half the bytes on 16
+    # more streams.
+    for chunk in (1 << 20, 4 << 20):
+        nch = 64
+        hb = torch.empty(16 * nch * chunk, dtype=torch.uint8).pin_memory()
+        db = torch.empty(16 * nch * chunk, dtype=torch.uint8, device="cuda")
+        ho = torch.empty(16 * nch * chunk // 2, dtype=torch.uint8).pin_memory()
+        do = torch.empty(16 * nch * chunk // 2, dtype=torch.uint8, device="cuda")
+        sin = [torch.cuda.Stream() for _ in range(16)]
+        sout = [torch.cuda.Stream() for _ in range(16)]
+
+        def many(duplex: bool):
+            for r in range(16):
+                with torch.cuda.stream(sin[r]):
+                    for i in range(nch):
+                        o = (r * nch + i) * chunk
+                        db[o:o + chunk].copy_(hb[o:o + chunk], non_blocking=True)
+                if duplex:
+                    with torch.cuda.stream(sout[r]):
+                        for i in range(nch // 2):
+                            o = (r * nch // 2 + i) * chunk
+                            ho[o:o + chunk].copy_(do[o:o + chunk], non_blocking=True)
+            for st in sin + (sout if duplex else []):
+                torch.cuda.current_stream().wait_stream(st)
+
+        byts = 16 * nch * chunk
+        t = _time(lambda: many(False), reps=3)
+        print(f"H2D 16 streams x 64 x {chunk >> 20} MiB: {byts / t / 1e9:.1f} GB/s", flush=True)
+        t = _time(lambda: many(True), reps=3)
+        print(f"H2D + D2H 16+16 streams, {chunk >> 20} MiB chunks: {1.5 * byts / t / 1e9:.1f} GB/s total", flush=True)
 
 
 def main(argv) -> None:

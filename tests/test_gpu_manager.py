@@ -248,3 +248,56 @@ def test_order_and_times(gvm):
                     t0, t1 = rk.task_times(seq)
                     assert 0 < t0 <= t1
                     check_result(spec, inputs, out)
+
+
+@pytest.mark.parametrize("mode", ["barrier", "continuous"])
+def test_spmd_harness_steps(gvm, mode):
+    # gvm_spmd_run: one native thread per rank submits its batch each step,
+    # flush (barrier mode), sync. Every step's results must be the oracle's;
+    # the last step's outputs are checked (each step rewrites them), and the
+    # per-step times must be positive.
+    w = synth.Workload(name="spmd", ranks=4, tasks=[
+        synth.TaskSpec(rank=r, index=i, kind=synth.TASK_VADD if i % 2 == 0 else synth.TASK_SGEMM,
+                       seed=synth.task_seed(r, i), n=65536 + 257 * r if i % 2 == 0 else 300,
+                       m=0 if i % 2 == 0 else 130 + r, k=0 if i % 2 == 0 else 96)
+        for r in range(4) for i in range(6)])
+    with gvm.Manager(w.ranks, ring_depth=8, mode=mode, sgemm_path="split3", slice_bytes=64 << 20) as mgr:
+        ranks = [mgr.attach(r) for r in range(w.ranks)]
+        arrays = [(gvm.GvmTask * 6)() for _ in range(w.ranks)]
+        keep = []
+        for spec in w.tasks:
+            t = arrays[spec.rank][spec.index]
+            if spec.kind == synth.TASK_VADD:
+                a, b = synth.vadd_inputs(spec.seed, spec.n)
+                ins = (pinned(a), pinned(b))
+                out = torch.empty(spec.n, dtype=torch.float32).pin_memory()
+                t.type, t.n = gvm.GVM_TASK_VADD, spec.n
+                ref = (a, b)
+            else:
+                A, B = synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
+                ins = (pinned(A), pinned(B))
+                out = torch.empty(spec.m, spec.n, dtype=torch.float32).pin_memory()
+                t.type, t.m, t.n, t.k = gvm.GVM_TASK_SGEMM, spec.m, spec.n, spec.k
+                ref = (A, B)
+            t.flags = 0
+            t.a, t.b, t.c = ins[0].data_ptr(), ins[1].data_ptr(), out.data_ptr()
+            keep.append((spec, ins, out, ref))
+        if mode == "barrier":
+            dev, launch, host = mgr.spmd_run(ranks, arrays, 3)
+            assert all(x > 0 for x in dev) and all(x > 0 for x in launch)
+            assert all(l <= d for l, d in zip(launch, dev))
+        else:
+            n = len(ranks)
+            import ctypes
+
+            hs = (ctypes.c_void_p * n)(*[r.handle for r in ranks])
+            tp = (ctypes.POINTER(gvm.GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(gvm.GvmTask)) for a in arrays])
+            cnt = (ctypes.c_uint32 * n)(*[6] * n)
+            host = (ctypes.c_double * 3)()
+            rc = gvm._abi.lib().gvm_spmd_run(mgr.handle, hs, tp, cnt, n, 3, None, None, host)
+            assert rc == 0, rc
+            host = list(host)
+        assert all(x > 0 for x in host)
+        for spec, _, out, ref in keep:
+            check_result(spec, ref, out)
+        assert mgr.stats()["device_status"] == 0
