@@ -289,25 +289,45 @@ def gpu_arm(args, w, desc, rank, world):
         res_need[spec.rank] = off + (la + lb + lc + 255) // 256 * 256
         sizes[(spec.rank, spec.index)] = (la, lb, lc)
     resident = max(res_need)
-    scratch = 0
-    if args.path == "split3":
-        scratch = sum(g.sgemm_scratch_bytes(s.m, s.n, s.k) for s in w.tasks if s.kind == synth.TASK_SGEMM) // R
     host_stage = max(sum(sizes[(s.rank, s.index)]) for s in w.tasks) * per_rank
-    slice_bytes = resident + max(scratch, 1 << 20) + host_stage + (64 << 20)
+    slice_bytes = resident + host_stage + (64 << 20)
     slice_bytes = (slice_bytes + (1 << 20) - 1) // (1 << 20) * (1 << 20)
     mgr = g.Manager(
         R, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode=args.mode, sgemm_path=args.path,
         slice_bytes=slice_bytes, resident_bytes=resident, ingest_quantum=args.quantum,
     )
     ranks = [mgr.attach(r) for r in range(R)]
-    # place resident operands
+    # Host buffers: per rank, one pinned block holding every task's A then B
+    # in submission order and one holding the outputs, each operand at a
+    # 256-byte multiple (as a rank of an SPMD program would keep its batch);
+    # the manager merges copies that are adjacent on both sides.
+    def al256(x):
+        return (x + 255) // 256 * 256
+
+    in_off, out_off = {}, {}
+    in_need, out_need = [0] * R, [0] * R
+    for spec in w.tasks:
+        la, lb, lc = sizes[(spec.rank, spec.index)]
+        in_off[(spec.rank, spec.index)] = in_need[spec.rank]
+        in_need[spec.rank] += al256(la) + al256(lb)
+        out_off[(spec.rank, spec.index)] = out_need[spec.rank]
+        out_need[spec.rank] += al256(lc)
+    in_blocks = [torch.empty(max(n, 256), dtype=torch.uint8).pin_memory() for n in in_need]
+    out_blocks = [torch.empty(max(n, 256), dtype=torch.uint8).pin_memory() for n in out_need]
+
+    def view(block, off, nbytes):
+        return block[off:off + nbytes].view(torch.float32)
+
     host = {}
     for spec, inp in zip(w.tasks, inputs):
         a, b = inp
-        ta = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        tb = torch.from_numpy(np.ascontiguousarray(b)).pin_memory()
         la, lb, lc = sizes[(spec.rank, spec.index)]
-        tc = torch.empty(lc // 4, dtype=torch.float32).pin_memory()
+        io = in_off[(spec.rank, spec.index)]
+        ta = view(in_blocks[spec.rank], io, la)
+        tb = view(in_blocks[spec.rank], io + al256(la), lb)
+        ta.copy_(torch.from_numpy(np.ascontiguousarray(a)).reshape(-1))
+        tb.copy_(torch.from_numpy(np.ascontiguousarray(b)).reshape(-1))
+        tc = view(out_blocks[spec.rank], out_off[(spec.rank, spec.index)], lc)
         host[(spec.rank, spec.index)] = (ta, tb, tc)
         oa, ob, _ = res_offs[(spec.rank, spec.index)]
         ranks[spec.rank].write(oa, ta)

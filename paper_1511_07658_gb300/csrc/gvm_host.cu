@@ -61,6 +61,11 @@ bool debug_on() {
 
 // gvm_sync gives the device this long beyond its own wait limit to report.
 constexpr uint64_t kStreamQueryNs = 2000000;  // gvm_sync: driver status check period (2 ms)
+// Copies of one batch are merged when both sides are adjacent, up to this
+// many bytes per copy: the link serves 1 MiB copies at less than half its
+// rate, while a few MiB per copy still lets the scheduler start on the first
+// tasks while later inputs are in flight.
+constexpr uint64_t kMaxCopyRun = 16ull << 20;
 constexpr uint64_t kHostGraceNs = 1000ull * 1000 * 1000;
 
 inline uint64_t now_ns() {
@@ -176,56 +181,89 @@ void reap(gvm_rank* r) {
   }
 }
 
-// Reserve `bytes` (a multiple of 256) in the rank's staging ring. Returns the
-// device address, 0 when there is no room right now. *held gets the bytes
-// charged (including any space skipped at the ring's end).
-uint64_t stage_alloc(gvm_rank* r, uint64_t bytes, uint64_t* held) {
-  if (bytes == 0) {
-    *held = 0;
-    return 0;
+// A copy between a host buffer (src) and staging (dst) still to issue, or a
+// run of adjacent ones.
+struct CopyRun {
+  uint64_t dst;
+  const uint8_t* src;
+  uint64_t bytes;
+  uint32_t first_piece, pieces;  // the operand copies it merges
+};
+
+// Issues one merged copy. Host buffers that are adjacent may still be
+// separate page-locked allocations, which one copy may not span (the call
+// fails with cudaErrorInvalidValue and enqueues nothing): then the run's
+// operand copies are issued one by one.
+cudaError_t issue_run(const CopyRun& run, const std::vector<CopyRun>& pieces, cudaMemcpyKind kind,
+                      cudaStream_t st) {
+  void* dst = kind == cudaMemcpyHostToDevice ? reinterpret_cast<void*>(run.dst) : const_cast<uint8_t*>(run.src);
+  const void* src = kind == cudaMemcpyHostToDevice ? static_cast<const void*>(run.src)
+                                                   : reinterpret_cast<const void*>(run.dst);
+  cudaError_t e = cudaMemcpyAsync(dst, src, run.bytes, kind, st);
+  if (e != cudaErrorInvalidValue || run.pieces < 2) return e;
+  (void)cudaGetLastError();
+  for (uint32_t i = 0; i < run.pieces; ++i) {
+    const CopyRun& p = pieces[run.first_piece + i];
+    void* d = kind == cudaMemcpyHostToDevice ? reinterpret_cast<void*>(p.dst) : const_cast<uint8_t*>(p.src);
+    const void* s = kind == cudaMemcpyHostToDevice ? static_cast<const void*>(p.src)
+                                                   : reinterpret_cast<const void*>(p.dst);
+    e = cudaMemcpyAsync(d, s, p.bytes, kind, st);
+    if (e != cudaSuccess) return e;
   }
-  uint64_t pos = r->ring_head;
-  const uint64_t off = pos % r->ring_bytes;
-  uint64_t waste = 0;
-  if (off + bytes > r->ring_bytes) waste = r->ring_bytes - off;
-  if (pos + waste + bytes - r->ring_tail > r->ring_bytes) return 0;
-  pos += waste;
-  r->ring_head = pos + bytes;
-  *held = waste + bytes;
-  return r->ring_base + (pos % r->ring_bytes);
+  return cudaSuccess;
 }
 
-// Pushes the output operations (wait on done, device-to-host copy, completion
-// word) of tasks out_pushed .. upto-1 on the rank's output stream. Called only
-// once the scheduler launch that will write those done words has been pushed:
-// a blocked wait can then never sit ahead of its own producer in a hardware
-// queue that two streams share.
+// Pushes the output operations of tasks out_pushed .. upto-1 on the rank's
+// output stream: a wait on each task's done word, the device-to-host copy of
+// its output, its completion word. Outputs adjacent on both sides (a batch's
+// outputs are packed in staging; adjacent host buffers are the caller's
+// choice) share one copy of up to kMaxCopyRun bytes after all their waits.
+// Called only once the scheduler launch that will write those done words has
+// been pushed: a blocked wait can then never sit ahead of its own producer in
+// a hardware queue that two streams share.
 int push_out_ops(gvm_rank* r, uint64_t upto) {
   gvm_ctx* ctx = r->ctx;
   const DriverApi* api = driver_api();
   const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
+  CUstream os = reinterpret_cast<CUstream>(r->out_stream);
   while (r->out_pushed < upto) {
-    const uint64_t s = r->out_pushed;
-    SlotInfo& si = r->slots[s & (D - 1)];
-    if (si.needs_out) {
-      const uint32_t idx = (uint32_t)r->id * D + (uint32_t)(s & (D - 1));
-      const uint32_t tag = tag_of(s);
-      CUresult cr = api->wait_value32(reinterpret_cast<CUstream>(r->out_stream),
-                                      reinterpret_cast<CUdeviceptr>(ctx->params.done + idx), tag,
-                                      CU_STREAM_WAIT_VALUE_EQ);
-      cudaError_t e = cudaSuccess;
-      if (cr == CUDA_SUCCESS && si.c_bytes)
-        e = cudaMemcpyAsync(si.c_host, reinterpret_cast<void*>(si.c_dev), si.c_bytes, cudaMemcpyDeviceToHost,
-                            r->out_stream);
-      if (cr == CUDA_SUCCESS && e == cudaSuccess)
-        cr = api->write_value32(reinterpret_cast<CUstream>(r->out_stream),
-                                reinterpret_cast<CUdeviceptr>(&ctx->params.host_complete[idx].tag), tag,
-                                CU_STREAM_WRITE_VALUE_DEFAULT);
-      if (cr != CUDA_SUCCESS || e != cudaSuccess) return GVM_EDEVICE;
-      ctx->d2h.fetch_add(si.c_bytes);
-      si.needs_out = false;
+    const uint64_t s0 = r->out_pushed;
+    SlotInfo& first = r->slots[s0 & (D - 1)];
+    if (!first.needs_out) {
+      r->out_pushed = s0 + 1;
+      continue;
     }
-    r->out_pushed = s + 1;
+    // The run: s0 .. s1-1, outputs adjacent in device and host memory.
+    std::vector<CopyRun> pieces;
+    pieces.push_back(CopyRun{first.c_dev, static_cast<const uint8_t*>(first.c_host), first.c_bytes, 0, 1});
+    uint64_t s1 = s0 + 1, bytes = first.c_bytes;
+    while (s1 < upto) {
+      const SlotInfo& nx = r->slots[s1 & (D - 1)];
+      if (!nx.needs_out || nx.c_dev != first.c_dev + bytes ||
+          static_cast<const uint8_t*>(nx.c_host) != static_cast<const uint8_t*>(first.c_host) + bytes ||
+          bytes + nx.c_bytes > kMaxCopyRun)
+        break;
+      pieces.push_back(CopyRun{nx.c_dev, static_cast<const uint8_t*>(nx.c_host), nx.c_bytes, 0, 1});
+      bytes += nx.c_bytes;
+      ++s1;
+    }
+    const CopyRun run{first.c_dev, static_cast<const uint8_t*>(first.c_host), bytes, 0, (uint32_t)pieces.size()};
+    for (uint64_t s = s0; s < s1; ++s) {
+      const uint32_t idx = (uint32_t)r->id * D + (uint32_t)(s & (D - 1));
+      if (api->wait_value32(os, reinterpret_cast<CUdeviceptr>(ctx->params.done + idx), tag_of(s),
+                            CU_STREAM_WAIT_VALUE_EQ) != CUDA_SUCCESS)
+        return GVM_EDEVICE;
+    }
+    if (bytes && issue_run(run, pieces, cudaMemcpyDeviceToHost, r->out_stream) != cudaSuccess) return GVM_EDEVICE;
+    for (uint64_t s = s0; s < s1; ++s) {
+      const uint32_t idx = (uint32_t)r->id * D + (uint32_t)(s & (D - 1));
+      if (api->write_value32(os, reinterpret_cast<CUdeviceptr>(&ctx->params.host_complete[idx].tag), tag_of(s),
+                             CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
+        return GVM_EDEVICE;
+      r->slots[s & (D - 1)].needs_out = false;
+    }
+    ctx->d2h.fetch_add(bytes);
+    r->out_pushed = s1;
   }
   return GVM_OK;
 }
@@ -453,17 +491,22 @@ int gvm_attach(gvm_ctx* ctx, int32_t rank, gvm_rank** out) {
   return GVM_OK;
 }
 
-int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
-  if (!r || !t) return GVM_EINVAL;
-  gvm_ctx* ctx = r->ctx;
-  std::lock_guard<std::mutex> g(r->mu);
-  if (!r->attached || ctx->shut) return GVM_ESTATE;
-  bind_device(ctx);
+}  // extern "C"
+
+namespace {
+
+// One validated task of a batch.
+struct Prep {
+  const gvm_task* t;
+  bool resident;
+  uint64_t bytes_a, bytes_b, bytes_c;  // operand bytes
+  uint64_t sa, sb, sc;                 // staging bytes (256-aligned; 0 when resident)
+};
+
+// Shape, offset and pointer checks of one task (nothing is reserved).
+int prep_task(gvm_rank* r, const gvm_task* t, Prep* p) {
   const bool resident = (t->flags & GVM_TASK_RESIDENT) != 0;
   if (t->flags & ~GVM_TASK_RESIDENT) return GVM_EINVAL;
-  const bool split3 = ctx->path == kPathSplit3;
-
-  // ---- shape and operand checks
   uint64_t bytes_a = 0, bytes_b = 0, bytes_c = 0;
   if (t->type == GVM_TASK_VADD) {
     if (t->n < 0 || t->n > (int64_t(1) << 34)) return GVM_EINVAL;
@@ -489,134 +532,276 @@ int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
     if (!t->a || !t->b || !t->c) return GVM_EINVAL;
     if (!is_pinned(t->a) || !is_pinned(t->b) || !is_pinned(t->c)) return GVM_EINVAL;
   }
+  p->t = t;
+  p->resident = resident;
+  p->bytes_a = bytes_a;
+  p->bytes_b = bytes_b;
+  p->bytes_c = bytes_c;
+  p->sa = resident ? 0 : align_up(bytes_a, 256);
+  p->sb = resident ? 0 : align_up(bytes_b, 256);
+  p->sc = resident ? 0 : align_up(bytes_c, 256);
+  return GVM_OK;
+}
 
+// Staging bytes the ring would charge for `bytes` now (incl. the waste at the
+// ring's end), or 0 when it has no room.
+uint64_t stage_room(const gvm_rank* r, uint64_t bytes) {
+  const uint64_t pos = r->ring_head, off = pos % r->ring_bytes;
+  const uint64_t waste = off + bytes > r->ring_bytes ? r->ring_bytes - off : 0;
+  if (pos + waste + bytes - r->ring_tail > r->ring_bytes) return 0;
+  return waste + bytes;
+}
+
+void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t da, uint64_t db, uint64_t dc,
+               TaskBody* body) {
+  const gvm_task* t = p.t;
   const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
-  reap(r);
-  const uint64_t seq = r->next_seq;
-  if (seq - r->synced >= D) return GVM_EAGAIN;
-
-  // ---- staging: copied operands (host mode)
-  const uint64_t sa = resident ? 0 : align_up(bytes_a, 256);
-  const uint64_t sb = resident ? 0 : align_up(bytes_b, 256);
-  const uint64_t sc = resident ? 0 : align_up(bytes_c, 256);
-  const uint64_t need = sa + sb + sc;
-  if (need > r->ring_bytes) return GVM_ENOMEM;
-  const uint64_t cap = ctx->cfg.admission_cap_bytes;
-  if (cap && need > cap) return GVM_ENOMEM;
-  if (cap && ctx->staged.load() + need > cap) return GVM_EAGAIN;
-  uint64_t held = 0, base = 0;
-  if (need) {
-    base = stage_alloc(r, need, &held);
-    if (!base) return GVM_EAGAIN;
-  }
-  const uint64_t st = ctx->staged.fetch_add(held) + held;
-  uint64_t pk = ctx->staged_peak.load();
-  while (st > pk && !ctx->staged_peak.compare_exchange_weak(pk, st)) {
-  }
-  SlotInfo& si = r->slots[seq & (D - 1)];
-  si.bytes = held;
-  si.stage_end = r->ring_head;
-
-  // ---- descriptor
-  const uint32_t slot = (uint32_t)(seq & (D - 1));
-  const uint32_t idx = (uint32_t)r->id * D + slot;
-  const uint32_t tag = tag_of(seq);
-  TaskBody body;
-  memset(&body, 0, sizeof(body));
-  body.type = (uint32_t)t->type;
-  body.rank = (uint32_t)r->id;
-  body.slot = slot;
-  body.tag = tag;
-  body.flags = resident ? 0u : (kFlagNeedsReady | kFlagNeedsD2H);
-  uint64_t da, db, dcp;
-  if (resident) {
-    da = r->slice + t->a_off;
-    db = r->slice + t->b_off;
-    dcp = r->slice + t->c_off;
-  } else {
-    da = base;
-    db = base + sa;
-    dcp = base + sa + sb;
-  }
-  body.a = da;
-  body.b = db;
-  body.c = dcp;
+  memset(body, 0, sizeof(*body));
+  body->type = (uint32_t)t->type;
+  body->rank = (uint32_t)r->id;
+  body->slot = (uint32_t)(seq & (D - 1));
+  body->tag = tag_of(seq);
+  body->flags = p.resident ? 0u : (kFlagNeedsReady | kFlagNeedsD2H);
+  body->a = da;
+  body->b = db;
+  body->c = dc;
   if (t->type == GVM_TASK_VADD) {
-    body.n = t->n;
+    body->n = t->n;
     int64_t vt = (t->n + ctx->grid - 1) / std::max(ctx->grid, 1);
     vt = (vt + 4095) / 4096 * 4096;
     vt = std::min<int64_t>(std::max<int64_t>(vt, kVaddTileMin), kVaddTileMax);
-    body.vadd_tile = vt;
-    body.ntiles = (uint32_t)((t->n + vt - 1) / vt);
-    body.nsplit = 0;
+    body->vadd_tile = vt;
+    body->ntiles = (uint32_t)((t->n + vt - 1) / vt);
   } else {
-    body.m = t->m;
-    body.k = t->k;
-    body.n = t->n;
-    if (split3) {
-      // Fused split3 tiles (the bf16 split happens in the tile itself).
-      body.flags |= kFlagSplit3;
-      body.tiles_m = (uint32_t)((t->m + kTcM - 1) / kTcM);
-      body.tiles_n = (uint32_t)((t->n + kTcN - 1) / kTcN);
-      body.nsplit = 0;
-      body.ntiles = body.tiles_m * body.tiles_n;
-    } else {
-      body.tiles_m = (uint32_t)((t->m + kFmaTile - 1) / kFmaTile);
-      body.tiles_n = (uint32_t)((t->n + kFmaTile - 1) / kFmaTile);
-      body.nsplit = 0;
-      body.ntiles = body.tiles_m * body.tiles_n;
+    body->m = t->m;
+    body->k = t->k;
+    body->n = t->n;
+    // Split3: fused tiles (the bf16 split happens in the tile itself).
+    const int tm = ctx->path == kPathSplit3 ? kTcM : kFmaTile;
+    const int tn = ctx->path == kPathSplit3 ? kTcN : kFmaTile;
+    if (ctx->path == kPathSplit3) body->flags |= kFlagSplit3;
+    body->tiles_m = (uint32_t)((t->m + tm - 1) / tm);
+    body->tiles_n = (uint32_t)((t->n + tn - 1) / tn);
+    body->ntiles = body->tiles_m * body->tiles_n;
+  }
+  body->nsplit = 0;
+}
+
+// Admits tasks[0 .. count-1] of rank r in order, as far as the ring and the
+// staging space allow now. The batch's host-mode tasks share one staging
+// region: all their inputs first, in order, then all their outputs, so that
+// inputs (and outputs) the caller keeps in adjacent host buffers move in a
+// few large copies. Returns the number admitted; when that is 0, *err says
+// why (GVM_EAGAIN: not now; anything else: task 0 is invalid or can never
+// fit). Caller holds r->mu.
+int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* first_seq, int* err) {
+  gvm_ctx* ctx = r->ctx;
+  *err = GVM_OK;
+  if (!r->attached || ctx->shut) {
+    *err = GVM_ESTATE;
+    return 0;
+  }
+  bind_device(ctx);
+  const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
+  reap(r);
+  const uint64_t seq0 = r->next_seq;
+  const uint32_t free_slots = (uint32_t)(D - (seq0 - r->synced));
+  if (r->ring_head == r->ring_tail && r->ring_head % r->ring_bytes) {
+    // Empty ring: restart at its beginning, so that a region as large as the
+    // ring fits again.
+    r->ring_head = r->ring_tail = align_up(r->ring_head, r->ring_bytes);
+  }
+  uint32_t n = std::min(count, free_slots);
+
+  // ---- validate (stop before the first invalid task)
+  std::vector<Prep> prep(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const int rc = prep_task(r, &tasks[i], &prep[i]);
+    if (rc != GVM_OK) {
+      if (i == 0) {
+        *err = rc;
+        return 0;
+      }
+      n = i;
+      break;
     }
   }
-  memcpy(&ctx->descs[idx], &body, sizeof(body));
-
-  // ---- host mode: input copies + ready; output wait + copy + completion
-  if (!resident) {
-    const DriverApi* api = driver_api();
-    cudaError_t e = cudaSuccess;
-    if (bytes_a) e = cudaMemcpyAsync(reinterpret_cast<void*>(da), t->a, bytes_a, cudaMemcpyHostToDevice, r->in_stream);
-    if (e == cudaSuccess && bytes_b)
-      e = cudaMemcpyAsync(reinterpret_cast<void*>(db), t->b, bytes_b, cudaMemcpyHostToDevice, r->in_stream);
-    CUresult cr = CUDA_SUCCESS;
-    if (e == cudaSuccess)
-      cr = api->write_value32(reinterpret_cast<CUstream>(r->in_stream),
-                              reinterpret_cast<CUdeviceptr>(ctx->params.ready + idx), tag,
-                              CU_STREAM_WRITE_VALUE_DEFAULT);
-    if (e != cudaSuccess || cr != CUDA_SUCCESS) return GVM_EDEVICE;  // manager now unusable for this rank
-    ctx->h2d.fetch_add(bytes_a + bytes_b);
-    si.c_host = t->c;
-    si.c_dev = dcp;
-    si.c_bytes = bytes_c;
-    si.needs_out = true;
-  } else {
-    si.needs_out = false;
+  if (n == 0) {
+    // No free slot: the first task must still be valid to say "not now".
+    if (count > 0) {
+      Prep p0;
+      const int rc = prep_task(r, &tasks[0], &p0);
+      *err = rc != GVM_OK ? rc : GVM_EAGAIN;
+    }
+    return 0;
   }
 
-  // ---- publish
-  __atomic_store_n(&ctx->heads[r->id].head, (uint32_t)(seq + 1), __ATOMIC_RELEASE);
-  r->next_seq = seq + 1;
-  r->published.store(seq + 1, std::memory_order_release);
-  ctx->submitted.fetch_add(1);
-  if (seq_out) *seq_out = seq;
+  // ---- staging: the longest prefix whose region fits the ring and the cap now
+  const uint64_t cap = ctx->cfg.admission_cap_bytes;
+  const uint64_t staged_now = ctx->staged.load();
+  uint64_t need = 0, held = 0;
+  uint32_t k = 0;
+  for (; k < n; ++k) {
+    const uint64_t add = prep[k].sa + prep[k].sb + prep[k].sc;
+    if (add == 0) continue;
+    const uint64_t h = stage_room(r, need + add);
+    if (h == 0 || (cap && staged_now + h > cap)) break;
+    need += add;
+    held = h;
+  }
+  if (k == 0) {
+    const uint64_t add = prep[0].sa + prep[0].sb + prep[0].sc;
+    *err = (add > r->ring_bytes || (cap && add > cap)) ? GVM_ENOMEM : GVM_EAGAIN;
+    return 0;
+  }
+  uint64_t base = 0;
+  if (need) {
+    const uint64_t pos = r->ring_head + (held - need);  // skip the waste at the ring's end
+    base = r->ring_base + (pos % r->ring_bytes);
+    r->ring_head = pos + need;
+    const uint64_t st = ctx->staged.fetch_add(held) + held;
+    uint64_t pk = ctx->staged_peak.load();
+    while (st > pk && !ctx->staged_peak.compare_exchange_weak(pk, st)) {
+    }
+  }
+  uint64_t in_total = 0;
+  for (uint32_t i = 0; i < k; ++i) in_total += prep[i].sa + prep[i].sb;
+
+  // ---- descriptors; input copies gathered into runs
+  std::vector<CopyRun> runs, pieces;
+  std::vector<uint32_t> ready_after;  // per task: index of the run that completes its inputs
+  ready_after.assign(k, 0);
+  uint64_t in_off = 0, out_off = in_total, last_host = UINT64_MAX;
+  for (uint32_t i = 0; i < k; ++i)
+    if (prep[i].sa + prep[i].sb + prep[i].sc) last_host = i;
+  uint64_t h2d = 0;
+  for (uint32_t i = 0; i < k; ++i) {
+    const Prep& p = prep[i];
+    const gvm_task* t = p.t;
+    const uint64_t seq = seq0 + i;
+    const uint32_t slot = (uint32_t)(seq & (D - 1));
+    const uint32_t idx = (uint32_t)r->id * D + slot;
+    uint64_t da, db, dc;
+    if (p.resident) {
+      da = r->slice + t->a_off;
+      db = r->slice + t->b_off;
+      dc = r->slice + t->c_off;
+    } else {
+      da = base + in_off;
+      db = da + p.sa;
+      dc = base + out_off;
+      in_off += p.sa + p.sb;
+      out_off += p.sc;
+    }
+    TaskBody body;
+    fill_body(ctx, r, p, seq, da, db, dc, &body);
+    memcpy(&ctx->descs[idx], &body, sizeof(body));
+    SlotInfo& si = r->slots[slot];
+    si.bytes = (i == last_host) ? held : 0;
+    si.stage_end = r->ring_head;
+    si.needs_out = !p.resident;
+    si.c_host = t->c;
+    si.c_dev = dc;
+    si.c_bytes = p.resident ? 0 : p.bytes_c;
+    if (!p.resident) {
+      const uint64_t srcs_dst[2][3] = {{da, (uint64_t)(uintptr_t)t->a, p.bytes_a},
+                                       {db, (uint64_t)(uintptr_t)t->b, p.bytes_b}};
+      for (int j = 0; j < 2; ++j) {
+        const uint64_t dst = srcs_dst[j][0], bytes = srcs_dst[j][2];
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(srcs_dst[j][1]);
+        if (bytes == 0) continue;
+        h2d += bytes;
+        pieces.push_back(CopyRun{dst, src, bytes, 0, 1});
+        if (!runs.empty()) {
+          CopyRun& b = runs.back();
+          if (b.dst + b.bytes == dst && b.src + b.bytes == src && b.bytes + bytes <= kMaxCopyRun) {
+            b.bytes += bytes;
+            b.pieces += 1;
+            continue;
+          }
+        }
+        runs.push_back(CopyRun{dst, src, bytes, (uint32_t)pieces.size() - 1, 1});
+      }
+      ready_after[i] = runs.empty() ? 0 : (uint32_t)runs.size() - 1;
+    }
+  }
+
+  // ---- input copies, each task's ready word after the run that ends its inputs
+  {
+    const DriverApi* api = driver_api();
+    size_t next_ready = 0;
+    auto write_ready = [&](uint32_t upto_run) -> bool {
+      for (; next_ready < k; ++next_ready) {
+        const Prep& p = prep[next_ready];
+        if (p.resident) continue;
+        if (!runs.empty() && ready_after[next_ready] > upto_run) return true;
+        const uint64_t seq = seq0 + next_ready;
+        const uint32_t idx = (uint32_t)r->id * D + (uint32_t)(seq & (D - 1));
+        const CUresult cr = api->write_value32(reinterpret_cast<CUstream>(r->in_stream),
+                                               reinterpret_cast<CUdeviceptr>(ctx->params.ready + idx), tag_of(seq),
+                                               CU_STREAM_WRITE_VALUE_DEFAULT);
+        if (cr != CUDA_SUCCESS) {
+          GVM_TRACE("submit: ready write for rank %d seq %llu failed (%d)", r->id, (unsigned long long)seq, (int)cr);
+          return false;
+        }
+      }
+      return true;
+    };
+    bool ok = true;
+    for (uint32_t j = 0; ok && j < runs.size(); ++j) {
+      const cudaError_t e = issue_run(runs[j], pieces, cudaMemcpyHostToDevice, r->in_stream);
+      if (e != cudaSuccess)
+        GVM_TRACE("submit: copy of %llu bytes to 0x%llx failed: %s", (unsigned long long)runs[j].bytes,
+                  (unsigned long long)runs[j].dst, cudaGetErrorString(e));
+      ok = e == cudaSuccess;
+      if (ok) ok = write_ready(j);
+    }
+    if (ok) ok = write_ready(UINT32_MAX);
+    if (!ok) {
+      *err = GVM_EDEVICE;  // the manager is now unusable for this rank
+      return 0;
+    }
+    ctx->h2d.fetch_add(h2d);
+  }
+
+  // ---- publish the batch
+  __atomic_store_n(&ctx->heads[r->id].head, (uint32_t)(seq0 + k), __ATOMIC_RELEASE);
+  r->next_seq = seq0 + k;
+  r->published.store(seq0 + k, std::memory_order_release);
+  ctx->submitted.fetch_add(k);
+  if (first_seq) *first_seq = seq0;
   if (ctx->cfg.mode == GVM_MODE_CONTINUOUS) {
     // The resident scheduler was launched before any output wait was pushed.
-    return push_out_ops(r, r->next_seq);
+    if (push_out_ops(r, r->next_seq) != GVM_OK) {
+      *err = GVM_EDEVICE;
+      return (int)k;
+    }
   }
-  return GVM_OK;
+  return (int)k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gvm_submit(gvm_rank* r, const gvm_task* t, uint64_t* seq_out) {
+  if (!r || !t) return GVM_EINVAL;
+  std::lock_guard<std::mutex> g(r->mu);
+  int err = GVM_OK;
+  const int n = submit_batch(r, t, 1, seq_out, &err);
+  if (n == 1) return err;
+  return err != GVM_OK ? err : GVM_EAGAIN;
 }
 
 int gvm_submit_many(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* first_seq) {
   if (!r || (!tasks && count)) return GVM_EINVAL;
-  uint32_t done = 0;
-  for (; done < count; ++done) {
-    uint64_t s = 0;
-    const int rc = gvm_submit(r, &tasks[done], &s);
-    if (rc != GVM_OK) {
-      if (done == 0 && rc != GVM_EAGAIN) return rc;
-      break;
-    }
-    if (done == 0 && first_seq) *first_seq = s;
-  }
-  return (int)done;
+  if (count == 0) return 0;
+  std::lock_guard<std::mutex> g(r->mu);
+  int err = GVM_OK;
+  const int n = submit_batch(r, tasks, count, first_seq, &err);
+  if (n == 0 && err != GVM_EAGAIN) return err;
+  if (n > 0 && err == GVM_EDEVICE) return GVM_EDEVICE;
+  return n;
 }
 
 int gvm_poll(gvm_rank* r, uint64_t seq) {
