@@ -301,3 +301,70 @@ def test_spmd_harness_steps(gvm, mode):
         for spec, _, out, ref in keep:
             check_result(spec, ref, out)
         assert mgr.stats()["device_status"] == 0
+
+
+@pytest.mark.parametrize("slice_mb", [64, 2])
+def test_batch_from_contiguous_host_blocks(gvm, slice_mb):
+    # A rank's operands in one pinned block (A then B per task) and its
+    # outputs in another: gvm_submit_many packs the batch's staging the same
+    # way and merges adjacent copies. Sizes mix 256-byte multiples (merged)
+    # with others (not merged). With a 2 MiB slice the batch is admitted a
+    # prefix at a time (the binding flushes and syncs in between).
+    specs = []
+    for i in range(10):
+        if i % 3 == 0:
+            specs.append(("v", 65536 if i % 2 == 0 else 1000 + i))
+        else:
+            specs.append(("g", (128, 256, 64) if i % 2 == 0 else (67, 130, 45)))
+    R = 2
+    with gvm.Manager(R, ring_depth=16, sgemm_path="split3", slice_bytes=slice_mb << 20) as mgr:
+        ranks = [mgr.attach(r) for r in range(R)]
+        checks = []
+        arrays = []
+        for r in range(R):
+            sizes = []
+            for kind, shp in specs:
+                if kind == "v":
+                    sizes.append((4 * shp, 4 * shp, 4 * shp))
+                else:
+                    m, n, k = shp
+                    sizes.append((4 * m * k, 4 * k * n, 4 * m * n))
+            al = lambda x: (x + 255) // 256 * 256  # noqa: E731
+            inb = torch.zeros(sum(al(a) + al(b) for a, b, _ in sizes), dtype=torch.uint8).pin_memory()
+            outb = torch.zeros(sum(al(c) for _, _, c in sizes), dtype=torch.uint8).pin_memory()
+            arr = (gvm.GvmTask * len(specs))()
+            io = oo = 0
+            for i, ((kind, shp), (la, lb, lc)) in enumerate(zip(specs, sizes)):
+                ta = inb[io:io + la].view(torch.float32)
+                tb = inb[io + al(la):io + al(la) + lb].view(torch.float32)
+                tc = outb[oo:oo + lc].view(torch.float32)
+                io += al(la) + al(lb)
+                oo += al(lc)
+                seed = synth.task_seed(r, i)
+                t = arr[i]
+                if kind == "v":
+                    a, b = synth.vadd_inputs(seed, shp)
+                    t.type, t.n = gvm.GVM_TASK_VADD, shp
+                    checks.append((synth.TaskSpec(rank=r, index=i, kind=synth.TASK_VADD, n=shp), (a, b), tc))
+                else:
+                    m, n, k = shp
+                    a, b = synth.sgemm_inputs(seed, m, n, k)
+                    t.type, t.m, t.n, t.k = gvm.GVM_TASK_SGEMM, m, n, k
+                    checks.append((synth.TaskSpec(rank=r, index=i, kind=synth.TASK_SGEMM, m=m, n=n, k=k), (a, b),
+                                   tc.view(m, n)))
+                ta.copy_(torch.from_numpy(np.ascontiguousarray(a)).reshape(-1))
+                tb.copy_(torch.from_numpy(np.ascontiguousarray(b)).reshape(-1))
+                t.flags = 0
+                t.a, t.b, t.c = ta.data_ptr(), tb.data_ptr(), tc.data_ptr()
+            arrays.append((arr, inb, outb))
+        lasts = []
+        for r in range(R):
+            first, cnt = ranks[r].submit_many(arrays[r][0])
+            assert cnt == len(specs)
+            lasts.append(first + cnt - 1)
+        mgr.flush()
+        for r in range(R):
+            ranks[r].sync(lasts[r])
+        for spec, ins, out in checks:
+            check_result(spec, ins, out)
+        assert mgr.stats()["device_status"] == 0
