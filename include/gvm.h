@@ -72,6 +72,9 @@ extern "C" {
 #define GVM_SGEMM_SPLIT3_FUSED 2 /* gvm_sgemm_f32 only: the manager's form of split3 (split
                               during staging, no scratch); bit-identical to
                               GVM_SGEMM_SPLIT3 */
+#define GVM_SGEMM_SPLIT3_PAIR 3 /* gvm_sgemm_f32 only: split during staging on CTA pairs
+                              (two-SM tcgen05 MMAs, 256 x 256 tiles); the same products
+                              in the same order, bit-identical to GVM_SGEMM_SPLIT3 */
 
 /* ---- manager modes ------------------------------------------------------ */
 #define GVM_MODE_BARRIER 0    /* Section 5 request barrier: gvm_flush runs the scheduler

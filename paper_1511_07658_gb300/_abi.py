@@ -26,6 +26,7 @@ GVM_TASK_RESIDENT = 1
 GVM_SGEMM_FMA = 0
 GVM_SGEMM_SPLIT3 = 1
 GVM_SGEMM_SPLIT3_FUSED = 2
+GVM_SGEMM_SPLIT3_PAIR = 3
 GVM_MODE_BARRIER = 0
 GVM_MODE_CONTINUOUS = 1
 

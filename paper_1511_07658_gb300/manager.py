@@ -20,6 +20,7 @@ from ._abi import (
     GVM_SGEMM_FMA,
     GVM_SGEMM_SPLIT3,
     GVM_SGEMM_SPLIT3_FUSED,
+    GVM_SGEMM_SPLIT3_PAIR,
     GVM_TASK_RESIDENT,
     GVM_TASK_SGEMM,
     GVM_TASK_VADD,
@@ -30,7 +31,12 @@ from ._abi import (
     lib,
 )
 
-_PATHS = {"fma": GVM_SGEMM_FMA, "split3": GVM_SGEMM_SPLIT3, "split3_fused": GVM_SGEMM_SPLIT3_FUSED}
+_PATHS = {
+    "fma": GVM_SGEMM_FMA,
+    "split3": GVM_SGEMM_SPLIT3,
+    "split3_fused": GVM_SGEMM_SPLIT3_FUSED,
+    "split3_pair": GVM_SGEMM_SPLIT3_PAIR,
+}
 _MODES = {"barrier": GVM_MODE_BARRIER, "continuous": GVM_MODE_CONTINUOUS}
 
 

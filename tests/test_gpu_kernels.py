@@ -85,7 +85,7 @@ def run_sgemm(gvm, A, B, path):
     return tC.cpu().numpy()
 
 
-@pytest.mark.parametrize("path", ["fma", "split3", "split3_fused"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_fused", "split3_pair"])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_sgemm_normal_inputs(gvm, path, shape):
     m, n, k = shape
@@ -143,6 +143,25 @@ def test_split3_fused_equals_prepass(gvm, shape):
     A, B = synth.sgemm_inputs(synth.task_seed(7, m % 1000), m, n, k)
     C1 = run_sgemm(gvm, A, B, "split3")
     C2 = run_sgemm(gvm, A, B, "split3_fused")
+    assert np.array_equal(bits(C1), bits(C2)), shape
+    from paper_1511_07658_gb300.manager import kernel_status
+
+    assert kernel_status() == 0
+
+
+@pytest.mark.parametrize(
+    "shape",
+    [(256, 256, 32), (257, 130, 67), (512, 512, 512), (129, 257, 513), (300, 1001, 77),
+     (130, 260, 100), (1000, 520, 2052), (4096, 2048, 96), (2500, 3000, 40)],
+)
+def test_split3_pair_equals_prepass(gvm, shape):
+    # CTA pairs (two-SM MMAs, 256 x 256 tiles): the same split and the same
+    # three products per 16-wide k slice, so the result must equal the
+    # pre-pass form bit for bit, on ragged and unaligned shapes too.
+    m, n, k = shape
+    A, B = synth.sgemm_inputs(synth.task_seed(9, m % 1000), m, n, k)
+    C1 = run_sgemm(gvm, A, B, "split3")
+    C2 = run_sgemm(gvm, A, B, "split3_pair")
     assert np.array_equal(bits(C1), bits(C2)), shape
     from paper_1511_07658_gb300.manager import kernel_status
 
