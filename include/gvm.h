@@ -118,6 +118,10 @@ typedef struct gvm_config {
                                rings; 0 = 1000 ns */
   int32_t grid_ctas;        /* scheduler CTAs; 0 = one per SM */
   int32_t ingest_quantum;   /* tasks taken from one rank per ingest pass; 0 = 4 */
+  uint64_t copy_run_bytes;  /* host-mode copies of one batch that are adjacent on both
+                               sides are merged up to this many bytes; 0 = 16 MiB */
+  int64_t vadd_tile;        /* elements per vector-add tile (rounded to 1024); 0 = per
+                               task: n / scheduler CTAs, within 16 Ki .. 1 Mi */
 } gvm_config;
 
 typedef struct gvm_task {

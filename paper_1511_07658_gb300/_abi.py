@@ -49,6 +49,8 @@ class GvmConfig(ctypes.Structure):
         ("idle_poll_ns", c_uint64),
         ("grid_ctas", c_int32),
         ("ingest_quantum", c_int32),
+        ("copy_run_bytes", c_uint64),
+        ("vadd_tile", c_int64),
     ]
 
 

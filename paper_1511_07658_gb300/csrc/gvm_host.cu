@@ -61,11 +61,11 @@ bool debug_on() {
 
 // gvm_sync gives the device this long beyond its own wait limit to report.
 constexpr uint64_t kStreamQueryNs = 2000000;  // gvm_sync: driver status check period (2 ms)
-// Copies of one batch are merged when both sides are adjacent, up to this
-// many bytes per copy: the link serves 1 MiB copies at less than half its
-// rate, while a few MiB per copy still lets the scheduler start on the first
-// tasks while later inputs are in flight.
-constexpr uint64_t kMaxCopyRun = 16ull << 20;
+// Copies of one batch are merged when both sides are adjacent, by default up
+// to this many bytes per copy (gvm_config.copy_run_bytes): the link serves
+// 1 MiB copies at less than half its rate, while a few MiB per copy still
+// lets the scheduler start on the first tasks while later inputs arrive.
+constexpr uint64_t kDefaultCopyRun = 16ull << 20;
 constexpr uint64_t kHostGraceNs = 1000ull * 1000 * 1000;
 
 inline uint64_t now_ns() {
@@ -217,7 +217,7 @@ cudaError_t issue_run(const CopyRun& run, const std::vector<CopyRun>& pieces, cu
 // output stream: a wait on each task's done word, the device-to-host copy of
 // its output, its completion word. Outputs adjacent on both sides (a batch's
 // outputs are packed in staging; adjacent host buffers are the caller's
-// choice) share one copy of up to kMaxCopyRun bytes after all their waits.
+// choice) share one copy of up to copy_run_bytes after all their waits.
 // Called only once the scheduler launch that will write those done words has
 // been pushed: a blocked wait can then never sit ahead of its own producer in
 // a hardware queue that two streams share.
@@ -241,7 +241,7 @@ int push_out_ops(gvm_rank* r, uint64_t upto) {
       const SlotInfo& nx = r->slots[s1 & (D - 1)];
       if (!nx.needs_out || nx.c_dev != first.c_dev + bytes ||
           static_cast<const uint8_t*>(nx.c_host) != static_cast<const uint8_t*>(first.c_host) + bytes ||
-          bytes + nx.c_bytes > kMaxCopyRun)
+          bytes + nx.c_bytes > ctx->cfg.copy_run_bytes)
         break;
       pieces.push_back(CopyRun{nx.c_dev, static_cast<const uint8_t*>(nx.c_host), nx.c_bytes, 0, 1});
       bytes += nx.c_bytes;
@@ -351,6 +351,9 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   if (slice == 0 || resident > slice) return GVM_EINVAL;
   if (cfg.wait_timeout_ns == 0) cfg.wait_timeout_ns = 10ull * 1000 * 1000 * 1000;
   if (cfg.idle_poll_ns == 0) cfg.idle_poll_ns = 1000;
+  if (cfg.copy_run_bytes == 0) cfg.copy_run_bytes = kDefaultCopyRun;
+  if (cfg.vadd_tile < 0) return GVM_EINVAL;
+  if (cfg.vadd_tile > 0) cfg.vadd_tile = std::max<int64_t>(1024, cfg.vadd_tile / 1024 * 1024);
   if (cfg.ingest_quantum <= 0) cfg.ingest_quantum = 4;
   if (cfg.copy_streams)
     for (int i = 0; i < 2 * cfg.max_ranks; ++i)
@@ -567,9 +570,12 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
   body->c = dc;
   if (t->type == GVM_TASK_VADD) {
     body->n = t->n;
-    int64_t vt = (t->n + ctx->grid - 1) / std::max(ctx->grid, 1);
-    vt = (vt + 4095) / 4096 * 4096;
-    vt = std::min<int64_t>(std::max<int64_t>(vt, kVaddTileMin), kVaddTileMax);
+    int64_t vt = ctx->cfg.vadd_tile;
+    if (vt == 0) {
+      vt = (t->n + ctx->grid - 1) / std::max(ctx->grid, 1);
+      vt = (vt + 4095) / 4096 * 4096;
+      vt = std::min<int64_t>(std::max<int64_t>(vt, kVaddTileMin), kVaddTileMax);
+    }
     body->vadd_tile = vt;
     body->ntiles = (uint32_t)((t->n + vt - 1) / vt);
   } else {
@@ -602,6 +608,10 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* f
     return 0;
   }
   bind_device(ctx);
+  if (ld_acq(&ctx->shared->status)) {  // the scheduler stopped on an error: admit nothing
+    *err = GVM_EDEVICE;
+    return 0;
+  }
   const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
   reap(r);
   const uint64_t seq0 = r->next_seq;
@@ -714,7 +724,7 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* f
         pieces.push_back(CopyRun{dst, src, bytes, 0, 1});
         if (!runs.empty()) {
           CopyRun& b = runs.back();
-          if (b.dst + b.bytes == dst && b.src + b.bytes == src && b.bytes + bytes <= kMaxCopyRun) {
+          if (b.dst + b.bytes == dst && b.src + b.bytes == src && b.bytes + bytes <= ctx->cfg.copy_run_bytes) {
             b.bytes += bytes;
             b.pieces += 1;
             continue;

@@ -1,13 +1,15 @@
 """Thin Python wrappers over the gvm C ABI.
 
-``Manager`` allocates the device arena and control block with PyTorch, takes
-its streams from PyTorch, and passes raw pointers to ``gvm_init``. ``Rank``
+``Manager`` allocates the device arena and control block with PyTorch and
+passes raw pointers to ``gvm_init`` (which creates the streams). ``Rank``
 wraps a rank handle (the paper's virtual GPU, Section 5): ``submit_*`` is
 SND()+STR(), ``sync`` is STP()+RCV(). Every step of a task runs in libgvm.
 """
 from __future__ import annotations
 
 import ctypes
+import json
+import os
 from ctypes import byref, c_uint32, c_uint64, c_void_p
 
 import torch
@@ -52,6 +54,19 @@ def _stream_handle(stream) -> int:
     return stream.cuda_stream
 
 
+TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+
+
+def tuning() -> dict:
+    """Manager parameters chosen by ``autotune`` on a GB300 (the committed
+    table), or {} when there is none: the library's own defaults apply."""
+    try:
+        with open(TUNING_FILE) as f:
+            return json.load(f).get("choice", {})
+    except (OSError, ValueError):
+        return {}
+
+
 class Rank:
     """One rank's virtual GPU: its ring, arena slice and streams."""
 
@@ -72,7 +87,7 @@ class Rank:
             rc = L.gvm_submit(self.handle, byref(task), byref(seq))
             if rc == GVM_EAGAIN and block:
                 self.mgr.flush_if_barrier()
-                L.gvm_sync(self.handle, self._oldest_pending())
+                self._sync_checked(self._oldest_pending())
                 continue
             check(rc, "gvm_submit")
             self._last = seq.value
@@ -100,8 +115,14 @@ class Rank:
                 if not block:
                     break
                 self.mgr.flush_if_barrier()
-                L.gvm_sync(self.handle, self._oldest_pending())
+                self._sync_checked(self._oldest_pending())
         return (first_seq if first_seq is not None else -1), total
+
+    def _sync_checked(self, seq: int) -> None:
+        rc = lib().gvm_sync(self.handle, seq)
+        if rc != 0:
+            st = self.mgr.stats()
+            check(rc, f"gvm_sync (device status {st['device_status']}, where {st['device_where']})")
 
     def _oldest_pending(self) -> int:
         last = getattr(self, "_last", None)
@@ -213,6 +234,8 @@ class Manager:
         idle_poll_ns: int = 1000,
         grid_ctas: int = 0,
         ingest_quantum: int = 4,
+        copy_run_bytes: int | None = None,
+        vadd_tile: int | None = None,
         device: int | None = None,
     ):
         if not torch.cuda.is_available():
@@ -251,6 +274,9 @@ class Manager:
         cfg.idle_poll_ns = idle_poll_ns
         cfg.grid_ctas = grid_ctas
         cfg.ingest_quantum = ingest_quantum
+        tuned = tuning()
+        cfg.copy_run_bytes = int(tuned.get("copy_run_bytes", 0) if copy_run_bytes is None else copy_run_bytes)
+        cfg.vadd_tile = int(tuned.get("vadd_tile", 0) if vadd_tile is None else vadd_tile)
         self.cfg = cfg
         h = c_void_p()
         with torch.cuda.device(self.device):
