@@ -662,6 +662,10 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* f
   if (k == 0) {
     const uint64_t add = prep[0].sa + prep[0].sb + prep[0].sc;
     *err = (add > r->ring_bytes || (cap && add > cap)) ? GVM_ENOMEM : GVM_EAGAIN;
+    GVM_TRACE("submit: rank %d refused (%d): needs %llu, ring head %llu tail %llu of %llu, synced %llu next %llu",
+              r->id, *err, (unsigned long long)add, (unsigned long long)r->ring_head,
+              (unsigned long long)r->ring_tail, (unsigned long long)r->ring_bytes, (unsigned long long)r->synced,
+              (unsigned long long)r->next_seq);
     return 0;
   }
   uint64_t base = 0;
@@ -977,8 +981,28 @@ int gvm_shutdown(gvm_ctx* ctx) {
   const DriverApi* api = driver_api();
   const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
   for (auto& rk : ctx->ranks) {
+    GVM_TRACE("shutdown: rank %d: input stream (out_pushed=%llu synced=%llu next=%llu)", rk->id,
+              (unsigned long long)rk->out_pushed, (unsigned long long)rk->synced,
+              (unsigned long long)rk->next_seq);
     if (cudaStreamSynchronize(rk->in_stream) != cudaSuccess) rc = GVM_EDEVICE;
-    if (!device_ok) {
+    // An output stream still waiting after the scheduler has exited waits
+    // for a done word no launch will write: wait a bounded time, then treat
+    // it like a device error.
+    bool out_stuck = false;
+    if (device_ok) {
+      const uint64_t t0 = now_ns();
+      cudaError_t q;
+      while ((q = cudaStreamQuery(rk->out_stream)) == cudaErrorNotReady &&
+             now_ns() - t0 < ctx->cfg.wait_timeout_ns + kHostGraceNs)
+        std::this_thread::yield();
+      out_stuck = q == cudaErrorNotReady;
+      if (out_stuck) {
+        fprintf(stderr, "[gvm] shutdown: rank %d output stream still waits (synced=%llu out_pushed=%llu)\n", rk->id,
+                (unsigned long long)rk->synced, (unsigned long long)rk->out_pushed);
+        rc = GVM_ETIMEDOUT;
+      }
+    }
+    if (!device_ok || out_stuck) {
       // The scheduler stopped on an error: release every output-stream wait
       // whose done word will never be written, so that the caller's streams
       // do not stay blocked after the manager is gone. Those tasks' outputs
@@ -993,6 +1017,7 @@ int gvm_shutdown(gvm_ctx* ctx) {
       }
       if (cudaStreamSynchronize(rk->in_stream) != cudaSuccess) rc = GVM_EDEVICE;
     }
+    GVM_TRACE("shutdown: rank %d: output stream", rk->id);
     if (cudaStreamSynchronize(rk->out_stream) != cudaSuccess) rc = GVM_EDEVICE;
     GVM_TRACE("shutdown: rank %d streams idle (synced=%llu next=%llu)", rk->id, (unsigned long long)rk->synced,
               (unsigned long long)rk->next_seq);

@@ -115,6 +115,22 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
     return out;
   }
   __threadfence();
+  // Drain mode: once a pass has found the rings empty (`drained`, set below
+  // under this lock), nothing more is published in this launch, even if the
+  // host has published descriptors since: CTAs leave with reservations
+  // beyond the published tiles, and a tile published after its reserver
+  // left would never run. Those descriptors wait in the rings for the next
+  // launch.
+  uint32_t closed = 0;
+  if (lane == 0 && p.drain) closed = ld_relaxed_gpu(&p.ctrl->drained);
+  if (__shfl_sync(0xffffffffu, closed, 0)) {
+    if (lane == 0) {
+      __threadfence();
+      atomicExch(&p.ctrl->ingest_lock, 0u);
+    }
+    __syncwarp();
+    return out;
+  }
   const uint64_t pub0 = ld_relaxed_gpu64(&p.ctrl->published);
   const uint64_t tiles0 = ld_relaxed_gpu64(&p.ctrl->published_tiles);
   const uint64_t consumed = ld_relaxed_gpu64(&p.ctrl->cursor);
@@ -230,8 +246,10 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
   fence_tensormap_release();
   __syncwarp();
   if (lane == 0) {
-    if (pending == 0 && pub == pub0)
+    if (pending == 0 && pub == pub0) {
       *reinterpret_cast<volatile uint64_t*>(&p.ctrl->quiet_until) = now + kQuietNs;
+      if (p.drain) st_release_gpu(&p.ctrl->drained, 1u);  // under the lock: no later pass publishes
+    }
     if (pub != pub0) {
       st_release_gpu64(&p.ctrl->published, pub);
       st_release_gpu64(&p.ctrl->published_tiles, ptiles);
@@ -396,9 +414,7 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
     if (!r.locked_out) {
       if (r.pending == 0) {
         set_stall(0);
-        if (p.drain) {
-          if (lane == 0) atomicExch(&p.ctrl->drained, 1u);
-          __syncwarp();
+        if (p.drain) {  // this pass (or an earlier one) closed the launch: `drained` is set
           if (reserved_published()) continue;
           return 0;
         }
