@@ -246,3 +246,40 @@ def grouped_mixed(ranks: int = 64, per_rank: int = 256, recipe_seed: int = 0xB47
             w.tasks.append(TaskSpec(r, t, TASK_SGEMM, n=n, m=m, k=k, seed=task_seed(r, t)))
             i += 1
     return w
+
+
+def stress_mix(
+    ranks: int = 128,
+    per_rank: int = 8,
+    vadd_median: float = 2.0 ** 20,
+    side_median: float = 768.0,
+    rate_per_rank_hz: float = 1000.0,
+    recipe_seed: int = 0x57E5,
+) -> Workload:
+    """Open-loop stress mix: 70% vector add, 30% square SGEMM, Poisson
+    arrivals. Vector-add length n = round(vadd_median * e^(1.5 Z)) clamped to
+    [2^10, 2^28]; SGEMM side round(side_median * e^(0.7 Z)) clamped to
+    [64, 4096] (Z standard normal). Smaller medians give the same shape mix
+    at test size (the clamps then follow the medians' scale)."""
+    w = Workload(f"stress_r{ranks}x{per_rank}", ranks)
+    total = ranks * per_rank
+    kind_u = _draws(recipe_seed, total)
+    z = standard_normal(recipe_seed + 1, total)
+    gaps = -np.log1p(-_draws(recipe_seed + 2, total)) / rate_per_rank_hz
+    scale = vadd_median / 2.0 ** 20
+    lo_n, hi_n = max(1, int(2 ** 10 * scale)), max(2, int(2 ** 28 * scale))
+    sscale = side_median / 768.0
+    lo_s, hi_s = max(1, int(64 * sscale)), max(2, int(4096 * sscale))
+    i = 0
+    for r in range(ranks):
+        t_arr = 0.0
+        for t in range(per_rank):
+            t_arr += float(gaps[i])
+            if kind_u[i] < 0.7:
+                n = int(min(max(round(vadd_median * math.exp(1.5 * float(z[i]))), lo_n), hi_n))
+                w.tasks.append(TaskSpec(r, t, TASK_VADD, n=n, seed=task_seed(r, t), arrival_s=t_arr))
+            else:
+                sd = int(min(max(round(side_median * math.exp(0.7 * float(z[i]))), lo_s), hi_s))
+                w.tasks.append(TaskSpec(r, t, TASK_SGEMM, n=sd, m=sd, k=sd, seed=task_seed(r, t), arrival_s=t_arr))
+            i += 1
+    return w

@@ -368,3 +368,12 @@ def test_batch_from_contiguous_host_blocks(gvm, slice_mb):
         for spec, ins, out in checks:
             check_result(spec, ins, out)
         assert mgr.stats()["device_status"] == 0
+
+
+@pytest.mark.parametrize("mode,path", [("barrier", "split3"), ("continuous", "split3"), ("barrier", "fma")])
+def test_stress_mix_ragged_sizes(gvm, mode, path):
+    # The stress config's shape mix (70% vector adds with lognormal lengths,
+    # 30% square SGEMMs with lognormal sides; most sizes odd, none aligned)
+    # scaled to test size: 8 ranks x 6 tasks, every result against the oracle.
+    w = synth.stress_mix(ranks=8, per_rank=6, vadd_median=4096, side_median=96)
+    run_workload(gvm, w, mode=mode, path=path, depth=8, slice_mb=32)

@@ -298,3 +298,23 @@ def test_workload_recipes():
             assert t.m == t.n == t.k and t.m in (256, 512, 1024, 2048)
     g = synth.grouped_mixed(ranks=4, per_rank=8)
     assert all(128 <= x <= 2048 and x % 64 == 0 for t in g.tasks for x in (t.m, t.n, t.k))
+
+
+def test_stress_mix_recipe():
+    # The stress recipe's own invariants: 70/30 mix within sampling noise,
+    # clamps respected, arrivals increasing per rank, and the same draw every
+    # time (seeded).
+    w = synth.stress_mix(ranks=64, per_rank=32)
+    kinds = [t.kind for t in w.tasks]
+    frac = kinds.count(synth.TASK_VADD) / len(kinds)
+    assert 0.65 < frac < 0.75
+    for t in w.tasks:
+        if t.kind == synth.TASK_VADD:
+            assert 2 ** 10 <= t.n <= 2 ** 28
+        else:
+            assert 64 <= t.m == t.n == t.k <= 4096
+    for r in range(64):
+        arr = [t.arrival_s for t in w.tasks if t.rank == r]
+        assert all(b > a for a, b in zip(arr, arr[1:]))
+    w2 = synth.stress_mix(ranks=64, per_rank=32)
+    assert [(t.n, t.m, t.arrival_s) for t in w.tasks] == [(t.n, t.m, t.arrival_s) for t in w2.tasks]
