@@ -923,6 +923,173 @@ def model_check(args, w):
             "mean_deviation": statistics.mean(r["deviation"] for r in rows)}
 
 
+def paper_ps_check():
+    """The paper's own mechanism and model (Sections 4.2.1-4.2.3): one host
+    thread issues every process's task on that process's stream, in
+    programming style 1 (all input copies, then all kernels, then all output
+    copies) or style 2 (per stream: input, kernel, output), with the task
+    kernels alone (no persistent scheduler), for N = 1, 2, 4, 8, 16. Measured
+    times against Eqs. 2-7 from solo T_in, T_comp, T_out, for a
+    compute-intensive task (FMA SGEMM 2048^3) and an I/O-intensive one
+    (vector add, n = 2^24). Deviation as the paper reports it (Section 6)."""
+    import torch
+
+    import paper_1511_07658_gb300 as g
+    from oracle import model
+
+    reps = 5
+    out = {}
+    cases = {"ci_sgemm_fma_2048": ("sgemm", 2048), "ioi_vadd_2p24": ("vadd", 1 << 24)}
+    for name, (kind, size) in cases.items():
+        nmax = 16
+        if kind == "sgemm":
+            hin = [[torch.randn(size, size).pin_memory(), torch.randn(size, size).pin_memory()] for _ in range(nmax)]
+            hout = [torch.empty(size, size).pin_memory() for _ in range(nmax)]
+        else:
+            hin = [[torch.randn(size).pin_memory(), torch.randn(size).pin_memory()] for _ in range(nmax)]
+            hout = [torch.empty(size).pin_memory() for _ in range(nmax)]
+        din = [[x.cuda() for x in h] for h in hin]
+        dout = [torch.empty_like(h, device="cuda") for h in hout]
+        streams = [torch.cuda.Stream() for _ in range(nmax)]
+
+        def h2d(r):
+            for d, h in zip(din[r], hin[r]):
+                d.copy_(h, non_blocking=True)
+
+        def comp(r):
+            if kind == "sgemm":
+                g.sgemm_f32(din[r][0], din[r][1], dout[r], path="fma", stream=streams[r])
+            else:
+                g.vadd_f32(din[r][0], din[r][1], dout[r], stream=streams[r])
+
+        def d2h(r):
+            hout[r].copy_(dout[r], non_blocking=True)
+
+        def run(n, style):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for r in range(n):
+                streams[r].wait_event(e0)
+            if style == 1:
+                for phase in (h2d, comp, d2h):
+                    for r in range(n):
+                        with torch.cuda.stream(streams[r]):
+                            phase(r)
+            else:
+                for r in range(n):
+                    with torch.cuda.stream(streams[r]):
+                        h2d(r)
+                        comp(r)
+                        d2h(r)
+            ends = []
+            for r in range(n):
+                ev = torch.cuda.Event()
+                ev.record(streams[r])
+                ends.append(ev)
+            cur = torch.cuda.current_stream()
+            for ev in ends:
+                cur.wait_event(ev)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record()
+            e1.synchronize()
+            return e0.elapsed_time(e1) / 1e3
+
+        def solo(fn):
+            times = []
+            for _ in range(reps + 2):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(streams[0]):
+                    e0.record(streams[0])
+                    fn(0)
+                    e1.record(streams[0])
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            return statistics.median(times[2:])
+
+        t_in, t_comp, t_out = solo(h2d), solo(comp), solo(d2h)
+        rows = []
+        for n in (1, 2, 4, 8, 16):
+            row = {"N": n}
+            for style in (1, 2):
+                run(n, style)
+                meas = statistics.median(run(n, style) for _ in range(reps))
+                if style == 1:
+                    pred = model.t_total_ci_ps1(n, t_in, t_comp, t_out)  # Eq. 2 = Eq. 4
+                else:
+                    pred = (model.t_total_ci_ps2(n, t_in, t_comp, t_out) if model.classify(t_in, t_comp, t_out) == model.CI
+                            else model.t_total_ioi_ps2(n, t_in, t_comp, t_out))  # Eq. 3 or Eq. 7
+                row[f"ps{style}_measured_s"] = meas
+                row[f"ps{style}_model_s"] = pred
+                row[f"ps{style}_deviation"] = model.deviation(meas, pred)
+            row["eq1_no_init_s"] = model.t_total_no_vt(n, 0.0, t_in, t_comp, t_out, 0.0)
+            rows.append(row)
+        out[name] = {
+            "t_in_s": t_in, "t_comp_s": t_comp, "t_out_s": t_out, "class": model.classify(t_in, t_comp, t_out),
+            "rows": rows,
+            "mean_deviation_ps1": statistics.mean(r["ps1_deviation"] for r in rows),
+            "mean_deviation_ps2": statistics.mean(r["ps2_deviation"] for r in rows),
+        }
+        del din, dout, hin, hout
+        torch.cuda.empty_cache()
+    return out
+
+
+def overhead_check():
+    """Virtualization-layer overhead (Section 6): one rank, one vector add of
+    1 MB to 400 MB per operand array through the manager (host buffers,
+    submit -> flush -> sync on the host clock) against the same copies and
+    kernel issued directly on one stream (CUDA events): (turnaround - direct)
+    / direct per size."""
+    import torch
+
+    import paper_1511_07658_gb300 as g
+
+    rows = []
+    for mb in (1, 4, 16, 64, 256, 400):
+        n = mb * (1 << 20) // 4
+        a = torch.rand(n).pin_memory()
+        b = torch.rand(n).pin_memory()
+        c = torch.empty(n).pin_memory()
+        da, db, dc = a.cuda(), b.cuda(), torch.empty(n, device="cuda")
+        st = torch.cuda.Stream()
+
+        def direct():
+            with torch.cuda.stream(st):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                da.copy_(a, non_blocking=True)
+                db.copy_(b, non_blocking=True)
+                g.vadd_f32(da, db, dc, stream=st)
+                c.copy_(dc, non_blocking=True)
+                e1.record(st)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / 1e3
+
+        for _ in range(2):
+            direct()
+        t_direct = statistics.median(direct() for _ in range(5))
+        mgr = g.Manager(1, ring_depth=2, slice_bytes=3 * 4 * n + (8 << 20))
+        rk = mgr.attach(0)
+
+        def managed():
+            t0 = time.perf_counter()
+            seq = rk.submit_vadd(a, b, c)
+            mgr.flush()
+            rk.sync(seq)
+            return time.perf_counter() - t0
+
+        for _ in range(2):
+            managed()
+        t_mgr = statistics.median(managed() for _ in range(5))
+        mgr.shutdown()
+        rows.append({"mb_per_array": mb, "direct_s": t_direct, "manager_s": t_mgr,
+                     "overhead": (t_mgr - t_direct) / t_direct})
+        del a, b, c, da, db, dc
+    return {"rows": rows, "kind": "one rank, host buffers; direct = copies + kernel on one stream"}
+
+
 # --------------------------------------------------------------- grouped
 
 
@@ -1081,6 +1248,8 @@ def main():
             out["plain_per_rank"] = plain_per_rank(w)
         if args.model:
             out["model_check"] = model_check(args, w)
+            out["paper_ps_model"] = paper_ps_check()
+            out["virtualization_overhead"] = overhead_check()
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
