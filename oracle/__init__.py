@@ -11,6 +11,8 @@ Computing Systems"):
 
 * ``vadd`` -- the vector-addition task of Table 2: one binary32 addition per
   element.
+* ``vmul`` -- the vector-multiplication task of Table 2 (VecMult): ``iters``
+  binary32 multiplications by ``b`` per element, each rounded.
 * ``sgemm64`` -- the single-precision matrix-multiplication task of Table 2
   (Section 6), as the exact product computed in binary64.
 * ``run_rank`` / ``run_workload`` -- every rank's tasks in its submission
@@ -67,6 +69,8 @@ def _load():
             i64 = ctypes.c_int64
             lib.oracle_vadd_f32.argtypes = [f32p, f32p, f32p, i64]
             lib.oracle_vadd_f32.restype = None
+            lib.oracle_vmul_f32.argtypes = [f32p, f32p, f32p, i64, ctypes.c_int32]
+            lib.oracle_vmul_f32.restype = None
             lib.oracle_sgemm_f64.argtypes = [f32p, f32p, f64p, i64, i64, i64]
             lib.oracle_sgemm_f64.restype = None
             lib.oracle_rel_fro_err.argtypes = [f32p, f64p, i64]
@@ -93,6 +97,19 @@ def vadd(a, b) -> np.ndarray:
     c = np.empty_like(a)
     _load().oracle_vadd_f32(_ptr(a, ctypes.c_float), _ptr(b, ctypes.c_float),
                             _ptr(c, ctypes.c_float), a.size)
+    return c
+
+
+def vmul(a, b, iters: int) -> np.ndarray:
+    """c = a * b * ... * b with ``iters`` binary32 products (Table 2, VecMult)."""
+    a, b = _f32(a), _f32(b)
+    if a.shape != b.shape:
+        raise ValueError("vmul operands differ in shape")
+    if not 1 <= iters <= 1024:
+        raise ValueError("vmul iters outside 1..1024")
+    c = np.empty_like(a)
+    _load().oracle_vmul_f32(_ptr(a, ctypes.c_float), _ptr(b, ctypes.c_float),
+                            _ptr(c, ctypes.c_float), a.size, iters)
     return c
 
 
@@ -132,6 +149,9 @@ def run_task(spec):
     if spec.kind == synth.TASK_VADD:
         a, b = synth.vadd_inputs(spec.seed, spec.n)
         return vadd(a, b)
+    if spec.kind == synth.TASK_VMUL:
+        a, b = synth.vmul_inputs(spec.seed, spec.n)
+        return vmul(a, b, spec.k)
     if spec.kind == synth.TASK_SGEMM:
         A, B = synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
         return sgemm64(A, B)

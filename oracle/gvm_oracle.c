@@ -14,6 +14,9 @@
  *
  *   vector add (Table 2, "VecAdd"): c[i] = fl32(a[i] + b[i]), one IEEE-754
  *     binary32 addition, round to nearest even, subnormals kept.
+ *   vector multiply (Table 2, "VecMult", 15 iterations there): c[i] =
+ *     fl32(...fl32(fl32(a[i] * b[i]) * b[i]) ... * b[i]) with `iters`
+ *     binary32 multiplications in turn, each rounded to nearest even.
  *   matrix multiply (Table 2, "MM"; Section 6 calls it single precision):
  *     C[i][j] = sum_k A[i][k] * B[k][j], row-major A (M x K), B (K x N),
  *     C (M x N), computed here in binary64 with k = 0 .. K-1 in order.
@@ -28,6 +31,18 @@
 /* Vector add: one binary32 addition per element (Table 2, VecAdd). */
 void oracle_vadd_f32(const float* a, const float* b, float* c, int64_t n) {
   for (int64_t i = 0; i < n; ++i) c[i] = a[i] + b[i];
+}
+
+/*
+ * Vector multiply (Table 2, VecMult): the element is multiplied by b[i]
+ * `iters` times in binary32, one rounding per product.
+ */
+void oracle_vmul_f32(const float* a, const float* b, float* c, int64_t n, int32_t iters) {
+  for (int64_t i = 0; i < n; ++i) {
+    float z = a[i];
+    for (int32_t t = 0; t < iters; ++t) z = z * b[i];
+    c[i] = z;
+  }
 }
 
 /*

@@ -33,6 +33,7 @@ MASK64 = (1 << 64) - 1
 
 TASK_VADD = 1
 TASK_SGEMM = 2
+TASK_VMUL = 3
 
 _CHUNK = 1 << 22
 
@@ -104,6 +105,15 @@ def vadd_inputs(seed: int, n: int) -> tuple[np.ndarray, np.ndarray]:
     return uniform_pm1(seed, n, 0), uniform_pm1(seed, n, n)
 
 
+def vmul_inputs(seed: int, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """Operands of a vector-multiply task: a in [-1, 1) from draws [0, n), and
+    b = 1 + u/4 in [0.75, 1.25) from draws [n, 2n), so that up to 40 repeated
+    products by b stay normal binary32 numbers (0.75**40 > 1e-5, 1.25**40 < 1e4)."""
+    a = uniform_pm1(seed, n, 0)
+    b = (np.float32(1.0) + uniform_pm1(seed, n, n) * np.float32(0.25)).astype(np.float32)
+    return a, b
+
+
 def sgemm_inputs(seed: int, m: int, n: int, k: int) -> tuple[np.ndarray, np.ndarray]:
     """Row-major A (m x k) from stream ``seed`` and B (k x n) from ``seed + 2**32``."""
     a = standard_normal(seed, m * k).reshape(m, k)
@@ -130,22 +140,22 @@ def sgemm_int_inputs(seed: int, m: int, n: int, k: int, lim: int = 16):
 class TaskSpec:
     rank: int
     index: int  # position in the rank's submission order
-    kind: int  # TASK_VADD or TASK_SGEMM
-    n: int = 0  # vector length (VADD) or N (SGEMM)
+    kind: int  # TASK_VADD, TASK_SGEMM or TASK_VMUL
+    n: int = 0  # vector length (VADD, VMUL) or N (SGEMM)
     m: int = 0
-    k: int = 0
+    k: int = 0  # K (SGEMM) or products per element (VMUL)
     seed: int = 0
     arrival_s: float = 0.0  # open-loop arrival time (serving workloads)
 
     @property
     def in_bytes(self) -> int:
-        if self.kind == TASK_VADD:
+        if self.kind in (TASK_VADD, TASK_VMUL):
             return 8 * self.n
         return 4 * (self.m * self.k + self.k * self.n)
 
     @property
     def out_bytes(self) -> int:
-        if self.kind == TASK_VADD:
+        if self.kind in (TASK_VADD, TASK_VMUL):
             return 4 * self.n
         return 4 * self.m * self.n
 
@@ -153,6 +163,8 @@ class TaskSpec:
     def flops(self) -> int:
         if self.kind == TASK_VADD:
             return self.n
+        if self.kind == TASK_VMUL:
+            return self.n * self.k
         return 2 * self.m * self.n * self.k
 
 

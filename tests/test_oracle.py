@@ -78,6 +78,78 @@ def test_vadd_empty():
     assert oracle.vadd(np.zeros(0, np.float32), np.zeros(0, np.float32)).size == 0
 
 
+# ---------------------------------------------------------------- vector multiply
+
+
+def _vmul_by_float64_rounding(a, b, iters):
+    """Each binary32 product is exact in binary64 (24 + 24 bits < 53), so one
+    cast back to binary32 is the single round-to-nearest-even of IEEE-754."""
+    z = a.astype(np.float32)
+    for _ in range(iters):
+        z = (z.astype(np.float64) * b.astype(np.float64)).astype(np.float32)
+    return z
+
+
+@pytest.mark.parametrize("iters", [1, 2, 15, 40])
+def test_vmul_matches_exact_product_rounded_once_per_step(iters):
+    a, b = synth.vmul_inputs(synth.task_seed(2, iters), 40000)
+    assert np.array_equal(f32_bits(oracle.vmul(a, b, iters)), f32_bits(_vmul_by_float64_rounding(a, b, iters)))
+
+
+def test_vmul_one_product_is_numpy_float32_multiply():
+    a, b = synth.vmul_inputs(synth.task_seed(4, 1), 65536)
+    assert np.array_equal(f32_bits(oracle.vmul(a, b, 1)), f32_bits(np.multiply(a, b, dtype=np.float32)))
+
+
+def test_vmul_powers_of_two_closed_form():
+    # b = 2**e: every product is exact, so c = a * 2**(e * iters) exactly.
+    a, _ = synth.vmul_inputs(synth.task_seed(5, 0), 4096)
+    for e, iters in [(1, 15), (-1, 15), (3, 7), (0, 1024)]:
+        b = np.full_like(a, np.float32(2.0 ** e))
+        want = (a.astype(np.float64) * 2.0 ** (e * iters)).astype(np.float32)
+        assert np.array_equal(f32_bits(oracle.vmul(a, b, iters)), f32_bits(want))
+
+
+def test_vmul_small_cases_by_exact_rationals():
+    # Brute force: exact rational product, rounded to the nearest binary32
+    # (ties to even) by search among the two neighbours.
+    a, b = synth.vmul_inputs(synth.task_seed(6, 0), 64)
+    iters = 5
+    got = oracle.vmul(a, b, iters)
+    for i in range(a.size):
+        z = np.float32(a[i])
+        for _ in range(iters):
+            exact = Fraction(float(z)) * Fraction(float(b[i]))
+            lo = np.float32(float(exact))
+            cands = {lo, np.nextafter(lo, np.float32(np.inf)), np.nextafter(lo, np.float32(-np.inf))}
+            best = min(cands, key=lambda c: (abs(Fraction(float(c)) - exact), int(f32_bits(c)) & 1))
+            z = best
+        assert f32_bits(got[i]) == f32_bits(z)
+
+
+def test_vmul_order_is_pinned():
+    # Mutant: a * (b ** iters) with the power taken first; the rounding differs,
+    # so the pins above would catch a wrong product order.
+    a, b = synth.vmul_inputs(synth.task_seed(7, 0), 65536)
+    p = np.ones_like(b)
+    for _ in range(15):
+        p = np.multiply(p, b, dtype=np.float32)
+    mutant = np.multiply(a, p, dtype=np.float32)
+    assert not np.array_equal(f32_bits(mutant), f32_bits(_vmul_by_float64_rounding(a, b, 15)))
+
+
+def test_vmul_empty_and_limits():
+    z = np.zeros(0, np.float32)
+    assert oracle.vmul(z, z, 15).size == 0
+    with pytest.raises(ValueError):
+        oracle.vmul(z, z, 0)
+    a, b = synth.vmul_inputs(synth.task_seed(8, 0), 1 << 16)
+    assert a.min() >= -1.0 and a.max() < 1.0 and b.min() >= 0.75 and b.max() < 1.25
+    c = oracle.vmul(a, b, 40)
+    nz = c[a != 0]
+    assert np.all(np.abs(nz) >= np.float32(2.0 ** -126))  # no subnormal on the recipe
+
+
 # ---------------------------------------------------------------- matrix multiply
 
 
