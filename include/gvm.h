@@ -57,6 +57,9 @@ extern "C" {
 /* ---- task types (Section 6, Table 2) ------------------------------------ */
 #define GVM_TASK_VADD 1   /* c[i] = a[i] + b[i], binary32, n elements */
 #define GVM_TASK_SGEMM 2  /* C = A B, binary32, row-major A (m x k), B (k x n), C (m x n) */
+#define GVM_TASK_VMUL 3   /* c[i] = a[i] * b[i] * ... * b[i] with k binary32 products, each
+                             rounded to nearest (Table 2, VecMul: the I/O-intensive task of
+                             the model validation, 15 iterations), n elements */
 
 /* ---- task flags --------------------------------------------------------- */
 #define GVM_TASK_RESIDENT 1 /* a_off/b_off/c_off address the rank's resident region;
@@ -125,19 +128,21 @@ typedef struct gvm_config {
 } gvm_config;
 
 typedef struct gvm_task {
-  int32_t type;   /* GVM_TASK_VADD or GVM_TASK_SGEMM */
+  int32_t type;   /* GVM_TASK_VADD, GVM_TASK_SGEMM or GVM_TASK_VMUL */
   int32_t flags;  /* 0 or GVM_TASK_RESIDENT */
-  int64_t n;      /* VADD: element count (>= 0). SGEMM: columns of B and C (>= 1) */
+  int64_t n;      /* VADD, VMUL: element count (>= 0). SGEMM: columns of B and C (>= 1) */
   int32_t m;      /* SGEMM: rows of A and C (>= 1) */
-  int32_t k;      /* SGEMM: columns of A, rows of B (>= 1) */
+  int32_t k;      /* SGEMM: columns of A, rows of B (>= 1). VMUL: products per element
+                     (1 .. 1024) */
   /* host mode (flags without GVM_TASK_RESIDENT): page-locked host buffers,
      caller-owned, valid and untouched until gvm_sync returns for this task.
-     VADD: a, b, c hold n floats. SGEMM: a = A (m*k), b = B (k*n), c = C (m*n). */
+     VADD, VMUL: a, b, c hold n floats. SGEMM: a = A (m*k), b = B (k*n), c = C (m*n). */
   const void* a;
   const void* b;
   void* c;
   /* resident mode: byte offsets into the rank's resident region, 16-byte aligned
-     for SGEMM and 4-byte aligned for VADD; operands must lie inside the region. */
+     for SGEMM and 4-byte aligned for VADD and VMUL; operands must lie inside the
+     region. */
   uint64_t a_off;
   uint64_t b_off;
   uint64_t c_off;
@@ -291,6 +296,11 @@ GVM_API const char* gvm_strerror(int code);
 /* c = a + b, n binary32 elements (Table 2, VecAdd). Device pointers; any
    alignment; n >= 0. Returns GVM_EINVAL for n < 0 or NULL with n > 0. */
 GVM_API int gvm_vadd_f32(const float* a, const float* b, float* c, int64_t n, void* stream);
+
+/* VMUL alone: c[i] = a[i] * b[i]^iters (iters binary32 products, each rounded
+   to nearest), n elements, device pointers, on stream (cudaStream_t or NULL).
+   GVM_EINVAL for n < 0, iters outside 1 .. 1024 or NULL pointers. */
+GVM_API int gvm_vmul_f32(const float* a, const float* b, float* c, int64_t n, int32_t iters, void* stream);
 
 /* Scratch bytes gvm_sgemm_f32 needs for (m, n, k, path): 0 for the FMA path;
    for split3 the bf16 hi/lo copies of A (m x kp) and of B transposed

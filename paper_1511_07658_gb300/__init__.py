@@ -44,12 +44,13 @@ from ._abi import (  # noqa: E402
     lib,
     lib_path,
 )
-from .manager import Manager, Rank, sgemm_f32, sgemm_scratch_bytes, vadd_f32  # noqa: E402
+from .manager import Manager, Rank, sgemm_f32, sgemm_scratch_bytes, vadd_f32, vmul_f32  # noqa: E402
 
 __all__ = [
     "Manager",
     "Rank",
     "vadd_f32",
+    "vmul_f32",
     "sgemm_f32",
     "sgemm_scratch_bytes",
     "lib",

@@ -22,6 +22,7 @@ GVM_ENODEV = -9
 
 GVM_TASK_VADD = 1
 GVM_TASK_SGEMM = 2
+GVM_TASK_VMUL = 3
 GVM_TASK_RESIDENT = 1
 GVM_SGEMM_FMA = 0
 GVM_SGEMM_SPLIT3 = 1
@@ -121,6 +122,7 @@ PROTOTYPES = {
     ),
     "gvm_strerror": (c_char_p, [c_int]),
     "gvm_vadd_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
+    "gvm_vmul_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p]),
     "gvm_sgemm_scratch_bytes": (c_uint64, [c_int32, c_int32, c_int32, c_int32]),
     "gvm_sgemm_f32": (
         c_int,

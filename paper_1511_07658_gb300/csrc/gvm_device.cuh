@@ -2,6 +2,7 @@
 // kernels: PTX wrappers, and one function per tile kind.
 //
 //   vadd_range   vector-add task (Table 2, VecAdd): c = a + b, binary32
+//   vmul_range   vector-multiply task (Table 2, VecMul): iterated binary32 products
 //   fma_tile     matrix-multiply task (Table 2, MM) on the CUDA cores
 //   split_*      split3 pre-pass: x -> (hi, lo) bf16 pair, x = hi + lo + r
 //   tc_tile      split3 product AhBh + AhBl + AlBh on tcgen05 tensor cores,
@@ -216,10 +217,26 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
 
 // ---------------------------------------------------------------- vector add
 
-// c[i] = a[i] + b[i] for lo <= i < hi, by threads tid = 0 .. nthr-1 of the
-// CTA (the scheduler leaves warp 0 out to find the next tile meanwhile).
-__device__ __forceinline__ void vadd_range(const float* __restrict__ a, const float* __restrict__ b,
-                                           float* __restrict__ c, int64_t lo, int64_t hi, int tid, int nthr) {
+// Elementwise tasks over [lo, hi), by threads tid = 0 .. nthr-1 (a CTA's
+// share of one tile): float4 streaming loads (evict-first), 4 in flight per
+// thread, scalar head/tail when the operands are not 16-byte aligned there.
+//   ELEM_ADD: c[i] = a[i] + b[i]                     (Table 2, VecAdd)
+//   ELEM_MUL: c[i] = (...((a[i] * b[i]) * b[i])...) * b[i], `iters` products
+//             (Table 2, VecMul: 15 iterations), each rounded to nearest
+enum : int { kElemAdd = 0, kElemMul = 1 };
+
+template <int OP>
+__device__ __forceinline__ float elem_op(float x, float y, int iters) {
+  if (OP == kElemAdd) return __fadd_rn(x, y);
+  float z = x;
+  for (int i = 0; i < iters; ++i) z = __fmul_rn(z, y);
+  return z;
+}
+
+template <int OP>
+__device__ __forceinline__ void elementwise_range(const float* __restrict__ a, const float* __restrict__ b,
+                                                  float* __restrict__ c, int64_t lo, int64_t hi, int tid, int nthr,
+                                                  int iters) {
   const bool vec = ((reinterpret_cast<uintptr_t>(a + lo) | reinterpret_cast<uintptr_t>(b + lo) |
                      reinterpret_cast<uintptr_t>(c + lo)) &
                     15) == 0;
@@ -241,25 +258,35 @@ __device__ __forceinline__ void vadd_range(const float* __restrict__ a, const fl
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         float4 z;
-        z.x = __fadd_rn(x[u].x, y[u].x);
-        z.y = __fadd_rn(x[u].y, y[u].y);
-        z.z = __fadd_rn(x[u].z, y[u].z);
-        z.w = __fadd_rn(x[u].w, y[u].w);
+        z.x = elem_op<OP>(x[u].x, y[u].x, iters);
+        z.y = elem_op<OP>(x[u].y, y[u].y, iters);
+        z.z = elem_op<OP>(x[u].z, y[u].z, iters);
+        z.w = elem_op<OP>(x[u].w, y[u].w, iters);
         __stcs(c4 + i + u * nthr, z);
       }
     }
     for (; i < nv; i += nthr) {
       const float4 x = __ldcs(a4 + i), y = __ldcs(b4 + i);
       float4 z;
-      z.x = __fadd_rn(x.x, y.x);
-      z.y = __fadd_rn(x.y, y.y);
-      z.z = __fadd_rn(x.z, y.z);
-      z.w = __fadd_rn(x.w, y.w);
+      z.x = elem_op<OP>(x.x, y.x, iters);
+      z.y = elem_op<OP>(x.y, y.y, iters);
+      z.z = elem_op<OP>(x.z, y.z, iters);
+      z.w = elem_op<OP>(x.w, y.w, iters);
       __stcs(c4 + i, z);
     }
     done = lo + (nv << 2);
   }
-  for (int64_t i = done + tid; i < hi; i += nthr) c[i] = __fadd_rn(a[i], b[i]);
+  for (int64_t i = done + tid; i < hi; i += nthr) c[i] = elem_op<OP>(a[i], b[i], iters);
+}
+
+__device__ __forceinline__ void vadd_range(const float* __restrict__ a, const float* __restrict__ b,
+                                           float* __restrict__ c, int64_t lo, int64_t hi, int tid, int nthr) {
+  elementwise_range<kElemAdd>(a, b, c, lo, hi, tid, nthr, 0);
+}
+__device__ __forceinline__ void vmul_range(const float* __restrict__ a, const float* __restrict__ b,
+                                           float* __restrict__ c, int64_t lo, int64_t hi, int tid, int nthr,
+                                           int iters) {
+  elementwise_range<kElemMul>(a, b, c, lo, hi, tid, nthr, iters);
 }
 
 // ---------------------------------------------------------------- FMA SGEMM

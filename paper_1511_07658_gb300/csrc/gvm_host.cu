@@ -511,8 +511,9 @@ int prep_task(gvm_rank* r, const gvm_task* t, Prep* p) {
   const bool resident = (t->flags & GVM_TASK_RESIDENT) != 0;
   if (t->flags & ~GVM_TASK_RESIDENT) return GVM_EINVAL;
   uint64_t bytes_a = 0, bytes_b = 0, bytes_c = 0;
-  if (t->type == GVM_TASK_VADD) {
+  if (t->type == GVM_TASK_VADD || t->type == GVM_TASK_VMUL) {
     if (t->n < 0 || t->n > (int64_t(1) << 34)) return GVM_EINVAL;
+    if (t->type == GVM_TASK_VMUL && (t->k < 1 || t->k > 1024)) return GVM_EINVAL;
     bytes_a = bytes_b = bytes_c = 4ull * (uint64_t)t->n;
   } else if (t->type == GVM_TASK_SGEMM) {
     if (t->m < 1 || t->k < 1 || t->n < 1 || t->m > 32768 || t->k > 32768 || t->n > 32768) return GVM_EINVAL;
@@ -524,7 +525,7 @@ int prep_task(gvm_rank* r, const gvm_task* t, Prep* p) {
   }
   const uint64_t res_bytes = r->ring_base - r->slice;
   if (resident) {
-    const uint64_t al = t->type == GVM_TASK_SGEMM ? 16 : 4;
+    const uint64_t al = t->type == GVM_TASK_SGEMM ? 16 : 4;  // VADD, VMUL: 4
     const uint64_t offs[3] = {t->a_off, t->b_off, t->c_off};
     const uint64_t lens[3] = {bytes_a, bytes_b, bytes_c};
     for (int i = 0; i < 3; ++i) {
@@ -568,8 +569,9 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
   body->a = da;
   body->b = db;
   body->c = dc;
-  if (t->type == GVM_TASK_VADD) {
+  if (t->type == GVM_TASK_VADD || t->type == GVM_TASK_VMUL) {
     body->n = t->n;
+    body->k = t->type == GVM_TASK_VMUL ? t->k : 0;  // products per element
     int64_t vt = ctx->cfg.vadd_tile;
     if (vt == 0) {
       vt = (t->n + ctx->grid - 1) / std::max(ctx->grid, 1);

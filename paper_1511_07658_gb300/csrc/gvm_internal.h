@@ -24,7 +24,7 @@ constexpr int kProfSlots = 12;        // per-launch phase counters (see kProf*)
 constexpr uint32_t kTcStageBytes = (2u * kTcM + 2u * kTcN) * kTcBK * 2u;
 
 // ---- task kinds, phases, flags ---------------------------------------------
-enum : uint32_t { kTaskVadd = 1, kTaskSgemm = 2 };
+enum : uint32_t { kTaskVadd = 1, kTaskSgemm = 2, kTaskVmul = 3 };
 enum : uint32_t { kPhaseSplit = 0, kPhaseMain = 1 };
 enum : uint32_t {
   kFlagNeedsReady = 1u,   // host-mode inputs: wait for the input stream's ready word

@@ -24,6 +24,13 @@ __global__ void __launch_bounds__(kThreads) vadd_kernel(const float* a, const fl
   vadd_range(a, b, c, lo, min(n, lo + chunk), threadIdx.x, kThreads);
 }
 
+__global__ void __launch_bounds__(kThreads) vmul_kernel(const float* a, const float* b, float* c, int64_t n,
+                                                        int64_t chunk, int iters) {
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  if (lo >= n) return;
+  vmul_range(a, b, c, lo, min(n, lo + chunk), threadIdx.x, kThreads, iters);
+}
+
 __global__ void __launch_bounds__(kThreads, 2) fma_sgemm_kernel(const float* A, const float* B, float* C, int m,
                                                                  int n, int k) {
   extern __shared__ uint8_t dyn_smem[];
@@ -256,6 +263,20 @@ extern "C" int gvm_vadd_f32(const float* a, const float* b, float* c, int64_t n,
   if (chunk < kVaddTileMin) chunk = kVaddTileMin;
   const int64_t grid = (n + chunk - 1) / chunk;
   vadd_kernel<<<(unsigned)grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(a, b, c, n, chunk);
+  return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
+}
+
+extern "C" int gvm_vmul_f32(const float* a, const float* b, float* c, int64_t n, int32_t iters, void* stream) {
+  if (n < 0 || iters < 1 || iters > 1024) return GVM_EINVAL;
+  if (n == 0) return GVM_OK;
+  if (!a || !b || !c) return GVM_EINVAL;
+  const int sms = sm_count();
+  if (sms <= 0) return GVM_ENODEV;
+  int64_t chunk = (n + (int64_t)sms * 4 - 1) / ((int64_t)sms * 4);
+  chunk = (chunk + 1023) / 1024 * 1024;
+  if (chunk < kVaddTileMin) chunk = kVaddTileMin;
+  const int64_t grid = (n + chunk - 1) / chunk;
+  vmul_kernel<<<(unsigned)grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(a, b, c, n, chunk, iters);
   return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
 }
 

@@ -549,14 +549,17 @@ __global__ void __launch_bounds__(kThreads, 2) sched_fma_kernel(const SchedParam
     int bucket = kProfVadd;
     bool early = false;  // warp 0 claims the next tile while this one runs
 
-    if (b.type == kTaskVadd) {
+    if (b.type == kTaskVadd || b.type == kTaskVmul) {
       const int64_t lo = (int64_t)tile * b.vadd_tile;
       const int64_t hi = min(b.n, lo + b.vadd_tile);
       if (warp == 0) {
         claim(nxt, false);
-      } else {
+      } else if (b.type == kTaskVadd) {
         vadd_range(reinterpret_cast<const float*>(b.a), reinterpret_cast<const float*>(b.b),
                    reinterpret_cast<float*>(b.c), lo, hi, tid - 32, kThreads - 32);
+      } else {
+        vmul_range(reinterpret_cast<const float*>(b.a), reinterpret_cast<const float*>(b.b),
+                   reinterpret_cast<float*>(b.c), lo, hi, tid - 32, kThreads - 32, b.k);
       }
       early = true;
     } else {
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 2) sched_fma_kernel(const SchedParam
 // barriers, so the next tile's claim, staging and MMAs overlap this one's.
 
 constexpr int kFzItems = 4;
-constexpr uint32_t kItemExit = 0, kItemNop = 3;  // besides kTaskVadd, kTaskSgemm
+constexpr uint32_t kItemExit = 0, kItemNop = 0xffu;  // besides the task types
 constexpr int kFinSlots = 16;  // per-item finish counters (items in flight < 16)
 
 // A staged GEMM tile whose accumulator is not drained yet.
@@ -619,7 +622,7 @@ struct FzPend {
 };
 
 struct FzItem {
-  uint32_t kind;  // kItemExit, kTaskVadd, kTaskSgemm or kItemNop
+  uint32_t kind;  // kItemExit, kItemNop or a task type (kTaskVadd, kTaskSgemm, kTaskVmul)
   uint32_t task;
   uint32_t tile;
   uint32_t tag;
@@ -852,8 +855,9 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
         has_drain = true;
         ++tile_no;
         if (tid == 0) sh.prof[kProfGemm] += globaltimer() - t0;
-      } else {
+      } else {  // vector add or vector multiply
         const uint32_t task = item.task, ntiles = item.ntiles, tag = item.tag, flags = item.flags;
+        const int iters = item.k;
         const int64_t lo = (int64_t)item.tile * item.vadd_tile;
         const int64_t hi = min(item.n, lo + item.vadd_tile);
         const float* a = reinterpret_cast<const float*>(item.a);
@@ -863,7 +867,8 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
         if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
         ok = flush();
         if (ok) {
-          vadd_range(a, b, c, lo, hi, tid, kFzConvThreads);
+          if (kind == kTaskVmul) vmul_range(a, b, c, lo, hi, tid, kFzConvThreads, iters);
+          else vadd_range(a, b, c, lo, hi, tid, kFzConvThreads);
           conv_item_done(p, sh, seq, task, ntiles, tag, flags);
         }
         if (tid == 0) sh.prof[kProfVadd] += globaltimer() - t0;

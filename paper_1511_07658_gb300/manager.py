@@ -26,6 +26,7 @@ from ._abi import (
     GVM_TASK_RESIDENT,
     GVM_TASK_SGEMM,
     GVM_TASK_VADD,
+    GVM_TASK_VMUL,
     GvmConfig,
     GvmStats,
     GvmTask,
@@ -143,6 +144,16 @@ class Rank:
         t.a, t.b, t.c = _ptr(a), _ptr(b), _ptr(c)
         return self.submit(t, block)
 
+    def submit_vmul(self, a: torch.Tensor, b: torch.Tensor, c: torch.Tensor, iters: int, block: bool = True) -> int:
+        """Host mode: c = a * b * ... * b with `iters` float32 products per element."""
+        t = GvmTask()
+        t.type = GVM_TASK_VMUL
+        t.flags = 0
+        t.n = a.numel()
+        t.k = iters
+        t.a, t.b, t.c = _ptr(a), _ptr(b), _ptr(c)
+        return self.submit(t, block)
+
     def submit_sgemm(self, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, block: bool = True) -> int:
         """Host mode: pinned float32 host tensors A (m x k), B (k x n), C (m x n)."""
         t = GvmTask()
@@ -158,6 +169,14 @@ class Rank:
         t.type = GVM_TASK_VADD
         t.flags = GVM_TASK_RESIDENT
         t.n = n
+        t.a_off, t.b_off, t.c_off = a_off, b_off, c_off
+        return self.submit(t, block)
+
+    def submit_vmul_resident(self, a_off: int, b_off: int, c_off: int, n: int, iters: int, block: bool = True) -> int:
+        t = GvmTask()
+        t.type = GVM_TASK_VMUL
+        t.flags = GVM_TASK_RESIDENT
+        t.n, t.k = n, iters
         t.a_off, t.b_off, t.c_off = a_off, b_off, c_off
         return self.submit(t, block)
 
@@ -346,6 +365,13 @@ class Manager:
 def vadd_f32(a: torch.Tensor, b: torch.Tensor, c: torch.Tensor, stream=None) -> None:
     """c = a + b on the device (the vector-add task kernel alone)."""
     check(lib().gvm_vadd_f32(_ptr(a), _ptr(b), _ptr(c), a.numel(), _stream_handle(stream)), "gvm_vadd_f32")
+
+
+def vmul_f32(a: torch.Tensor, b: torch.Tensor, c: torch.Tensor, iters: int, stream=None) -> None:
+    """c = a * b * ... * b (`iters` float32 products) on the device (the vector-multiply task kernel alone)."""
+    check(
+        lib().gvm_vmul_f32(_ptr(a), _ptr(b), _ptr(c), a.numel(), iters, _stream_handle(stream)), "gvm_vmul_f32"
+    )
 
 
 def sgemm_scratch_bytes(m: int, n: int, k: int, path: str = "split3") -> int:

@@ -1,5 +1,6 @@
-"""Parity of the task kernels alone (gvm_vadd_f32, gvm_sgemm_f32) against the
-CPU oracle, through the C ABI. Vector add: bit-exact. SGEMM: relative
+"""Parity of the task kernels alone (gvm_vadd_f32, gvm_vmul_f32,
+gvm_sgemm_f32) against the CPU oracle, through the C ABI. Vector add and
+vector multiply: bit-exact. SGEMM: relative
 Frobenius error <= 1e-5 against the binary64 oracle, and exact on integer
 operands whose products and sums are exact in both arithmetics."""
 import numpy as np
@@ -62,6 +63,39 @@ def test_vadd_ieee_cases(gvm, golden):
     gvm.vadd_f32(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), tc)
     torch.cuda.synchronize()
     assert np.array_equal(bits(tc.cpu().numpy()), want)
+
+
+@pytest.mark.parametrize("n,iters", [(0, 15), (1, 1), (4097, 15), (65536 + 3, 2), ((1 << 22) + 5, 15), (70001, 1024)])
+def test_vmul_bitexact(gvm, n, iters):
+    a, b = synth.vmul_inputs(synth.task_seed(9, n % 1000), n)
+    if iters > 40:  # keep long products normal: b = 1 +- 2**-10
+        b = (np.float32(1.0) + (b - np.float32(1.0)) * np.float32(2.0 ** -8)).astype(np.float32)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    tc = torch.full_like(ta, float("nan"))
+    gvm.vmul_f32(ta, tb, tc, iters)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(tc.cpu().numpy()), bits(oracle.vmul(a, b, iters)))
+
+
+@pytest.mark.parametrize("shift", [1, 3])
+def test_vmul_misaligned(gvm, shift):
+    n = 100003
+    a, b = synth.vmul_inputs(98, n + 8)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    tc = torch.zeros(n + 8, device="cuda")
+    gvm.vmul_f32(ta[shift : shift + n], tb[(shift + 1) % 4 : (shift + 1) % 4 + n], tc[shift : shift + n], 15)
+    torch.cuda.synchronize()
+    want = oracle.vmul(a[shift : shift + n], b[(shift + 1) % 4 : (shift + 1) % 4 + n], 15)
+    got = tc.cpu().numpy()
+    assert np.array_equal(bits(got[shift : shift + n]), bits(want))
+    assert np.all(got[:shift] == 0) and np.all(got[shift + n :] == 0)
+
+
+def test_vmul_rejects_bad_iters(gvm):
+    t = torch.zeros(16, device="cuda")
+    for iters in (0, 1025):
+        with pytest.raises(RuntimeError):
+            gvm.vmul_f32(t, t, t, iters)
 
 
 SHAPES = [

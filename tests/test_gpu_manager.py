@@ -42,6 +42,11 @@ def submit_spec(rk, spec):
         out = torch.empty(spec.n, dtype=torch.float32).pin_memory()
         seq = rk.submit_vadd(pinned(a), pinned(b), out)
         return seq, (a, b), out
+    if spec.kind == synth.TASK_VMUL:
+        a, b = synth.vmul_inputs(spec.seed, spec.n)
+        out = torch.empty(spec.n, dtype=torch.float32).pin_memory()
+        seq = rk.submit_vmul(pinned(a), pinned(b), out, spec.k)
+        return seq, (a, b), out
     A, B = synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
     out = torch.empty(spec.m, spec.n, dtype=torch.float32).pin_memory()
     tA, tB = pinned(A), pinned(B)
@@ -52,6 +57,8 @@ def submit_spec(rk, spec):
 def check_result(spec, inputs, out):
     if spec.kind == synth.TASK_VADD:
         assert np.array_equal(bits(out.numpy()), bits(oracle.vadd(*inputs))), spec
+    elif spec.kind == synth.TASK_VMUL:
+        assert np.array_equal(bits(out.numpy()), bits(oracle.vmul(*inputs, spec.k))), spec
     else:
         err = oracle.rel_fro_err(out.numpy(), oracle.sgemm64(inputs[0], inputs[1]))
         assert err <= SGEMM_TOL, (spec, err)
@@ -101,6 +108,45 @@ def test_mixed_ragged_tasks(gvm, path):
                 w.tasks.append(synth.TaskSpec(r, t, synth.TASK_SGEMM, m=m, n=n, k=k, seed=2000 + i))
             i += 1
     run_workload(gvm, w, path=path, depth=8)
+
+
+@pytest.mark.parametrize("mode", ["barrier", "continuous"])
+@pytest.mark.parametrize("path", ["fma", "split3"])
+def test_vmul_tasks_in_mix(gvm, mode, path):
+    """Vector-multiply tasks (the paper's VecMult, 15 products) shared with
+    vector adds and matrix multiplies, ragged lengths, host mode."""
+    w = synth.Workload("vmul-mix", 4)
+    i = 0
+    for r in range(4):
+        for t in range(5):
+            kind = (r + t) % 3
+            if kind == 0:
+                w.tasks.append(synth.TaskSpec(r, t, synth.TASK_VMUL, n=[0, 3, 70001, 1 << 20][i % 4], k=[15, 1, 15, 40][i % 4], seed=3000 + i))
+            elif kind == 1:
+                w.tasks.append(synth.TaskSpec(r, t, synth.TASK_VADD, n=33333 + i, seed=4000 + i))
+            else:
+                w.tasks.append(synth.TaskSpec(r, t, synth.TASK_SGEMM, m=130, n=257, k=65, seed=5000 + i))
+            i += 1
+    run_workload(gvm, w, mode=mode, path=path, depth=8)
+
+
+def test_vmul_resident_and_bad_iters(gvm):
+    n = 50001
+    a, b = synth.vmul_inputs(synth.task_seed(1, 2), n)
+    with gvm.Manager(1, ring_depth=4, slice_bytes=16 << 20, resident_bytes=12 * 65536) as mgr:
+        rk = mgr.attach(0)
+        rk.write(0, torch.from_numpy(a))
+        rk.write(4 * 65536, torch.from_numpy(b))
+        seq = rk.submit_vmul_resident(0, 4 * 65536, 8 * 65536, n, 15)
+        mgr.flush()
+        rk.sync(seq)
+        c = torch.empty(n)
+        rk.read(8 * 65536, c)
+        assert np.array_equal(bits(c.numpy()), bits(oracle.vmul(a, b, 15)))
+        for iters in (0, 1025):
+            with pytest.raises(RuntimeError):
+                rk.submit_vmul_resident(0, 4 * 65536, 8 * 65536, n, iters)
+        assert mgr.stats()["device_status"] == 0
 
 
 @pytest.mark.parametrize("path", ["fma", "split3"])
