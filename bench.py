@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--plain", action="store_true", help="also time the plain one-context-per-rank form")
     p.add_argument("--model", action="store_true", help="also check timings against Eqs. 1, 2 and 7")
+    p.add_argument("--paper-modes", action="store_true",
+                   help="also run the workload in the paper's host-issued PS-1 / PS-2 modes")
     p.add_argument("--quantum", type=int, default=8)
     p.add_argument("--harness", choices=["native", "python"], default="native",
                    help="rank threads: native (gvm_spmd_run) or Python threads calling the API")
@@ -263,6 +265,37 @@ def run_step(mgr, ranks, arrays, pool, record=True):
 
 
 HOST_TIMES = []  # per step: (submit, flush, sync) host seconds
+
+
+def paper_modes_check(args, g, w, slice_bytes, resident, res_arrays, host_arrays, host, res_offs, tasks_per_step):
+    """The same workload through the same API in the paper's own mechanism
+    (GVM_MODE_PS1 / GVM_MODE_PS2: the manager's host thread issues every
+    task's copies and kernel on its rank's stream at the request barrier;
+    Sections 4.2.1 and 5) instead of the persistent scheduler: tasks/s with
+    device-resident operands (host clock around each native SPMD step) and
+    end to end from the same pinned host buffers."""
+    R = w.ranks
+    per_rank = len(w.tasks) // R
+    out = {}
+    for mode in ("ps1", "ps2"):
+        mgr = g.Manager(R, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode=mode, sgemm_path=args.path,
+                        slice_bytes=slice_bytes, resident_bytes=resident)
+        ranks = [mgr.attach(r) for r in range(R)]
+        for spec in w.tasks:
+            ta, tb, _ = host[(spec.rank, spec.index)]
+            oa, ob, _ = res_offs[(spec.rank, spec.index)]
+            ranks[spec.rank].write(oa, ta)
+            ranks[spec.rank].write(ob, tb)
+        row = {}
+        for leg, arrays in (("value", res_arrays), ("e2e", host_arrays)):
+            mgr.spmd_run(ranks, arrays, max(1, args.warmup))
+            steps = args.steps if leg == "value" else max(3, args.steps // 2)
+            _, _, hst = mgr.spmd_run(ranks, arrays, steps)
+            row[leg] = tasks_per_step * steps / (sum(hst) / 1e3)
+        row["kernel_launches_per_step"] = tasks_per_step
+        out[mode] = row
+        mgr.shutdown()
+    return out
 
 
 def gpu_arm(args, w, desc, rank, world):
@@ -505,6 +538,10 @@ def gpu_arm(args, w, desc, rank, world):
 
     mgr.shutdown()
     pool.shutdown()
+    paper_modes = None
+    if args.paper_modes and not cont:
+        paper_modes = paper_modes_check(args, g, w, slice_bytes, resident, res_arrays, host_arrays, host, res_offs,
+                                        tasks_per_step)
     pk, pk_kind = peaks()
     kmean = statistics.mean(t_kernel)
     if w.tasks[0].kind == synth.TASK_SGEMM:
@@ -565,6 +602,8 @@ def gpu_arm(args, w, desc, rank, world):
         "parity_spot_rel_err": max(spot) if spot else None,
         "manager_stats": {k: stats_after_value[k] for k in ("launches", "staged_peak", "device_status")},
     }
+    if paper_modes is not None:
+        out["paper_modes"] = paper_modes
     return out
 
 

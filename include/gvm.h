@@ -88,13 +88,24 @@ extern "C" {
                                  so a device-wide synchronisation in the process
                                  (cudaDeviceSynchronize, cudaFree, cudaFreeHost) waits
                                  until gvm_shutdown */
+/* The paper's own mechanism (Sections 4.2.1 and 5): no persistent scheduler.
+   gvm_flush is the request barrier; it issues every task submitted before it
+   on its rank's stream (the input stream of gvm_stream) as separate copies of
+   each operand and one launch of the task's kernel (gvm_vadd_f32,
+   gvm_vmul_f32, or gvm_sgemm_f32 on the manager's SGEMM path), followed by the
+   completion word. Submission only validates and stages. */
+#define GVM_MODE_PS1 2 /* programming style 1: all ranks' input copies, then all
+                          kernels, then all output copies (Eq. 2 / Eq. 4) */
+#define GVM_MODE_PS2 3 /* programming style 2: rank by rank, each task's input,
+                          kernel and output in turn (Eq. 3 / Eqs. 5-7) */
 
 #define GVM_MAX_RANKS 1024
 
 typedef struct gvm_config {
   int32_t max_ranks;      /* ranks that may attach: 1 .. GVM_MAX_RANKS */
   int32_t ring_depth;     /* task descriptors per rank; power of two, 2 .. 4096 */
-  int32_t mode;           /* GVM_MODE_BARRIER or GVM_MODE_CONTINUOUS */
+  int32_t mode;           /* GVM_MODE_BARRIER, GVM_MODE_CONTINUOUS, GVM_MODE_PS1 or
+                             GVM_MODE_PS2 */
   int32_t sgemm_path;     /* GVM_SGEMM_FMA or GVM_SGEMM_SPLIT3 */
   void* arena;            /* caller-owned device memory, 256-byte aligned. Split into
                              max_ranks equal slices (Section 5: one memory object per
@@ -212,8 +223,9 @@ GVM_API int gvm_submit_many(gvm_rank* rank, const gvm_task* tasks, uint32_t coun
    is complete and, in host mode, its output is in the host buffer. Results
    become visible to the rank in sequence order (Section 4.2.3 keeps the
    process order). GVM_ETIMEDOUT after wait_timeout_ns without progress,
-   GVM_EDEVICE if the scheduler reported an error, GVM_EINVAL if seq was never
-   issued. */
+   GVM_EDEVICE if the scheduler (or, in PS-1/PS-2 mode, the rank's stream)
+   reported an error, GVM_EINVAL if seq was never issued, GVM_ESTATE in
+   barrier, PS-1 or PS-2 mode if seq was submitted after the last gvm_flush. */
 GVM_API int gvm_sync(gvm_rank* rank, uint64_t seq);
 
 /* Non-blocking completion test: 1 if task seq is complete, 0 if not, or a
@@ -226,7 +238,10 @@ GVM_API int gvm_poll(gvm_rank* rank, uint64_t seq);
    the next flush. Continuous mode: nothing to do. Returns without waiting.
    Output copies of host-mode tasks are enqueued only after the launch that
    produces them (by gvm_sync / gvm_poll of the owning rank), so a stream wait
-   never sits ahead of its producer in a shared hardware queue. */
+   never sits ahead of its producer in a shared hardware queue.
+   GVM_MODE_PS1 / GVM_MODE_PS2: enqueues, in the style's order, the copies,
+   kernel launches and completion words of every task submitted before this
+   call (as in barrier mode, later tasks wait for the next flush). */
 GVM_API int gvm_flush(gvm_ctx* ctx);
 
 /* Waits until the scheduler kernel and all copy streams are idle. */
@@ -248,8 +263,9 @@ GVM_API void* gvm_stream(gvm_ctx* ctx, int32_t which);
    with their own kernels or copies), or NULL for a bad handle. */
 GVM_API void* gvm_rank_resident_ptr(gvm_rank* rank);
 
-/* RLS(): waits for the rank's tasks, then releases the rank. Barrier mode:
-   GVM_ESTATE if some task was submitted after the last gvm_flush. */
+/* RLS(): waits for the rank's tasks, then releases the rank. Barrier, PS-1
+   and PS-2 modes: GVM_ESTATE if some task was submitted after the last
+   gvm_flush. */
 GVM_API int gvm_detach(gvm_rank* rank);
 
 /* Stops the scheduler after in-flight work, waits for the streams, frees the

@@ -30,6 +30,8 @@ GVM_SGEMM_SPLIT3_FUSED = 2
 GVM_SGEMM_SPLIT3_PAIR = 3
 GVM_MODE_BARRIER = 0
 GVM_MODE_CONTINUOUS = 1
+GVM_MODE_PS1 = 2
+GVM_MODE_PS2 = 3
 
 
 class GvmConfig(ctypes.Structure):

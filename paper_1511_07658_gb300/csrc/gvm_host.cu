@@ -42,6 +42,11 @@ struct SlotInfo {
   uint64_t c_dev = 0;
   uint64_t c_bytes = 0;
   bool needs_out = false;
+  // PS-1 / PS-2 modes: the task's own input copies, issued by gvm_flush.
+  const void* a_host = nullptr;
+  const void* b_host = nullptr;
+  uint64_t a_dev = 0, b_dev = 0, a_bytes = 0, b_bytes = 0;
+  bool host_io = false;
 };
 
 inline uint32_t tag_of(uint64_t seq) { return (uint32_t)(seq + 1); }
@@ -125,10 +130,20 @@ bool cfg_valid(const gvm_config* c) {
   if (!c) return false;
   if (c->max_ranks < 1 || c->max_ranks > GVM_MAX_RANKS) return false;
   if (c->ring_depth < 2 || c->ring_depth > 4096 || (c->ring_depth & (c->ring_depth - 1))) return false;
-  if (c->mode != GVM_MODE_BARRIER && c->mode != GVM_MODE_CONTINUOUS) return false;
+  if (c->mode != GVM_MODE_BARRIER && c->mode != GVM_MODE_CONTINUOUS && c->mode != GVM_MODE_PS1 &&
+      c->mode != GVM_MODE_PS2)
+    return false;
   if (c->sgemm_path != GVM_SGEMM_FMA && c->sgemm_path != GVM_SGEMM_SPLIT3) return false;
   return true;
 }
+
+// PS-1 / PS-2: the host issues each task's copies and kernel (no scheduler).
+inline bool stream_mode(const gvm_ctx* ctx) {
+  return ctx->cfg.mode == GVM_MODE_PS1 || ctx->cfg.mode == GVM_MODE_PS2;
+}
+
+// Modes in which a task runs only after a gvm_flush that follows it.
+inline bool flush_mode(const gvm_ctx* ctx) { return ctx->cfg.mode != GVM_MODE_CONTINUOUS; }
 
 int cuda_err(cudaError_t e) {
   if (e == cudaSuccess) return GVM_OK;
@@ -302,6 +317,102 @@ int wait_scheduler(gvm_ctx* ctx) {
           (unsigned long long)c.published_tiles, (unsigned long long)c.next_tile, (unsigned long long)c.cursor,
           ld_acq(&ctx->shared->status));
   return GVM_ETIMEDOUT;
+}
+
+// ---- PS-1 / PS-2 (Section 4.2.1): the host issues every task's own work.
+
+// Input copies of task s, one per operand, on the rank's stream.
+int ps_issue_in(gvm_rank* r, uint64_t s) {
+  gvm_ctx* ctx = r->ctx;
+  const SlotInfo& si = r->slots[s & (uint64_t)(ctx->cfg.ring_depth - 1)];
+  if (!si.host_io) return GVM_OK;
+  if (si.a_bytes && cudaMemcpyAsync(reinterpret_cast<void*>(si.a_dev), si.a_host, si.a_bytes,
+                                    cudaMemcpyHostToDevice, r->in_stream) != cudaSuccess)
+    return GVM_EDEVICE;
+  if (si.b_bytes && cudaMemcpyAsync(reinterpret_cast<void*>(si.b_dev), si.b_host, si.b_bytes,
+                                    cudaMemcpyHostToDevice, r->in_stream) != cudaSuccess)
+    return GVM_EDEVICE;
+  ctx->h2d.fetch_add(si.a_bytes + si.b_bytes);
+  return GVM_OK;
+}
+
+// The task's kernel, launched alone on the rank's stream.
+int ps_issue_comp(gvm_rank* r, uint64_t s) {
+  gvm_ctx* ctx = r->ctx;
+  const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
+  const TaskBody& b = ctx->descs[(uint32_t)r->id * D + (uint32_t)(s & (D - 1))];
+  const float* A = reinterpret_cast<const float*>(b.a);
+  const float* B = reinterpret_cast<const float*>(b.b);
+  float* C = reinterpret_cast<float*>(b.c);
+  int rc = GVM_OK;
+  if (b.type == kTaskVadd) {
+    if (b.n == 0) return GVM_OK;
+    rc = gvm_vadd_f32(A, B, C, b.n, r->in_stream);
+  } else if (b.type == kTaskVmul) {
+    if (b.n == 0) return GVM_OK;
+    rc = gvm_vmul_f32(A, B, C, b.n, b.k, r->in_stream);
+  } else {
+    // The fused split3 form needs no scratch and computes the same tiles as
+    // the scheduler's split3 path.
+    const int path = ctx->path == kPathSplit3 ? GVM_SGEMM_SPLIT3_FUSED : GVM_SGEMM_FMA;
+    rc = gvm_sgemm_f32(A, B, C, b.m, (int32_t)b.n, b.k, path, nullptr, 0, r->in_stream);
+  }
+  if (rc == GVM_OK) ctx->launches.fetch_add(1);
+  return rc;
+}
+
+// Output copy of task s, then its completion word.
+int ps_issue_out(gvm_rank* r, uint64_t s) {
+  gvm_ctx* ctx = r->ctx;
+  const uint32_t D = (uint32_t)ctx->cfg.ring_depth;
+  const SlotInfo& si = r->slots[s & (D - 1)];
+  if (si.host_io && si.c_bytes) {
+    if (cudaMemcpyAsync(si.c_host, reinterpret_cast<const void*>(si.c_dev), si.c_bytes, cudaMemcpyDeviceToHost,
+                        r->in_stream) != cudaSuccess)
+      return GVM_EDEVICE;
+    ctx->d2h.fetch_add(si.c_bytes);
+  }
+  const uint32_t idx = (uint32_t)r->id * D + (uint32_t)(s & (D - 1));
+  if (driver_api()->write_value32(reinterpret_cast<CUstream>(r->in_stream),
+                                  reinterpret_cast<CUdeviceptr>(&ctx->params.host_complete[idx].tag), tag_of(s),
+                                  CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
+    return GVM_EDEVICE;
+  return GVM_OK;
+}
+
+// The request barrier of PS-1 / PS-2: every task published before this call
+// and not yet issued, in the style's order. PS-1: all ranks' input copies,
+// then all kernels, then all output copies (within a rank, task order). PS-2:
+// rank by rank, task by task, input -> kernel -> output. Each rank's work goes
+// on its own stream, so the hardware overlaps what the style allows. Caller
+// holds launch_mu.
+int ps_flush_locked(gvm_ctx* ctx) {
+  const size_t R = ctx->ranks.size();
+  std::vector<uint64_t> from(R), upto(R);
+  for (size_t i = 0; i < R; ++i) {
+    upto[i] = ctx->ranks[i]->published.load(std::memory_order_acquire);
+    from[i] = std::min(ctx->ranks[i]->flushed.load(std::memory_order_acquire), upto[i]);
+  }
+  int rc = GVM_OK;
+  if (ctx->cfg.mode == GVM_MODE_PS1) {
+    for (int phase = 0; phase < 3 && rc == GVM_OK; ++phase)
+      for (size_t i = 0; i < R && rc == GVM_OK; ++i)
+        for (uint64_t s = from[i]; s < upto[i] && rc == GVM_OK; ++s) {
+          gvm_rank* r = ctx->ranks[i].get();
+          rc = phase == 0 ? ps_issue_in(r, s) : phase == 1 ? ps_issue_comp(r, s) : ps_issue_out(r, s);
+        }
+  } else {
+    for (size_t i = 0; i < R && rc == GVM_OK; ++i)
+      for (uint64_t s = from[i]; s < upto[i] && rc == GVM_OK; ++s) {
+        gvm_rank* r = ctx->ranks[i].get();
+        rc = ps_issue_in(r, s);
+        if (rc == GVM_OK) rc = ps_issue_comp(r, s);
+        if (rc == GVM_OK) rc = ps_issue_out(r, s);
+      }
+  }
+  if (rc != GVM_OK) return rc;
+  for (size_t i = 0; i < R; ++i) ctx->ranks[i]->flushed.store(upto[i], std::memory_order_release);
+  return GVM_OK;
 }
 
 bool is_pinned(const void* p) {
@@ -715,11 +826,18 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* f
     SlotInfo& si = r->slots[slot];
     si.bytes = (i == last_host) ? held : 0;
     si.stage_end = r->ring_head;
-    si.needs_out = !p.resident;
+    si.needs_out = !p.resident && !stream_mode(ctx);
     si.c_host = t->c;
     si.c_dev = dc;
     si.c_bytes = p.resident ? 0 : p.bytes_c;
-    if (!p.resident) {
+    si.host_io = !p.resident;
+    si.a_host = t->a;
+    si.b_host = t->b;
+    si.a_dev = da;
+    si.b_dev = db;
+    si.a_bytes = p.resident ? 0 : p.bytes_a;
+    si.b_bytes = p.resident ? 0 : p.bytes_b;
+    if (!p.resident && !stream_mode(ctx)) {
       const uint64_t srcs_dst[2][3] = {{da, (uint64_t)(uintptr_t)t->a, p.bytes_a},
                                        {db, (uint64_t)(uintptr_t)t->b, p.bytes_b}};
       for (int j = 0; j < 2; ++j) {
@@ -743,7 +861,8 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* f
   }
 
   // ---- input copies, each task's ready word after the run that ends its inputs
-  {
+  // (PS-1 / PS-2: gvm_flush issues them)
+  if (!stream_mode(ctx)) {
     const DriverApi* api = driver_api();
     size_t next_ready = 0;
     auto write_ready = [&](uint32_t upto_run) -> bool {
@@ -840,10 +959,9 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
   gvm_ctx* ctx = r->ctx;
   std::unique_lock<std::mutex> g(r->mu);
   if (seq >= r->next_seq) return GVM_EINVAL;
-  // Barrier mode: a task submitted after the last gvm_flush never runs
-  // until the next one.
-  if (ctx->cfg.mode == GVM_MODE_BARRIER && seq >= r->flushed.load(std::memory_order_acquire))
-    return GVM_ESTATE;
+  // Barrier, PS-1, PS-2 modes: a task submitted after the last gvm_flush
+  // never runs until the next one.
+  if (flush_mode(ctx) && seq >= r->flushed.load(std::memory_order_acquire)) return GVM_ESTATE;
   bind_device(ctx);
   if (push_flushed(r) != GVM_OK) return GVM_EDEVICE;
   uint64_t last = r->synced;
@@ -865,7 +983,7 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
     // and driver calls from many threads serialise).
     if (now - t_query > kStreamQueryNs) {
       t_query = now;
-      cudaError_t e = cudaStreamQuery(ctx->sched);
+      cudaError_t e = cudaStreamQuery(stream_mode(ctx) ? r->in_stream : ctx->sched);
       if (e != cudaSuccess && e != cudaErrorNotReady) return GVM_EDEVICE;
     }
     if ((++spins & 63) == 0) {
@@ -882,6 +1000,7 @@ int gvm_flush(gvm_ctx* ctx) {
   if (ctx->cfg.mode == GVM_MODE_CONTINUOUS) return GVM_OK;  // the scheduler is resident
   bind_device(ctx);
   std::lock_guard<std::mutex> g(ctx->launch_mu);
+  if (stream_mode(ctx)) return ps_flush_locked(ctx);
   // Every task published before this point is drained by the launch below.
   std::vector<uint64_t> upto(ctx->ranks.size());
   for (size_t i = 0; i < ctx->ranks.size(); ++i) upto[i] = ctx->ranks[i]->published.load(std::memory_order_acquire);
@@ -936,7 +1055,7 @@ void* gvm_rank_resident_ptr(gvm_rank* r) { return r ? reinterpret_cast<void*>(r-
 int gvm_detach(gvm_rank* r) {
   if (!r) return GVM_EINVAL;
   if (!r->attached) return GVM_ESTATE;
-  if (r->ctx->cfg.mode == GVM_MODE_BARRIER && r->flushed.load() < r->published.load()) return GVM_ESTATE;
+  if (flush_mode(r->ctx) && r->flushed.load() < r->published.load()) return GVM_ESTATE;
   if (r->next_seq > 0) {
     int rc = gvm_sync(r, r->next_seq - 1);
     if (rc != GVM_OK) return rc;
@@ -961,6 +1080,8 @@ int gvm_shutdown(gvm_ctx* ctx) {
     if (ctx->cfg.mode == GVM_MODE_BARRIER && pending) {
       if (launch_locked(ctx, 1) != GVM_OK) rc = GVM_EDEVICE;
       for (auto& rk : ctx->ranks) rk->flushed.store(rk->published.load());
+    } else if (stream_mode(ctx) && pending) {
+      if (ps_flush_locked(ctx) != GVM_OK) rc = GVM_EDEVICE;
     }
   }
   GVM_TRACE("shutdown: stop (launches=%llu)", (unsigned long long)ctx->launches.load());

@@ -4,6 +4,7 @@
 // same task computed by the manager agree bit for bit.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "gvm.h"
@@ -285,10 +286,10 @@ extern "C" uint64_t gvm_sgemm_scratch_bytes(int32_t m, int32_t n, int32_t k, int
   return path == GVM_SGEMM_SPLIT3 ? split_scratch_bytes(m, n, k) : 0;
 }
 
-static bool fma_attr_set = false;
-static bool tc_attr_set = false;
-static bool fz_attr_set = false;
-static bool pr_attr_set = false;
+// Set once per process; the attribute call is idempotent, so racing first calls are harmless.
+static std::atomic<bool> fma_attr_set{false};
+static std::atomic<bool> tc_attr_set{false};
+static std::atomic<bool> fz_attr_set{false};
 
 extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m, int32_t n, int32_t k,
                              int32_t path, void* scratch, uint64_t scratch_bytes, void* stream) {

@@ -19,6 +19,8 @@ from ._abi import (
     GVM_EAGAIN,
     GVM_MODE_BARRIER,
     GVM_MODE_CONTINUOUS,
+    GVM_MODE_PS1,
+    GVM_MODE_PS2,
     GVM_SGEMM_FMA,
     GVM_SGEMM_SPLIT3,
     GVM_SGEMM_SPLIT3_FUSED,
@@ -40,7 +42,7 @@ _PATHS = {
     "split3_fused": GVM_SGEMM_SPLIT3_FUSED,
     "split3_pair": GVM_SGEMM_SPLIT3_PAIR,
 }
-_MODES = {"barrier": GVM_MODE_BARRIER, "continuous": GVM_MODE_CONTINUOUS}
+_MODES = {"barrier": GVM_MODE_BARRIER, "continuous": GVM_MODE_CONTINUOUS, "ps1": GVM_MODE_PS1, "ps2": GVM_MODE_PS2}
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -320,7 +322,8 @@ class Manager:
         check(lib().gvm_flush(self.handle), "gvm_flush")
 
     def flush_if_barrier(self) -> None:
-        if self.mode == "barrier":
+        """gvm_flush in every mode that needs one (all but continuous)."""
+        if self.mode != "continuous":
             self.flush()
 
     def wait_idle(self) -> None:

@@ -87,6 +87,12 @@ def test_host_only_calls_without_gpu(built):
     cfg = GvmConfig()
     cfg.max_ranks, cfg.ring_depth, cfg.mode, cfg.sgemm_path = 16, 64, 0, 1
     assert L.gvm_ctrl_bytes(byref(cfg)) > 16 * 64 * 512
+    for mode in (1, 2, 3):  # continuous, PS-1, PS-2
+        cfg.mode = mode
+        assert L.gvm_ctrl_bytes(byref(cfg)) > 0
+    cfg.mode = 4
+    assert L.gvm_ctrl_bytes(byref(cfg)) == 0
+    cfg.mode = 0
     cfg.ring_depth = 63  # not a power of two
     assert L.gvm_ctrl_bytes(byref(cfg)) == 0
     h = c_void_p()
@@ -96,6 +102,9 @@ def test_host_only_calls_without_gpu(built):
     assert L.gvm_sgemm_scratch_bytes(0, 5, 5, 1) == 0
     assert L.gvm_vadd_f32(None, None, None, -1, None) == GVM_EINVAL
     assert L.gvm_vadd_f32(None, None, None, 0, None) == 0
+    assert L.gvm_vmul_f32(None, None, None, 0, 15, None) == 0
+    assert L.gvm_vmul_f32(None, None, None, 0, 0, None) == GVM_EINVAL
+    assert L.gvm_vmul_f32(None, None, None, 16, 1025, None) == GVM_EINVAL
     assert L.gvm_sgemm_f32(None, None, None, 0, 4, 4, 0, None, 0, None) == GVM_EINVAL
     assert L.gvm_attach(None, 0, byref(h)) == GVM_EINVAL
     assert L.gvm_submit(None, None, None) == GVM_EINVAL

@@ -1,8 +1,9 @@
 """Parity of the task kernels alone (gvm_vadd_f32, gvm_vmul_f32,
 gvm_sgemm_f32) against the CPU oracle, through the C ABI. Vector add and
-vector multiply: bit-exact. SGEMM: relative
-Frobenius error <= 1e-5 against the binary64 oracle, and exact on integer
-operands whose products and sums are exact in both arithmetics."""
+vector multiply: bit-exact. SGEMM: within the elementwise bound of the split
+arithmetic and, for results of 256 elements or more, relative Frobenius
+error <= 1e-5 against the binary64 oracle (``sgemm_bounds``); exact on
+integer operands whose products and sums are exact in both arithmetics."""
 import numpy as np
 import pytest
 import torch
@@ -12,7 +13,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-SGEMM_TOL = 1e-5
+from sgemm_bounds import check_sgemm  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -125,8 +126,7 @@ def test_sgemm_normal_inputs(gvm, path, shape):
     m, n, k = shape
     A, B = synth.sgemm_inputs(synth.task_seed(m, n % 1000), m, n, k)
     C = run_sgemm(gvm, A, B, path)
-    err = oracle.rel_fro_err(C, oracle.sgemm64(A, B))
-    assert err <= SGEMM_TOL, (path, shape, err)
+    check_sgemm(C, A, B)
     from paper_1511_07658_gb300.manager import kernel_status
 
     assert kernel_status() == 0
