@@ -610,9 +610,10 @@ def gpu_arm(args, w, desc, rank, world):
 # --------------------------------------------------------------- CPU oracle
 
 
-def oracle_rate(w, inputs_fn, max_tasks, threads):
+def oracle_rate(w, inputs_fn, max_tasks, threads, min_seconds=0.0):
     """The CPU oracle as it stands: one rank per thread, each rank's first
-    tasks in order, until max_tasks tasks are done."""
+    tasks in order, until max_tasks tasks are done; the same tasks are run
+    again, whole rounds at a time, until at least min_seconds have passed."""
     import oracle
 
     by_rank = w.by_rank()
@@ -633,19 +634,25 @@ def oracle_rate(w, inputs_fn, max_tasks, threads):
         else:
             oracle.sgemm64(*data[j])
 
+    done = 0
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(one, range(len(picks))))
+        while True:
+            list(ex.map(one, range(len(picks))))
+            done += len(picks)
+            if time.perf_counter() - t0 >= min_seconds:
+                break
     dt = time.perf_counter() - t0
-    return len(picks) / dt, len(picks), dt
+    return done / dt, done, dt
 
 
 def cpu_baseline(w):
     threads = min(16, os.cpu_count() or 1)
     n = 2 * threads if w.tasks[0].kind == synth.TASK_SGEMM else len(w.tasks)
-    rate, cnt, dt = oracle_rate(w, task_inputs, n, threads)
+    rate, cnt, dt = oracle_rate(w, task_inputs, n, threads, min_seconds=10.0)
     return {"value": rate, "unit": "tasks/s", "cores": threads, "kind": "oracle",
-            "sample": f"{cnt} tasks of the workload ({dt:.1f} s), one rank per thread, binary64 SGEMM"}
+            "sample": f"{cnt} task runs ({n} distinct tasks of the workload, repeated) in {dt:.1f} s, "
+                      f"one rank per thread, binary64 SGEMM"}
 
 
 def reference_arm(args, w, desc):
@@ -963,23 +970,25 @@ def model_check(args, w):
 
 
 def paper_ps_check():
-    """The paper's own mechanism and model (Sections 4.2.1-4.2.3): one host
-    thread issues every process's task on that process's stream, in
-    programming style 1 (all input copies, then all kernels, then all output
-    copies) or style 2 (per stream: input, kernel, output), with the task
-    kernels alone (no persistent scheduler), for N = 1, 2, 4, 8, 16. Measured
-    times against Eqs. 2-7 from solo T_in, T_comp, T_out, for compute-
-    intensive tasks (FMA SGEMM 2048^3, which fills the GPU, and a one-CTA FMA
-    SGEMM 128 x 128 x 16384, which leaves the other SMs free as the model's
-    full kernel overlap assumes) and I/O-intensive ones (vector add, and
-    vector multiply with 15 products as in Table 2, n = 2^24 each).
-    Deviation as the paper reports it (Section 6)."""
+    """The paper's own mechanism and model (Sections 4.2.1-4.2.3, Section 6):
+    N ranks of one manager in GVM_MODE_PS1 or GVM_MODE_PS2 each submit one
+    host-mode task; gvm_flush (the request barrier) issues every task's
+    copies and kernel on its rank's stream in the style's order. The shared
+    time (first issue to the last rank's completion, CUDA events on the rank
+    streams) for N = 1, 2, 4, 8, 16 against Eqs. 2-7 from solo T_in, T_comp,
+    T_out, profiled first with the same copies and kernel on one stream, as
+    the paper derives them. Cases: compute-intensive FMA SGEMM 2048^3 (fills
+    the GPU) and a one-CTA FMA SGEMM 128 x 128 x 16384 (leaves the other SMs
+    free, as the model's full kernel overlap assumes, like the paper's one-
+    block EP kernel); I/O-intensive vector add and vector multiply with 15
+    products (Table 2), n = 2^24 each. Deviation as Section 6 reports it."""
     import torch
 
     import paper_1511_07658_gb300 as g
     from oracle import model
 
     reps = 5
+    nmax = 16
     out = {}
     cases = {
         "ci_sgemm_fma_2048": ("sgemm", (2048, 2048, 2048)),
@@ -988,7 +997,6 @@ def paper_ps_check():
         "ioi_vmul_2p24_x15": ("vmul", 1 << 24),
     }
     for name, (kind, size) in cases.items():
-        nmax = 16
         if kind == "sgemm":
             mm, nn, kk = size
             hin = [[torch.randn(mm, kk).pin_memory(), torch.randn(kk, nn).pin_memory()] for _ in range(nmax)]
@@ -999,83 +1007,99 @@ def paper_ps_check():
         else:
             hin = [[torch.randn(size).pin_memory(), torch.randn(size).pin_memory()] for _ in range(nmax)]
             hout = [torch.empty(size).pin_memory() for _ in range(nmax)]
-        din = [[x.cuda() for x in h] for h in hin]
-        dout = [torch.empty_like(h, device="cuda") for h in hout]
-        streams = [torch.cuda.Stream() for _ in range(nmax)]
+        task_bytes = sum(x.numel() * 4 for x in hin[0]) + hout[0].numel() * 4
 
-        def h2d(r):
-            for d, h in zip(din[r], hin[r]):
+        # ---- solo profile: one stream, the task's copies and kernel alone
+        din = [x.cuda() for x in hin[0]]
+        dout = torch.empty_like(hout[0], device="cuda")
+        st = torch.cuda.Stream()
+
+        def h2d():
+            for d, h in zip(din, hin[0]):
                 d.copy_(h, non_blocking=True)
 
-        def comp(r):
+        def comp():
             if kind == "sgemm":
-                g.sgemm_f32(din[r][0], din[r][1], dout[r], path="fma", stream=streams[r])
+                g.sgemm_f32(din[0], din[1], dout, path="fma", stream=st)
             elif kind == "vmul":
-                g.vmul_f32(din[r][0], din[r][1], dout[r], 15, stream=streams[r])
+                g.vmul_f32(din[0], din[1], dout, 15, stream=st)
             else:
-                g.vadd_f32(din[r][0], din[r][1], dout[r], stream=streams[r])
+                g.vadd_f32(din[0], din[1], dout, stream=st)
 
-        def d2h(r):
-            hout[r].copy_(dout[r], non_blocking=True)
-
-        def run(n, style):
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for r in range(n):
-                streams[r].wait_event(e0)
-            if style == 1:
-                for phase in (h2d, comp, d2h):
-                    for r in range(n):
-                        with torch.cuda.stream(streams[r]):
-                            phase(r)
-            else:
-                for r in range(n):
-                    with torch.cuda.stream(streams[r]):
-                        h2d(r)
-                        comp(r)
-                        d2h(r)
-            ends = []
-            for r in range(n):
-                ev = torch.cuda.Event()
-                ev.record(streams[r])
-                ends.append(ev)
-            cur = torch.cuda.current_stream()
-            for ev in ends:
-                cur.wait_event(ev)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e1.record()
-            e1.synchronize()
-            return e0.elapsed_time(e1) / 1e3
+        def d2h():
+            hout[0].copy_(dout, non_blocking=True)
 
         def solo(fn):
             times = []
             for _ in range(reps + 2):
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                with torch.cuda.stream(streams[0]):
-                    e0.record(streams[0])
-                    fn(0)
-                    e1.record(streams[0])
+                with torch.cuda.stream(st):
+                    e0.record(st)
+                    fn()
+                    e1.record(st)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1) / 1e3)
             return statistics.median(times[2:])
 
         t_in, t_comp, t_out = solo(h2d), solo(comp), solo(d2h)
+        del din, dout
+        torch.cuda.empty_cache()
+
+        # ---- shared: the manager in PS-1 / PS-2 mode
+        def shared_times(style):
+            mgr = g.Manager(nmax, ring_depth=2, mode=f"ps{style}", sgemm_path="fma",
+                            slice_bytes=(task_bytes + (8 << 20)) // (1 << 20) * (1 << 20) + (1 << 20))
+            ranks = [mgr.attach(r) for r in range(nmax)]
+
+            def submit(r):
+                a, b = hin[r]
+                if kind == "sgemm":
+                    return ranks[r].submit_sgemm(a, b, hout[r])
+                if kind == "vmul":
+                    return ranks[r].submit_vmul(a, b, hout[r], 15)
+                return ranks[r].submit_vadd(a, b, hout[r])
+
+            def run(n):
+                torch.cuda.synchronize()
+                cur = torch.cuda.current_stream()
+                seqs = [submit(r) for r in range(n)]  # the ranks' requests; nothing is issued yet
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(cur)
+                for r in range(n):
+                    mgr.copy_streams[2 * r].wait_event(e0)
+                mgr.flush()
+                for r in range(n):
+                    ev = torch.cuda.Event()
+                    ev.record(mgr.copy_streams[2 * r])
+                    cur.wait_event(ev)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(cur)
+                e1.synchronize()
+                for r in range(n):
+                    ranks[r].sync(seqs[r])
+                return e0.elapsed_time(e1) / 1e3
+
+            res = {}
+            for n in (1, 2, 4, 8, 16):
+                run(n)
+                res[n] = statistics.median(run(n) for _ in range(reps))
+            mgr.shutdown()
+            return res
+
+        meas = {1: shared_times(1), 2: shared_times(2)}
         rows = []
         for n in (1, 2, 4, 8, 16):
             row = {"N": n}
             for style in (1, 2):
-                run(n, style)
-                meas = statistics.median(run(n, style) for _ in range(reps))
                 if style == 1:
                     pred = model.t_total_ci_ps1(n, t_in, t_comp, t_out)  # Eq. 2 = Eq. 4
                 else:
                     pred = (model.t_total_ci_ps2(n, t_in, t_comp, t_out) if model.classify(t_in, t_comp, t_out) == model.CI
                             else model.t_total_ioi_ps2(n, t_in, t_comp, t_out))  # Eq. 3 or Eq. 7
-                row[f"ps{style}_measured_s"] = meas
+                row[f"ps{style}_measured_s"] = meas[style][n]
                 row[f"ps{style}_model_s"] = pred
-                row[f"ps{style}_deviation"] = model.deviation(meas, pred)
+                row[f"ps{style}_deviation"] = model.deviation(meas[style][n], pred)
             row["eq1_no_init_s"] = model.t_total_no_vt(n, 0.0, t_in, t_comp, t_out, 0.0)
             rows.append(row)
         out[name] = {
@@ -1087,8 +1111,7 @@ def paper_ps_check():
             "mean_deviation_ps1_n1to8": statistics.mean(r["ps1_deviation"] for r in rows if r["N"] <= 8),
             "mean_deviation_ps2_n1to8": statistics.mean(r["ps2_deviation"] for r in rows if r["N"] <= 8),
         }
-        del din, dout, hin, hout
-        torch.cuda.empty_cache()
+        del hin, hout
     return out
 
 
