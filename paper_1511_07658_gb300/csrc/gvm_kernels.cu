@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     bool have_prev = false, ok = true;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
-      ok = fz_convert(t, big, &fs, it, timeout_ns, &abort_flag, &fail_where, nullptr);
+      ok = fz_convert<false>(t, big, &fs, it, timeout_ns, &abort_flag, &fail_where, nullptr);
       if (ok && have_prev) ok = fz_epilogue(prev, &fs, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
       prev = t;
       have_prev = true;

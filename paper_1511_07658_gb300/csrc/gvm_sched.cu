@@ -845,7 +845,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
           mbar_arrive(&sh.item_empty[slot]);
         }
         __syncwarp();
-        ok = fz_convert(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+        ok = fz_convert<true>(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
                         tid == 0 ? &sh.prof[kProfStageWait] : nullptr);
         it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
         if (ok) {
