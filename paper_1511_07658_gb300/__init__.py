@@ -29,14 +29,21 @@ from ._abi import (  # noqa: E402
     GVM_ENOMEM,
     GVM_ESTATE,
     GVM_ETIMEDOUT,
+    GVM_IPC_ATTACHED,
+    GVM_IPC_CLOSED,
+    GVM_IPC_FREE,
+    GVM_IPC_LOST,
     GVM_MODE_BARRIER,
     GVM_MODE_CONTINUOUS,
+    GVM_MODE_PS1,
+    GVM_MODE_PS2,
     GVM_OK,
     GVM_SGEMM_FMA,
     GVM_SGEMM_SPLIT3,
     GVM_TASK_RESIDENT,
     GVM_TASK_SGEMM,
     GVM_TASK_VADD,
+    GVM_TASK_VMUL,
     GvmConfig,
     GvmError,
     GvmStats,
@@ -45,10 +52,14 @@ from ._abi import (  # noqa: E402
     lib_path,
 )
 from .manager import Manager, Rank, sgemm_f32, sgemm_scratch_bytes, vadd_f32, vmul_f32  # noqa: E402
+from .ipc import IpcClient, IpcRegion, IpcServer  # noqa: E402
 
 __all__ = [
     "Manager",
     "Rank",
+    "IpcRegion",
+    "IpcServer",
+    "IpcClient",
     "vadd_f32",
     "vmul_f32",
     "sgemm_f32",
@@ -71,9 +82,16 @@ __all__ = [
     "GVM_ENODEV",
     "GVM_TASK_VADD",
     "GVM_TASK_SGEMM",
+    "GVM_TASK_VMUL",
+    "GVM_IPC_FREE",
+    "GVM_IPC_ATTACHED",
+    "GVM_IPC_CLOSED",
+    "GVM_IPC_LOST",
     "GVM_TASK_RESIDENT",
     "GVM_SGEMM_FMA",
     "GVM_SGEMM_SPLIT3",
     "GVM_MODE_BARRIER",
     "GVM_MODE_CONTINUOUS",
+    "GVM_MODE_PS1",
+    "GVM_MODE_PS2",
 ]

@@ -91,6 +91,27 @@ class GvmStats(ctypes.Structure):
     ]
 
 
+class GvmIpcTask(ctypes.Structure):
+    """gvm_ipc_task: one cross-process request (offsets into the rank's data area)."""
+
+    _fields_ = [
+        ("type", c_int32),
+        ("reserved", c_int32),
+        ("m", c_int64),
+        ("n", c_int64),
+        ("k", c_int64),
+        ("a_off", c_uint64),
+        ("b_off", c_uint64),
+        ("c_off", c_uint64),
+    ]
+
+
+GVM_IPC_FREE = 0
+GVM_IPC_ATTACHED = 1
+GVM_IPC_CLOSED = 2
+GVM_IPC_LOST = 3
+
+
 class GvmError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
@@ -132,6 +153,21 @@ PROTOTYPES = {
     ),
     "gvm_kernel_status": (c_int, [POINTER(c_uint32)]),
     "gvm_sgemm_f32_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p]),
+    # cross-process ranks (gvm_ipc.h)
+    "gvm_ipc_create": (c_int, [c_char_p, c_int32, c_uint64, c_int32, POINTER(c_void_p)]),
+    "gvm_ipc_destroy": (c_int, [c_void_p]),
+    "gvm_ipc_serve": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),
+    "gvm_ipc_stop": (c_int, [c_void_p]),
+    "gvm_ipc_server_counts": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint64)]),
+    "gvm_ipc_peek": (
+        c_int, [c_void_p, c_int32, POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint32)]
+    ),
+    "gvm_ipc_open": (c_int, [c_char_p, c_int32, POINTER(c_void_p)]),
+    "gvm_ipc_data": (c_void_p, [c_void_p, POINTER(c_uint64)]),
+    "gvm_ipc_submit": (c_int, [c_void_p, POINTER(GvmIpcTask), POINTER(c_uint64)]),
+    "gvm_ipc_barrier": (c_int, [c_void_p]),
+    "gvm_ipc_wait": (c_int, [c_void_p, c_uint64, c_uint64]),
+    "gvm_ipc_close": (c_int, [c_void_p]),
 }
 
 _lib = None

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgvm.so")
-SOURCES = ["gvm_host.cu", "gvm_sched.cu", "gvm_kernels.cu", "gvm_noalloc.cu", "gvm_spmd.cu"]
+SOURCES = ["gvm_host.cu", "gvm_sched.cu", "gvm_kernels.cu", "gvm_noalloc.cu", "gvm_spmd.cu", "gvm_ipc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = [
     "-O3",
@@ -49,7 +49,7 @@ def _stale(obj: str, src: str) -> bool:
         return True
     t = os.path.getmtime(obj)
     deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    deps.append(os.path.join(ROOT, "include", "gvm.h"))
+    deps += [os.path.join(ROOT, "include", f) for f in ("gvm.h", "gvm_ipc.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -124,6 +124,11 @@ struct gvm_ctx {
   }
 };
 
+namespace gvm {
+int ctx_mode(const gvm_ctx* ctx) { return ctx->cfg.mode; }
+int ctx_max_ranks(const gvm_ctx* ctx) { return ctx->cfg.max_ranks; }
+}  // namespace gvm
+
 namespace {
 
 bool cfg_valid(const gvm_config* c) {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gvm.h"
 #include "gvm_internal.h"
 
 namespace gvm {
@@ -31,5 +32,9 @@ CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUten
 // and an asynchronous launch on `stream`.
 cudaError_t scheduler_setup(int path, int* blocks_per_sm, size_t* smem_bytes);
 cudaError_t launch_scheduler(int path, const SchedParams& p, int grid, size_t smem, cudaStream_t stream);
+
+// Configuration of a manager, for the library's other host modules.
+int ctx_mode(const gvm_ctx* ctx);
+int ctx_max_ranks(const gvm_ctx* ctx);
 
 }  // namespace gvm

@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports what include/gvm.h declares
+"""The C-ABI library builds, loads and exports what include/*.h declares
 (CPU only: no compute calls)."""
 import ctypes
 import os
@@ -9,13 +9,17 @@ import pytest
 
 from conftest import ROOT
 
-HEADER = os.path.join(ROOT, "include", "gvm.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(gvm_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(gvm_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -53,13 +57,15 @@ def test_python_binding_covers_the_abi(built):
 
 def test_struct_layouts_match_c(built, tmp_path):
     from paper_1511_07658_gb300 import GvmConfig, GvmStats, GvmTask
+    from paper_1511_07658_gb300._abi import GvmIpcTask
 
     src = tmp_path / "sz.c"
     src.write_text(
-        '#include <stdio.h>\n#include <stddef.h>\n#include "gvm.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(gvm_config), sizeof(gvm_task),"
+        '#include <stdio.h>\n#include <stddef.h>\n#include "gvm.h"\n#include "gvm_ipc.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(gvm_config), sizeof(gvm_task),"
         " sizeof(gvm_stats), offsetof(gvm_config, copy_streams), offsetof(gvm_config, ingest_quantum),"
-        " offsetof(gvm_task, c_off), offsetof(gvm_stats, device_where)); return 0;}\n"
+        " offsetof(gvm_task, c_off), offsetof(gvm_stats, device_where), sizeof(gvm_ipc_task),"
+        " offsetof(gvm_ipc_task, c_off)); return 0;}\n"
     )
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -72,6 +78,8 @@ def test_struct_layouts_match_c(built, tmp_path):
         GvmConfig.ingest_quantum.offset,
         GvmTask.c_off.offset,
         GvmStats.device_where.offset,
+        ctypes.sizeof(GvmIpcTask),
+        GvmIpcTask.c_off.offset,
     ]
     assert vals == want
 
