@@ -70,6 +70,9 @@ def parse():
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--plain", action="store_true", help="also time the plain one-context-per-rank form")
     p.add_argument("--model", action="store_true", help="also check timings against Eqs. 1, 2 and 7")
+    p.add_argument("--cross-process", action="store_true",
+                   help="also run the workload end to end with every rank a separate client process")
+    p.add_argument("--ipc-client", nargs=2, metavar=("NAME", "RANK"), help=argparse.SUPPRESS)
     p.add_argument("--paper-modes", action="store_true",
                    help="also run the workload in the paper's host-issued PS-1 / PS-2 modes")
     p.add_argument("--quantum", type=int, default=8)
@@ -300,6 +303,114 @@ def paper_modes_check(args, g, w, slice_bytes, resident, res_arrays, host_arrays
         out[mode] = row
         mgr.shutdown()
     return out
+
+
+def _ipc_layout(w):
+    """Per rank: byte offsets (a, b, c) of each task in the rank's data area
+    (256-byte aligned, inputs and output of a task adjacent) and the total."""
+    offs, need = {}, [0] * w.ranks
+    for spec in w.tasks:
+        if spec.kind in (synth.TASK_VADD, synth.TASK_VMUL):
+            la = lb = lc = 4 * spec.n
+        else:
+            la, lb, lc = 4 * spec.m * spec.k, 4 * spec.k * spec.n, 4 * spec.m * spec.n
+        o = need[spec.rank]
+        a256 = lambda x: (x + 255) // 256 * 256  # noqa: E731
+        offs[(spec.rank, spec.index)] = (o, o + a256(la), o + a256(la) + a256(lb))
+        need[spec.rank] = o + a256(la) + a256(lb) + a256(lc)
+    return offs, need
+
+
+def ipc_client_main(args):
+    """One client process of the cross-process leg (no CUDA): fills its data
+    area with its tasks' inputs, then runs warm-up and timed steps (submit
+    every task, arrive at the request barrier, wait for every result) and
+    prints its timed seconds."""
+    from paper_1511_07658_gb300 import GVM_EAGAIN, GvmError
+    from paper_1511_07658_gb300.ipc import IpcClient
+
+    name, rank = args.ipc_client[0], int(args.ipc_client[1])
+    w, _ = workload(args.workload, args.ranks, args.per_rank)
+    offs, _ = _ipc_layout(w)
+    mine = [s for s in w.tasks if s.rank == rank]
+    c = IpcClient(name, rank)
+    for spec in mine:
+        a, b = task_inputs(spec)
+        oa, ob, _ = offs[(rank, spec.index)]
+        c.floats(oa, a.size)[:] = np.ascontiguousarray(a).ravel()
+        c.floats(ob, b.size)[:] = np.ascontiguousarray(b).ravel()
+
+    def step():
+        seqs = []
+        for spec in mine:
+            oa, ob, oc = offs[(rank, spec.index)]
+            while True:
+                try:
+                    if spec.kind == synth.TASK_SGEMM:
+                        seqs.append(c.submit_sgemm(oa, ob, oc, spec.m, spec.n, spec.k))
+                    else:
+                        seqs.append(c.submit_vadd(oa, ob, oc, spec.n))
+                    break
+                except GvmError as e:  # ring full: let the barrier drain it
+                    if e.code != GVM_EAGAIN:
+                        raise
+                    c.barrier()
+                    c.wait(seqs[-1], timeout_s=60)
+        c.barrier()
+        for q in seqs:
+            c.wait(q, timeout_s=60)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    c.close()
+    print(json.dumps({"rank": rank, "seconds": dt}))
+
+
+def cross_process_check(args, w):
+    """The workload end to end with every rank a separate client process
+    (include/gvm_ipc.h): operands and results in each rank's shared-memory
+    data area, copies between it and the GPU inside the timed region, the
+    request barrier across processes. tasks/s = all ranks' tasks of the timed
+    steps / the slowest client's timed seconds."""
+    import subprocess
+
+    import paper_1511_07658_gb300 as g
+
+    R = w.ranks
+    per_rank = len(w.tasks) // R
+    _, need = _ipc_layout(w)
+    name = f"gvmbench-{os.getpid()}"
+    region = g.IpcRegion.create(name, R, max(need), max(2, 1 << (per_rank - 1).bit_length()))
+    try:
+        with g.Manager(R, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode="barrier",
+                       sgemm_path=args.path, slice_bytes=max(need) + (64 << 20)) as mgr:
+            server = g.IpcServer(mgr, region)
+            try:
+                cmd = [sys.executable, os.path.abspath(__file__), "--workload", args.workload, "--steps",
+                       str(max(3, args.steps // 2)), "--warmup", str(max(1, args.warmup))]
+                if args.ranks:
+                    cmd += ["--ranks", str(args.ranks), "--per-rank", str(args.per_rank)]
+                procs = [subprocess.Popen(cmd + ["--ipc-client", name, str(r)], stdout=subprocess.PIPE,
+                                          stderr=subprocess.PIPE, text=True) for r in range(R)]
+                outs = [p.communicate(timeout=600) for p in procs]
+                counts = server.counts()
+            finally:
+                server.stop()
+    finally:
+        region.destroy()
+    secs = []
+    for p, (o, e) in zip(procs, outs):
+        if p.returncode != 0:
+            raise RuntimeError(f"ipc client failed: {e[-2000:]}")
+        secs.append(json.loads(o.strip().splitlines()[-1])["seconds"])
+    steps = max(3, args.steps // 2)
+    return {"value": R * per_rank * steps / max(secs), "unit": "tasks/s", "clients": R, "steps": steps,
+            "kind": "end to end, one process per rank, data in POSIX shared memory",
+            "barriers": counts["barriers"], "tasks_completed": counts["completed"]}
 
 
 def gpu_arm(args, w, desc, rank, world):
@@ -1295,6 +1406,9 @@ def grouped_arm(args):
 
 def main():
     args = parse()
+    if args.ipc_client:
+        ipc_client_main(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.workload == "grouped":
@@ -1329,6 +1443,8 @@ def main():
             out["cpu_baseline"] = cpu_baseline(w)
         if args.plain and w.tasks[0].kind == synth.TASK_SGEMM:
             out["plain_per_rank"] = plain_per_rank(w)
+        if args.cross_process:
+            out["cross_process"] = cross_process_check(args, w)
         if args.model:
             out["model_check"] = model_check(args, w)
             out["paper_ps_model"] = paper_ps_check()

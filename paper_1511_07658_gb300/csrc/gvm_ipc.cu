@@ -633,7 +633,13 @@ int gvm_ipc_wait(gvm_ipc_client* c, uint64_t seq, uint64_t timeout_ns) {
       const int32_t sp = s->server_pid.load(std::memory_order_acquire);
       if (sp != 0 && !pid_alive(sp)) return GVM_ECANCELED;
     }
-    if (++spins > 64) std::this_thread::yield();
+    // Spin briefly, then back off: many clients may wait at once on as many
+    // cores as the manager's serving thread needs.
+    if (++spins > 4096) {
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    } else if (spins > 64) {
+      std::this_thread::yield();
+    }
   }
 }
 
