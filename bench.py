@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--plain", action="store_true", help="also time the plain one-context-per-rank form")
     p.add_argument("--model", action="store_true", help="also check timings against Eqs. 1, 2 and 7")
+    p.add_argument("--direct-output", type=int, choices=[0, 1], default=None,
+                   help="host-mode results written by the scheduler into the host buffers (default: tuning)")
     p.add_argument("--cross-process", action="store_true",
                    help="also run the workload end to end with every rank a separate client process")
     p.add_argument("--ipc-client", nargs=2, metavar=("NAME", "RANK"), help=argparse.SUPPRESS)
@@ -443,7 +445,9 @@ def gpu_arm(args, w, desc, rank, world):
     mgr = g.Manager(
         R, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode=args.mode, sgemm_path=args.path,
         slice_bytes=slice_bytes, resident_bytes=resident, ingest_quantum=args.quantum,
+        direct_output=None if args.direct_output is None else bool(args.direct_output),
     )
+    direct_output_used = mgr.cfg.direct_output
     ranks = [mgr.attach(r) for r in range(R)]
     # Host buffers: per rank, one pinned block holding every task's A then B
     # in submission order and one holding the outputs, each operand at a
@@ -686,6 +690,7 @@ def gpu_arm(args, w, desc, rank, world):
         "tasks_per_rank": per_rank,
         "sgemm_path": args.path,
         "mode": args.mode,
+        "direct_output": bool(direct_output_used),
         "operands": "resident in HBM for value; pinned host buffers for e2e",
         "l2": "inputs larger than L2 (2 GiB of operands per step)" if args.workload == "sgemm512"
         else "inputs smaller than L2; latency-bound",

@@ -136,6 +136,14 @@ typedef struct gvm_config {
                                sides are merged up to this many bytes; 0 = 16 MiB */
   int64_t vadd_tile;        /* elements per vector-add tile (rounded to 1024); 0 = per
                                task: n / scheduler CTAs, within 16 Ki .. 1 Mi */
+  int32_t direct_output;    /* barrier and continuous modes, host-mode tasks: 0 = the
+                               result is staged in the rank's slice and copied to c by the
+                               rank's output stream (Section 5's data path); 1 = the
+                               scheduler writes it straight into c through the buffer's
+                               device mapping (page-locked memory the GPU can address;
+                               a buffer without one uses the staged path), so outputs
+                               take no staging and no copy */
+  int32_t reserved0;        /* 0 */
 } gvm_config;
 
 typedef struct gvm_task {

@@ -54,6 +54,8 @@ class GvmConfig(ctypes.Structure):
         ("ingest_quantum", c_int32),
         ("copy_run_bytes", c_uint64),
         ("vadd_tile", c_int64),
+        ("direct_output", c_int32),
+        ("reserved0", c_int32),
     ]
 
 

@@ -469,6 +469,7 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   if (cfg.idle_poll_ns == 0) cfg.idle_poll_ns = 1000;
   if (cfg.copy_run_bytes == 0) cfg.copy_run_bytes = kDefaultCopyRun;
   if (cfg.vadd_tile < 0) return GVM_EINVAL;
+  if (cfg.direct_output < 0 || cfg.direct_output > 1 || cfg.reserved0 != 0) return GVM_EINVAL;
   if (cfg.vadd_tile > 0) cfg.vadd_tile = std::max<int64_t>(1024, cfg.vadd_tile / 1024 * 1024);
   if (cfg.ingest_quantum <= 0) cfg.ingest_quantum = 4;
   if (cfg.copy_streams)
@@ -618,6 +619,7 @@ namespace {
 struct Prep {
   const gvm_task* t;
   bool resident;
+  uint64_t c_direct;                   // device address of c when the kernel writes it there, else 0
   uint64_t bytes_a, bytes_b, bytes_c;  // operand bytes
   uint64_t sa, sb, sc;                 // staging bytes (256-aligned; 0 when resident)
 };
@@ -657,9 +659,18 @@ int prep_task(gvm_rank* r, const gvm_task* t, Prep* p) {
   p->bytes_a = bytes_a;
   p->bytes_b = bytes_b;
   p->bytes_c = bytes_c;
+  p->c_direct = 0;
+  if (!resident && bytes_c > 0 && r->ctx->cfg.direct_output && !stream_mode(r->ctx)) {
+    // The buffer's device mapping (the same address under unified addressing).
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, t->c) == cudaSuccess && at.devicePointer != nullptr)
+      p->c_direct = reinterpret_cast<uint64_t>(at.devicePointer);
+    else
+      (void)cudaGetLastError();
+  }
   p->sa = resident ? 0 : align_up(bytes_a, 256);
   p->sb = resident ? 0 : align_up(bytes_b, 256);
-  p->sc = resident ? 0 : align_up(bytes_c, 256);
+  p->sc = (resident || p->c_direct) ? 0 : align_up(bytes_c, 256);
   return GVM_OK;
 }
 
@@ -681,7 +692,7 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
   body->rank = (uint32_t)r->id;
   body->slot = (uint32_t)(seq & (D - 1));
   body->tag = tag_of(seq);
-  body->flags = p.resident ? 0u : (kFlagNeedsReady | kFlagNeedsD2H);
+  body->flags = p.resident ? 0u : p.c_direct ? (kFlagNeedsReady | kFlagDirectOut) : (kFlagNeedsReady | kFlagNeedsD2H);
   body->a = da;
   body->b = db;
   body->c = dc;
@@ -821,7 +832,7 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* f
     } else {
       da = base + in_off;
       db = da + p.sa;
-      dc = base + out_off;
+      dc = p.c_direct ? p.c_direct : base + out_off;
       in_off += p.sa + p.sb;
       out_off += p.sc;
     }
@@ -831,7 +842,8 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* f
     SlotInfo& si = r->slots[slot];
     si.bytes = (i == last_host) ? held : 0;
     si.stage_end = r->ring_head;
-    si.needs_out = !p.resident && !stream_mode(ctx);
+    si.needs_out = !p.resident && !stream_mode(ctx) && !p.c_direct;
+    if (p.c_direct) ctx->d2h.fetch_add(p.bytes_c);  // written by the kernel
     si.c_host = t->c;
     si.c_dev = dc;
     si.c_bytes = p.resident ? 0 : p.bytes_c;

@@ -30,6 +30,7 @@ enum : uint32_t {
   kFlagNeedsReady = 1u,   // host-mode inputs: wait for the input stream's ready word
   kFlagNeedsD2H = 2u,     // host-mode output: the output stream copies and completes
   kFlagSplit3 = 4u,       // SGEMM on the split-bf16 tensor-core path
+  kFlagDirectOut = 8u,    // host-mode output written by the kernel into host memory
 };
 
 // Device status words (written to HostShared::status with the place in `where`).

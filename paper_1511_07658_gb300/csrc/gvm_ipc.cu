@@ -479,7 +479,8 @@ int gvm_ipc_serve(gvm_ctx* ctx, gvm_ipc_region* reg, gvm_ipc_server** out) {
     // Page-locked once per region; gvm_ipc_destroy releases it (after the
     // manager has shut down: a resident scheduler holds the device until then).
     if (!reg->seg[r].registered) {
-      if (cudaHostRegister(rs.data, (size_t)rs.s->data_bytes, cudaHostRegisterPortable) != cudaSuccess) {
+      if (cudaHostRegister(rs.data, (size_t)rs.s->data_bytes,
+                                         cudaHostRegisterPortable | cudaHostRegisterMapped) != cudaSuccess) {
         (void)cudaGetLastError();
         rc = GVM_EDEVICE;
         break;

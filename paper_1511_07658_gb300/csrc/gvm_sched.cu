@@ -576,7 +576,12 @@ __global__ void __launch_bounds__(kThreads, 2) sched_fma_kernel(const SchedParam
       if (!early) sh.go[nxt] = 2;
       sh.need[cur] = sh.go[nxt] == 2 ? 1u : 0u;
     }
-    __threadfence();
+    // Results written into host memory: visible to the host before the
+    // task's completion word.
+    if (b.flags & kFlagDirectOut)
+      __threadfence_system();
+    else
+      __threadfence();
     __syncthreads();
     if (sh.abort) {
       if (tid == 0) report_error(p, kStatusTimeout, sh.fail_where, task);
@@ -663,7 +668,12 @@ __device__ void cta_fail(const SchedParams& p, FusedShared& sh, uint32_t where, 
 // tile. Lanes fence their own stores before lane 0 counts the warp.
 __device__ void conv_item_done(const SchedParams& p, FusedShared& sh, uint32_t seq, uint32_t task,
                                uint32_t ntiles, uint32_t tag, uint32_t flags) {
-  __threadfence();
+  // Results written into host memory must be visible to the host before the
+  // task's completion word is.
+  if (flags & kFlagDirectOut)
+    __threadfence_system();
+  else
+    __threadfence();
   __syncwarp();
   if ((threadIdx.x & 31) == 0) {
     uint32_t* f = &sh.fin[seq % kFinSlots];

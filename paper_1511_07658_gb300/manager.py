@@ -257,6 +257,7 @@ class Manager:
         ingest_quantum: int = 4,
         copy_run_bytes: int | None = None,
         vadd_tile: int | None = None,
+        direct_output: bool | None = None,
         device: int | None = None,
     ):
         if not torch.cuda.is_available():
@@ -298,6 +299,7 @@ class Manager:
         tuned = tuning()
         cfg.copy_run_bytes = int(tuned.get("copy_run_bytes", 0) if copy_run_bytes is None else copy_run_bytes)
         cfg.vadd_tile = int(tuned.get("vadd_tile", 0) if vadd_tile is None else vadd_tile)
+        cfg.direct_output = int(bool(tuned.get("direct_output", 0) if direct_output is None else direct_output))
         self.cfg = cfg
         h = c_void_p()
         with torch.cuda.device(self.device):

@@ -70,8 +70,9 @@ def check_result(spec, inputs, out):
             raise AssertionError(f"{spec}: {e}") from None
 
 
-def run_workload(gvm, w, *, mode="barrier", path="split3", depth=16, slice_mb=128):
-    with gvm.Manager(w.ranks, ring_depth=depth, mode=mode, sgemm_path=path, slice_bytes=slice_mb << 20) as mgr:
+def run_workload(gvm, w, *, mode="barrier", path="split3", depth=16, slice_mb=128, direct=False):
+    with gvm.Manager(w.ranks, ring_depth=depth, mode=mode, sgemm_path=path, slice_bytes=slice_mb << 20,
+                     direct_output=direct) as mgr:
         ranks = [mgr.attach(r) for r in range(w.ranks)]
         jobs = []
         for spec in w.tasks:
@@ -184,6 +185,34 @@ def test_paper_stream_modes(gvm, mode, path):
     sched = run_workload(gvm, w, mode="barrier", path=path, depth=8)
     for key in ps:
         assert np.array_equal(bits(ps[key].numpy()), bits(sched[key].numpy())), key
+
+
+@pytest.mark.parametrize("mode", ["barrier", "continuous"])
+@pytest.mark.parametrize("path", ["fma", "split3"])
+def test_direct_output(gvm, mode, path):
+    """Results written by the scheduler straight into the page-locked host
+    buffers (no output staging, no copy): oracle parity, bitwise the same as
+    the staged path, and no staging held for outputs."""
+    w = _ps_mix()
+    direct = run_workload(gvm, w, mode=mode, path=path, depth=8, direct=True)
+    staged = run_workload(gvm, w, mode=mode, path=path, depth=8, direct=False)
+    for key in direct:
+        assert np.array_equal(bits(direct[key].numpy()), bits(staged[key].numpy())), key
+
+
+def test_direct_output_takes_no_output_staging(gvm):
+    n = 1 << 20
+    a, b = synth.vadd_inputs(5, n)
+    ta, tb = pinned(a), pinned(b)
+    for direct, want in ((True, 8 * n), (False, 12 * n)):
+        out = torch.empty(n).pin_memory()
+        with gvm.Manager(1, ring_depth=4, slice_bytes=64 << 20, direct_output=direct) as mgr:
+            rk = mgr.attach(0)
+            seq = rk.submit_vadd(ta, tb, out)
+            assert mgr.stats()["staged_bytes"] == want
+            mgr.flush()
+            rk.sync(seq)
+        assert np.array_equal(bits(out.numpy()), bits(oracle.vadd(a, b)))
 
 
 @pytest.mark.parametrize("mode", ["ps1", "ps2"])
