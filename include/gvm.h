@@ -309,6 +309,21 @@ GVM_API int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* c
                          const uint32_t* counts, int32_t nranks, int32_t steps, float* step_ms_device,
                          float* launch_ms_device, double* step_ms_host);
 
+/* The same pattern with two steps in flight per rank: a rank submits step i
+   + 1 (and, in barrier mode, thread 0 flushes it) before it collects the
+   results of step i, so the copies of consecutive steps overlap on the host
+   link (inputs of one step while the outputs of the one before come back).
+   Even steps use tasks_even[r], odd steps tasks_odd[r] (NULL: tasks_even);
+   give the two distinct output buffers so that a step's results are not
+   overwritten before it is collected. A rank's ring and staging space must
+   hold two batches. *total_ms_host = host time from the first submit to the
+   last step's results; done_ms_host[i] (may be NULL) = when step i's results
+   were all collected, from the same start. Returns GVM_OK or the first error
+   any rank saw. */
+GVM_API int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks_even,
+                                    const gvm_task* const* tasks_odd, const uint32_t* counts, int32_t nranks,
+                                    int32_t steps, double* total_ms_host, double* done_ms_host);
+
 GVM_API const char* gvm_strerror(int code);
 
 /* ---- the task kernels alone -------------------------------------------- */

@@ -153,3 +153,60 @@ extern "C" int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task
       step_ms_host[i] = std::chrono::duration<double, std::milli>(t1[i] - t0[i]).count();
   return rc;
 }
+
+extern "C" int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks_even,
+                                       const gvm_task* const* tasks_odd, const uint32_t* counts, int32_t nranks,
+                                       int32_t steps, double* total_ms_host, double* done_ms_host) {
+  if (!ctx || !ranks || !tasks_even || !counts || nranks <= 0 || steps < 0 || !total_ms_host) return GVM_EINVAL;
+  for (int r = 0; r < nranks; ++r)
+    if (!ranks[r] || (counts[r] && (!tasks_even[r] || (tasks_odd && !tasks_odd[r])))) return GVM_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GVM_EINVAL;
+  SpinBarrier bar(nranks);
+  std::atomic<int> err{GVM_OK};
+  auto fail = [&](int rc) {
+    int ok = GVM_OK;
+    err.compare_exchange_strong(ok, rc);
+  };
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<std::chrono::steady_clock::time_point> t_done(steps);
+  auto body = [&](int r) {
+    cudaSetDevice(dev);
+    std::vector<uint64_t> last(steps, 0);
+    for (int i = 0; i <= steps; ++i) {
+      // Step i: submit (every rank), meet, flush (thread 0), meet.
+      if (i < steps) {
+        const gvm_task* t = (tasks_odd && (i & 1)) ? tasks_odd[r] : tasks_even[r];
+        if (err.load() == GVM_OK && counts[r]) {
+          const int rc = submit_batch(ranks[r], t, counts[r], &last[i]);
+          if (rc != GVM_OK) fail(rc);
+        }
+        bar.wait();
+        if (r == 0 && err.load() == GVM_OK) {
+          const int rc = gvm_flush(ctx);
+          if (rc != GVM_OK) fail(rc);
+        }
+        bar.wait();
+      }
+      // Then the results of step i - 1.
+      if (i >= 1) {
+        if (err.load() == GVM_OK && counts[r]) {
+          const int rc = gvm_sync(ranks[r], last[i - 1]);
+          if (rc != GVM_OK) fail(rc);
+        }
+        bar.wait();
+        if (r == 0) t_done[i - 1] = std::chrono::steady_clock::now();
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  th.reserve(nranks - 1);
+  for (int r = 1; r < nranks; ++r) th.emplace_back(body, r);
+  body(0);
+  for (auto& t : th) t.join();
+  const auto t1 = std::chrono::steady_clock::now();
+  *total_ms_host = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  if (done_ms_host)
+    for (int i = 0; i < steps; ++i) done_ms_host[i] = std::chrono::duration<double, std::milli>(t_done[i] - t0).count();
+  return err.load();
+}

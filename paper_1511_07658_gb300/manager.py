@@ -354,6 +354,24 @@ class Manager:
         check(lib().gvm_spmd_run(self.handle, hs, tp, cnt, n, steps, dev, launch, host), "gvm_spmd_run")
         return list(dev)[:steps], list(launch)[:steps], list(host)[:steps]
 
+    def spmd_run_overlapped(self, ranks, arrays_even, arrays_odd, steps: int) -> tuple[float, list[float]]:
+        """gvm_spmd_run_overlapped: like spmd_run with two steps in flight per
+        rank (step i + 1 submitted before step i is collected); even steps use
+        arrays_even, odd steps arrays_odd (None: the same). Returns (total ms,
+        per-step ms at which each step's results were all collected)."""
+        n = len(ranks)
+        hs = (c_void_p * n)(*[r.handle for r in ranks])
+        te = (ctypes.POINTER(GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(GvmTask)) for a in arrays_even])
+        to = None
+        if arrays_odd is not None:
+            to = (ctypes.POINTER(GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(GvmTask)) for a in arrays_odd])
+        cnt = (ctypes.c_uint32 * n)(*[len(a) for a in arrays_even])
+        total = ctypes.c_double()
+        done = (ctypes.c_double * max(steps, 1))()
+        check(lib().gvm_spmd_run_overlapped(self.handle, hs, te, to, cnt, n, steps, byref(total), done),
+              "gvm_spmd_run_overlapped")
+        return total.value, list(done)[:steps]
+
     def shutdown(self) -> None:
         if self.handle is not None:
             rc = lib().gvm_shutdown(self.handle)

@@ -440,6 +440,48 @@ def test_spmd_harness_steps(gvm, mode):
         assert mgr.stats()["device_status"] == 0
 
 
+@pytest.mark.parametrize("mode", ["barrier", "ps1"])
+def test_spmd_overlapped_steps(gvm, mode):
+    """gvm_spmd_run_overlapped: step i + 1 is submitted and flushed before
+    step i is collected; even and odd steps write separate host outputs, and
+    both hold the oracle's results afterwards."""
+    R, per = 4, 5
+    specs = []
+    for r in range(R):
+        for i in range(per):
+            if i % 2 == 0:
+                specs.append(synth.TaskSpec(r, i, synth.TASK_SGEMM, m=130 + r, n=200, k=96, seed=synth.task_seed(r, i)))
+            else:
+                specs.append(synth.TaskSpec(r, i, synth.TASK_VMUL, n=30001 + r, k=15, seed=synth.task_seed(r, i)))
+    with gvm.Manager(R, ring_depth=16, mode=mode, sgemm_path="split3", slice_bytes=32 << 20) as mgr:
+        ranks = [mgr.attach(r) for r in range(R)]
+        even = [(gvm.GvmTask * per)() for _ in range(R)]
+        odd = [(gvm.GvmTask * per)() for _ in range(R)]
+        keep = []
+        for spec in specs:
+            if spec.kind == synth.TASK_SGEMM:
+                A, B = synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
+                ins, shape = (pinned(A), pinned(B)), (spec.m, spec.n)
+            else:
+                a, b = synth.vmul_inputs(spec.seed, spec.n)
+                ins, shape = (pinned(a), pinned(b)), (spec.n,)
+            outs = (torch.full(shape, float("nan")).pin_memory(), torch.full(shape, float("nan")).pin_memory())
+            for arr, out in ((even, outs[0]), (odd, outs[1])):
+                t = arr[spec.rank][spec.index]
+                t.type = gvm.GVM_TASK_SGEMM if spec.kind == synth.TASK_SGEMM else gvm.GVM_TASK_VMUL
+                t.flags = 0
+                t.m, t.n, t.k = spec.m, spec.n, spec.k
+                t.a, t.b, t.c = ins[0].data_ptr(), ins[1].data_ptr(), out.data_ptr()
+            keep.append((spec, ins, outs))
+        total, done = mgr.spmd_run_overlapped(ranks, even, odd, 5)
+        assert total > 0 and len(done) == 5 and all(x > 0 for x in done)
+        assert done == sorted(done) and done[-1] <= total
+        assert mgr.stats()["device_status"] == 0
+    for spec, ins, outs in keep:
+        for out in outs:
+            check_result(spec, (ins[0].numpy(), ins[1].numpy()), out)
+
+
 @pytest.mark.parametrize("slice_mb", [64, 2])
 def test_batch_from_contiguous_host_blocks(gvm, slice_mb):
     # A rank's operands in one pinned block (A then B per task) and its
