@@ -210,6 +210,27 @@ def ncu_traffic(key):
     return e.get("bytes_per_launch")
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest value of x over the ranks of the process group (the time
+    of the slowest rank); x itself when running alone. NCCL reduces a CUDA
+    tensor, gloo a CPU one."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, slowest_s: float) -> float:
+    """Units all ranks processed per second of the slowest rank (ranks run
+    independent replicas of the workload: weak scaling)."""
+    return units_per_rank_step * steps * world / slowest_s
+
+
 def percentile(xs, q):
     if not xs:
         return None
@@ -591,10 +612,8 @@ def gpu_arm(args, w, desc, rank, world):
             lat.append((t1 - t0) / 1e3)
     tasks_per_step = len(w.tasks)
     if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = tasks_per_step * args.steps * world / total_s
+        total_s = max_over_ranks(total_s, world)
+    value = whole_job_rate(tasks_per_step, args.steps, world, total_s)
     stats_after_value = mgr.stats()
     st = stats_after_value
     ph = st["launch_phase"]
@@ -635,13 +654,11 @@ def gpu_arm(args, w, desc, rank, world):
         mgr2.shutdown()
         h_s = total_ms / 1e3
         if world > 1:
-            t = torch.tensor([h_s], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            h_s = float(t.item())
+            h_s = max_over_ranks(h_s, world)
         h2d = sum(sizes[k][0] + sizes[k][1] for k in sizes)
         d2h = sum(sizes[k][2] for k in sizes)
         e2e = {
-            "value": tasks_per_step * e_steps * world / h_s,
+            "value": whole_job_rate(tasks_per_step, e_steps, world, h_s),
             "unit": "tasks/s",
             "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h,
@@ -667,13 +684,11 @@ def gpu_arm(args, w, desc, rank, world):
                 run_step(mgr, ranks, host_arrays, pool, record=not cont)
         h_s = time.perf_counter() - h0
         if world > 1:
-            t = torch.tensor([h_s], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            h_s = float(t.item())
+            h_s = max_over_ranks(h_s, world)
         h2d = sum(sizes[k][0] + sizes[k][1] for k in sizes)
         d2h = sum(sizes[k][2] for k in sizes)
         e2e = {
-            "value": tasks_per_step * e_steps * world / h_s,
+            "value": whole_job_rate(tasks_per_step, e_steps, world, h_s),
             "unit": "tasks/s",
             "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h,
