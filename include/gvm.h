@@ -153,8 +153,13 @@ typedef struct gvm_task {
   int32_t m;      /* SGEMM: rows of A and C (>= 1) */
   int32_t k;      /* SGEMM: columns of A, rows of B (>= 1). VMUL: products per element
                      (1 .. 1024) */
-  /* host mode (flags without GVM_TASK_RESIDENT): page-locked host buffers,
-     caller-owned, valid and untouched until gvm_sync returns for this task.
+  /* host mode (flags without GVM_TASK_RESIDENT): host buffers, caller-owned,
+     valid and untouched until gvm_sync returns for this task. Page-locked
+     buffers are copied asynchronously; pageable ones are accepted too (the
+     driver stages their input copies, and a pageable result is copied out by
+     the rank's gvm_sync / gvm_poll once the task has completed). Device or
+     managed memory is refused (GVM_EINVAL): a rank reaches the GPU only
+     through the manager's copies.
      VADD, VMUL: a, b, c hold n floats. SGEMM: a = A (m*k), b = B (k*n), c = C (m*n). */
   const void* a;
   const void* b;

@@ -47,6 +47,9 @@ struct SlotInfo {
   const void* b_host = nullptr;
   uint64_t a_dev = 0, b_dev = 0, a_bytes = 0, b_bytes = 0;
   bool host_io = false;
+  // Output in pageable host memory: the task completes on the device with
+  // its result in staging; reap copies it out before reporting it.
+  bool out_pageable = false;
 };
 
 inline uint32_t tag_of(uint64_t seq) { return (uint32_t)(seq + 1); }
@@ -94,6 +97,7 @@ struct gvm_rank {
   uint64_t ring_base = 0, ring_bytes = 0;
   uint64_t ring_head = 0, ring_tail = 0;  // monotonic byte counters
   std::vector<SlotInfo> slots;
+  bool copy_failed = false;  // a pageable output could not be copied out
   cudaStream_t in_stream = nullptr, out_stream = nullptr;
   std::mutex mu;
 };
@@ -191,6 +195,19 @@ void reap(gvm_rank* r) {
     const uint32_t idx = (uint32_t)r->id * D + (uint32_t)(s & (D - 1));
     if (ld_acq(&ctx->completes[idx].tag) != tag_of(s)) break;
     SlotInfo& si = r->slots[s & (D - 1)];
+    if (si.out_pageable) {
+      // The result waits in staging: copy it to the caller's pageable buffer
+      // now (the input stream carries only copies, so waiting on it ends).
+      cudaError_t e = cudaMemcpyAsync(si.c_host, reinterpret_cast<const void*>(si.c_dev), si.c_bytes,
+                                      cudaMemcpyDeviceToHost, r->in_stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(r->in_stream);
+      if (e != cudaSuccess) {
+        r->copy_failed = true;
+        break;
+      }
+      ctx->d2h.fetch_add(si.c_bytes);
+      si.out_pageable = false;
+    }
     if (si.bytes) {
       r->ring_tail = si.stage_end;
       ctx->staged.fetch_sub(si.bytes);
@@ -420,13 +437,18 @@ int ps_flush_locked(gvm_ctx* ctx) {
   return GVM_OK;
 }
 
-bool is_pinned(const void* p) {
+// 1: page-locked host memory; 0: pageable host memory; -1: device or managed
+// memory, which a task may not name (a rank reaches the GPU only through the
+// manager's copies).
+int host_kind(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     (void)cudaGetLastError();
-    return false;
+    return 0;
   }
-  return a.type == cudaMemoryTypeHost;
+  if (a.type == cudaMemoryTypeHost) return 1;
+  if (a.type == cudaMemoryTypeUnregistered) return 0;
+  return -1;
 }
 
 }  // namespace
@@ -620,6 +642,7 @@ struct Prep {
   const gvm_task* t;
   bool resident;
   uint64_t c_direct;                   // device address of c when the kernel writes it there, else 0
+  bool out_pageable;                   // c is pageable: copied out by the host after completion
   uint64_t bytes_a, bytes_b, bytes_c;  // operand bytes
   uint64_t sa, sb, sc;                 // staging bytes (256-aligned; 0 when resident)
 };
@@ -627,6 +650,7 @@ struct Prep {
 // Shape, offset and pointer checks of one task (nothing is reserved).
 int prep_task(gvm_rank* r, const gvm_task* t, Prep* p) {
   const bool resident = (t->flags & GVM_TASK_RESIDENT) != 0;
+  int p_kc = 1;  // kind of the output buffer (host_kind)
   if (t->flags & ~GVM_TASK_RESIDENT) return GVM_EINVAL;
   uint64_t bytes_a = 0, bytes_b = 0, bytes_c = 0;
   if (t->type == GVM_TASK_VADD || t->type == GVM_TASK_VMUL) {
@@ -652,7 +676,9 @@ int prep_task(gvm_rank* r, const gvm_task* t, Prep* p) {
     }
   } else if (bytes_c > 0) {
     if (!t->a || !t->b || !t->c) return GVM_EINVAL;
-    if (!is_pinned(t->a) || !is_pinned(t->b) || !is_pinned(t->c)) return GVM_EINVAL;
+    const int ka = host_kind(t->a), kb = host_kind(t->b), kc = host_kind(t->c);
+    if (ka < 0 || kb < 0 || kc < 0) return GVM_EINVAL;
+    p_kc = kc;
   }
   p->t = t;
   p->resident = resident;
@@ -660,7 +686,8 @@ int prep_task(gvm_rank* r, const gvm_task* t, Prep* p) {
   p->bytes_b = bytes_b;
   p->bytes_c = bytes_c;
   p->c_direct = 0;
-  if (!resident && bytes_c > 0 && r->ctx->cfg.direct_output && !stream_mode(r->ctx)) {
+  p->out_pageable = !resident && bytes_c > 0 && p_kc == 0 && !stream_mode(r->ctx);
+  if (!resident && bytes_c > 0 && p_kc == 1 && r->ctx->cfg.direct_output && !stream_mode(r->ctx)) {
     // The buffer's device mapping (the same address under unified addressing).
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, t->c) == cudaSuccess && at.devicePointer != nullptr)
@@ -692,7 +719,10 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
   body->rank = (uint32_t)r->id;
   body->slot = (uint32_t)(seq & (D - 1));
   body->tag = tag_of(seq);
-  body->flags = p.resident ? 0u : p.c_direct ? (kFlagNeedsReady | kFlagDirectOut) : (kFlagNeedsReady | kFlagNeedsD2H);
+  body->flags = p.resident         ? 0u
+                : p.c_direct       ? (kFlagNeedsReady | kFlagDirectOut)
+                : p.out_pageable   ? kFlagNeedsReady  // completes on the device; reap copies C out
+                                   : (kFlagNeedsReady | kFlagNeedsD2H);
   body->a = da;
   body->b = db;
   body->c = dc;
@@ -842,7 +872,8 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* f
     SlotInfo& si = r->slots[slot];
     si.bytes = (i == last_host) ? held : 0;
     si.stage_end = r->ring_head;
-    si.needs_out = !p.resident && !stream_mode(ctx) && !p.c_direct;
+    si.needs_out = !p.resident && !stream_mode(ctx) && !p.c_direct && !p.out_pageable;
+    si.out_pageable = p.out_pageable;
     if (p.c_direct) ctx->d2h.fetch_add(p.bytes_c);  // written by the kernel
     si.c_host = t->c;
     si.c_dev = dc;
@@ -964,6 +995,7 @@ int gvm_poll(gvm_rank* r, uint64_t seq) {
   if (push_flushed(r) != GVM_OK) return GVM_EDEVICE;
   reap(r);
   if (r->synced > seq) return 1;
+  if (r->copy_failed) return GVM_EDEVICE;
   const uint32_t D = (uint32_t)r->ctx->cfg.ring_depth;
   const uint32_t idx = (uint32_t)r->id * D + (uint32_t)(seq & (D - 1));
   if (seq + D >= r->next_seq && ld_acq(&r->ctx->completes[idx].tag) == tag_of(seq)) return 1;
@@ -987,6 +1019,7 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
   while (true) {
     reap(r);
     if (r->synced > seq) return GVM_OK;
+    if (r->copy_failed) return GVM_EDEVICE;
     if (ld_acq(&ctx->shared->status)) return GVM_EDEVICE;
     const uint64_t now = now_ns();
     if (r->synced != last) {

@@ -215,6 +215,49 @@ def test_direct_output_takes_no_output_staging(gvm):
         assert np.array_equal(bits(out.numpy()), bits(oracle.vadd(a, b)))
 
 
+@pytest.mark.parametrize("mode", ["barrier", "continuous", "ps1"])
+def test_pageable_host_buffers(gvm, mode):
+    """Host-mode tasks on pageable (not page-locked) buffers, alone and mixed
+    with page-locked ones: results equal the oracle's."""
+    specs = [("vadd", 70001), ("vmul", 4099), ("sgemm", (130, 257, 65)), ("sgemm", (256, 256, 256))]
+    with gvm.Manager(2, ring_depth=8, mode=mode, sgemm_path="split3", slice_bytes=32 << 20) as mgr:
+        ranks = [mgr.attach(r) for r in range(2)]
+        jobs = []
+        for r, rk in enumerate(ranks):
+            for i, (kind, shape) in enumerate(specs):
+                pin = (r + i) % 2 == 0  # half page-locked, half pageable
+                mk = (lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()) if pin else \
+                     (lambda x: torch.from_numpy(np.ascontiguousarray(x)).clone())
+                seed = synth.task_seed(r, 50 + i)
+                if kind == "sgemm":
+                    m, n, k = shape
+                    A, B = synth.sgemm_inputs(seed, m, n, k)
+                    ta, tb = mk(A), mk(B)
+                    out = torch.full((m, n), float("nan"))
+                    out = out.pin_memory() if pin else out
+                    seq = rk.submit_sgemm(ta, tb, out)
+                    spec = synth.TaskSpec(r, i, synth.TASK_SGEMM, m=m, n=n, k=k)
+                    jobs.append((rk, seq, spec, (A, B, ta, tb), out))
+                else:
+                    n = shape
+                    a, b = synth.vmul_inputs(seed, n) if kind == "vmul" else synth.vadd_inputs(seed, n)
+                    ta, tb = mk(a), mk(b)
+                    out = torch.full((n,), float("nan"))
+                    out = out.pin_memory() if pin else out
+                    if kind == "vmul":
+                        seq = rk.submit_vmul(ta, tb, out, 15)
+                        spec = synth.TaskSpec(r, i, synth.TASK_VMUL, n=n, k=15)
+                    else:
+                        seq = rk.submit_vadd(ta, tb, out)
+                        spec = synth.TaskSpec(r, i, synth.TASK_VADD, n=n)
+                    jobs.append((rk, seq, spec, (a, b, ta, tb), out))
+        mgr.flush_if_barrier()
+        for rk, seq, spec, inputs, out in jobs:
+            rk.sync(seq)
+            check_result(spec, inputs, out)
+        assert mgr.stats()["device_status"] == 0
+
+
 @pytest.mark.parametrize("mode", ["ps1", "ps2"])
 def test_paper_stream_modes_barrier_rules(gvm, mode):
     """A task submitted after the last gvm_flush does not run: gvm_sync says
@@ -329,8 +372,8 @@ def test_errors_and_backpressure(gvm):
         with pytest.raises(gvm.GvmError) as e:
             mgr.attach(0)
         assert e.value.code == gvm.GVM_EBUSY
-        # pageable host buffers are refused
-        a = torch.zeros(16)
+        # device memory may not be named by a host-mode task
+        a = torch.zeros(16, device="cuda")
         with pytest.raises(gvm.GvmError) as e:
             rk.submit_vadd(a, a, a)
         assert e.value.code == gvm.GVM_EINVAL
