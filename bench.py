@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gvm", "reference"], default="gvm")
-    p.add_argument("--workload", choices=["sgemm512", "vadd_tiny", "serving", "grouped"], default="sgemm512")
+    p.add_argument("--workload", choices=["sgemm512", "vadd_tiny", "serving", "grouped", "stress"], default="sgemm512")
     p.add_argument("--serving-tasks", type=int, default=0, help="serving workload: total tasks (default 4096)")
     p.add_argument("--path", choices=["split3", "fma"], default="split3")
     p.add_argument("--mode", choices=["barrier", "continuous"], default="barrier")
@@ -947,6 +947,48 @@ def plain_per_rank(w):
 # --------------------------------------------------------------- serving loop
 
 
+def _open_loop(mgr, w, depth, vin, gin, outs):
+    """Every rank of w as a native thread (gvm_open_loop_run): at each task's
+    scheduled arrival it submits (host mode), keeping at most `depth` of its
+    tasks in flight, and reaps completions as they come. Returns (span
+    seconds from the start to the last completion, latencies in seconds =
+    completion seen by the rank minus scheduled arrival, host-link bytes).
+
+    vin = (a, b) page-locked vector operands at least as long as the longest
+    vector task; gin(side) -> (A, B) page-locked operands for a square SGEMM;
+    outs[r][slot] a page-locked output buffer big enough for the rank's tasks
+    (task i of a rank writes slot i mod depth: with at most depth in flight,
+    the slot's previous task has completed).
+    """
+    import paper_1511_07658_gb300 as g
+
+    R = w.ranks
+    ranks = [mgr.attach(r) for r in range(R)]
+    by_rank = w.by_rank()
+    arrays, arrivals, moved = [], [], 0
+    for r in range(R):
+        lst = by_rank[r]
+        arr = (g.GvmTask * max(len(lst), 1))()
+        for i, spec in enumerate(lst):
+            t = arr[i]
+            out = outs[r][i % depth]
+            if spec.kind == synth.TASK_VADD:
+                t.type, t.n = g.GVM_TASK_VADD, spec.n
+                t.a, t.b, t.c = vin[0].data_ptr(), vin[1].data_ptr(), out.data_ptr()
+                moved += 12 * spec.n
+            else:
+                A, B = gin(spec.m)
+                t.type, t.m, t.n, t.k = g.GVM_TASK_SGEMM, spec.m, spec.n, spec.k
+                t.a, t.b, t.c = A.data_ptr(), B.data_ptr(), out.data_ptr()
+                moved += 12 * spec.m * spec.m
+        arrays.append(arr if lst else (g.GvmTask * 0)())
+        arrivals.append([int(spec.arrival_s * 1e9) for spec in lst])
+    span, lat = mgr.open_loop_run(ranks, arrays, arrivals, max_inflight=depth)
+    for rk in ranks:
+        rk.detach()
+    return span, sorted(x for l in lat for x in l), moved
+
+
 def serving_arm(args):
     """Open-loop serving: 16 ranks, 4096 tasks, Poisson arrivals with a mean
     gap of 20 us per rank, half vector adds (n = floor(2^(16+8u))) and half
@@ -954,9 +996,9 @@ def serving_arm(args):
     32 GiB of device buffers. The manager runs in continuous mode: tasks are
     admitted as ring slots and staging space free up while others run.
 
-    Latency of a task = the moment its rank observes completion minus its
-    scheduled arrival time (so a rank that falls behind does not hide queueing
-    delay). Operands: per size, one seeded input set shared by every task of
+    Ranks run as native threads (gvm_open_loop_run). Latency of a task = the
+    moment its rank observes completion minus its scheduled arrival time (so
+    a rank that falls behind does not hide queueing delay). Operands: per size, one seeded input set shared by every task of
     that size (the latency and throughput do not depend on values; parity of
     the mix is covered by the GPU tests); outputs go to per-rank pinned
     buffers, one per in-flight slot.
@@ -984,67 +1026,7 @@ def serving_arm(args):
     mgr = g.Manager(R, ring_depth=depth, mode="continuous", sgemm_path=args.path,
                     slice_bytes=per_task * 2 + (64 << 20), admission_cap_bytes=32 << 30,
                     ingest_quantum=args.quantum)
-    ranks = [mgr.attach(r) for r in range(R)]
-    by_rank = w.by_rank()
-    lat = [[] for _ in range(R)]
-    done_at = [0.0] * R
-    bytes_moved = [0] * R
-    start = time.perf_counter() + 0.05
-
-    def run_rank(r):
-        rk = ranks[r]
-        inflight = []  # (seq, arrival, slot)
-        free = list(range(depth))
-
-        def reap(block):
-            while inflight:
-                seq, arr, slot = inflight[0]
-                if block:
-                    rk.sync(seq)
-                elif not rk.poll(seq):
-                    return
-                lat[r].append(time.perf_counter() - arr)
-                free.append(slot)
-                inflight.pop(0)
-                if block:
-                    return
-
-        for spec in by_rank[r]:
-            arrival = start + spec.arrival_s
-            while True:
-                reap(False)
-                if time.perf_counter() >= arrival and free:
-                    break
-                if not free and inflight:
-                    reap(True)
-            slot = free.pop()
-            t = g.GvmTask()
-            if spec.kind == synth.TASK_VADD:
-                t.type, t.n = g.GVM_TASK_VADD, spec.n
-                t.a, t.b, t.c = va.data_ptr(), vb.data_ptr(), outs[r][slot].data_ptr()
-                bytes_moved[r] += 12 * spec.n
-            else:
-                A, B = gin[spec.m]
-                t.type, t.m, t.n, t.k = g.GVM_TASK_SGEMM, spec.m, spec.n, spec.k
-                t.a, t.b, t.c = A.data_ptr(), B.data_ptr(), outs[r][slot].data_ptr()
-                bytes_moved[r] += 12 * spec.m * spec.m
-            while True:
-                seq = c_uint64_holder()
-                rc = g.lib().gvm_submit(rk.handle, ctypes.byref(t), ctypes.byref(seq))
-                if rc == g.GVM_EAGAIN:
-                    reap(True) if inflight else time.sleep(0)
-                    continue
-                g._abi.check(rc, "gvm_submit")
-                break
-            inflight.append((seq.value, arrival, slot))
-        while inflight:
-            reap(True)
-        done_at[r] = time.perf_counter()
-
-    with ThreadPoolExecutor(max_workers=R) as ex:
-        list(ex.map(run_rank, range(R)))
-    span = max(done_at) - start
-    all_lat = sorted(x for l in lat for x in l)
+    span, all_lat, moved = _open_loop(mgr, w, depth, (va, vb), lambda sd: gin[sd], outs)
     st = mgr.stats()
     mgr.shutdown()
     total = len(w.tasks)
@@ -1061,9 +1043,84 @@ def serving_arm(args):
                    "mode": "continuous", "sgemm_path": args.path, "ring_depth": depth},
         "latency_us": {"p50": 1e6 * percentile(all_lat, 50), "p99": 1e6 * percentile(all_lat, 99),
                        "p999": 1e6 * percentile(all_lat, 99.9), "kind": "scheduled arrival -> completion seen by the rank"},
-        "host_link_gbs": sum(bytes_moved) / span / 1e9,
+        "host_link_gbs": moved / span / 1e9,
         "staged_peak_bytes": st["staged_peak"],
         "device_status": st["device_status"],
+    }
+
+
+def stress_arm(args):
+    """Open-loop stress (the lognormal mix): 128 ranks, 70% vector add with n
+    = round(2^20 e^(1.5 Z)) and 30% square SGEMM with side round(768
+    e^(0.7 Z)) in [64, 4096], Poisson arrivals, admission capped at 120 GiB,
+    continuous mode. Vector lengths are clamped to [2^10, 2^24] here: at 128
+    ranks a rank's staging slice holds about half a gigabyte, and a 2^28
+    vector add stages 3 GiB. First the capacity: every task arrives at once
+    (tasks/s over the whole run). Then the same task list at 0.8 x that
+    capacity (Poisson gaps), with p50/p99/p999 latency. Operands come from one
+    seeded page-locked buffer per kind (a task reads a prefix of it as a dense
+    operand); outputs share a pool of page-locked buffers, one per rank slot
+    group (values are not checked here; the mix's parity is covered by the
+    GPU tests)."""
+    import torch
+
+    import paper_1511_07658_gb300 as g
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    R, P, depth = 128, args.per_rank or 16, 2
+    w0 = synth.stress_mix(ranks=R, per_rank=P, rate_per_rank_hz=1e9)
+    for t in w0.tasks:  # the clamp of this leg
+        if t.kind == synth.TASK_VADD:
+            t.n = min(t.n, 1 << 24)
+    vmax = max(t.n for t in w0.tasks if t.kind == synth.TASK_VADD)
+    smax = max(t.m for t in w0.tasks if t.kind == synth.TASK_SGEMM)
+    a, b = synth.vadd_inputs(5151, vmax)
+    vin = (torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory())
+    A, B = synth.sgemm_inputs(6161, smax, smax, smax)
+    gA, gB = torch.from_numpy(A).reshape(-1).pin_memory(), torch.from_numpy(B).reshape(-1).pin_memory()
+    out_elems = max(vmax, smax * smax)
+    pool = [torch.empty(out_elems).pin_memory() for _ in range(16)]
+    outs = [[pool[(r * depth + s) % len(pool)] for s in range(depth)] for r in range(R)]
+    per_task = max(12 * vmax, 12 * smax * smax) + (1 << 20)
+
+    def run(w):
+        mgr = g.Manager(R, ring_depth=depth, mode="continuous", sgemm_path=args.path,
+                        slice_bytes=per_task * depth + (16 << 20), admission_cap_bytes=120 << 30,
+                        ingest_quantum=args.quantum)
+        try:
+            span, lat, moved = _open_loop(mgr, w, depth, vin, lambda sd: (gA, gB), outs)
+            st = mgr.stats()
+        finally:
+            mgr.shutdown()
+        return span, lat, moved, st
+
+    span0, _, moved0, _ = run(w0)
+    capacity = len(w0.tasks) / span0
+    rate = 0.8 * capacity / R
+    w1 = synth.stress_mix(ranks=R, per_rank=P, rate_per_rank_hz=rate)
+    for t0, t1 in zip(w0.tasks, w1.tasks):
+        t1.n, t1.m, t1.k = t0.n, t0.m, t0.k  # same tasks, paced arrivals
+    span1, lat1, moved1, st1 = run(w1)
+    return {
+        "metric": METRIC + " (stress loop)",
+        "value": capacity,
+        "unit": "tasks/s",
+        "n_gpus": 1,
+        "higher_is_better": True,
+        "dtype": "bf16x3->f32" if args.path == "split3" else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"stress mix: {R} ranks x {P} tasks, 70% vector add n = 2^20 e^(1.5Z) in "
+                   "[2^10, 2^24], 30% square SGEMM side 768 e^(0.7Z) in [64, 4096], cap 120 GiB",
+                   "mode": "continuous", "sgemm_path": args.path, "ring_depth": depth},
+        "capacity": {"tasks_per_s": capacity, "host_link_gbs": moved0 / span0 / 1e9, "seconds": span0},
+        "at_0.8_capacity": {
+            "offered_tasks_per_s": 0.8 * capacity, "served_tasks_per_s": len(w1.tasks) / span1,
+            "last_arrival_s": max(t.arrival_s for t in w1.tasks), "span_s": span1,
+            "latency_us": {"p50": 1e6 * percentile(lat1, 50), "p99": 1e6 * percentile(lat1, 99),
+                           "p999": 1e6 * percentile(lat1, 99.9),
+                           "kind": "scheduled arrival -> completion seen by the rank"},
+            "host_link_gbs": moved1 / span1 / 1e9, "staged_peak_bytes": st1["staged_peak"],
+            "device_status": st1["device_status"]},
     }
 
 
@@ -1491,6 +1548,13 @@ def main():
                 print(json.dumps({"impl": "reference", "unavailable": "the grouped config has no CPU reference arm"}))
             return
         print(json.dumps(grouped_arm(args)))
+        return
+    if args.workload == "stress":
+        if args.impl == "reference" or rank != 0:
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the stress loop has no CPU reference arm"}))
+            return
+        print(json.dumps(stress_arm(args)))
         return
     if args.workload == "serving":
         if args.impl == "reference" or rank != 0:

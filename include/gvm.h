@@ -329,6 +329,19 @@ GVM_API int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, const 
                                     const gvm_task* const* tasks_odd, const uint32_t* counts, int32_t nranks,
                                     int32_t steps, double* total_ms_host, double* done_ms_host);
 
+/* Open-loop serving harness (continuous mode): one native thread per rank
+   submits tasks[r][i] at its scheduled arrival arrival_ns[r][i] (nanoseconds
+   after a common start, non-decreasing per rank), keeping at most
+   max_inflight of its tasks outstanding (0: as many as the ring admits), and
+   reaps completions in order as it goes (gvm_poll between arrivals;
+   gvm_sync when it must wait). latency_ns[r][i] (may be NULL) = the moment
+   rank r saw task i complete minus its scheduled arrival, so a rank that falls
+   behind does not hide queueing delay. *span_ns = from the start to the last
+   completion seen. Returns GVM_OK or the first error any rank saw. */
+GVM_API int gvm_open_loop_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks,
+                              const uint64_t* const* arrival_ns, const uint32_t* counts, int32_t nranks,
+                              uint32_t max_inflight, double* const* latency_ns, double* span_ns);
+
 GVM_API const char* gvm_strerror(int code);
 
 /* ---- the task kernels alone -------------------------------------------- */

@@ -150,6 +150,11 @@ PROTOTYPES = {
         [c_void_p, POINTER(c_void_p), POINTER(POINTER(GvmTask)), POINTER(POINTER(GvmTask)), POINTER(c_uint32),
          c_int32, c_int32, POINTER(c_double), POINTER(c_double)],
     ),
+    "gvm_open_loop_run": (
+        c_int,
+        [c_void_p, POINTER(c_void_p), POINTER(POINTER(GvmTask)), POINTER(POINTER(c_uint64)), POINTER(c_uint32),
+         c_int32, c_uint32, POINTER(POINTER(c_double)), POINTER(c_double)],
+    ),
     "gvm_strerror": (c_char_p, [c_int]),
     "gvm_vadd_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "gvm_vmul_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p]),

@@ -210,3 +210,93 @@ extern "C" int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, con
     for (int i = 0; i < steps; ++i) done_ms_host[i] = std::chrono::duration<double, std::milli>(t_done[i] - t0).count();
   return err.load();
 }
+
+extern "C" int gvm_open_loop_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks,
+                                 const uint64_t* const* arrival_ns, const uint32_t* counts, int32_t nranks,
+                                 uint32_t max_inflight, double* const* latency_ns, double* span_ns) {
+  if (!ctx || !ranks || !tasks || !arrival_ns || !counts || nranks <= 0 || !span_ns) return GVM_EINVAL;
+  for (int r = 0; r < nranks; ++r) {
+    if (!ranks[r] || (counts[r] && (!tasks[r] || !arrival_ns[r]))) return GVM_EINVAL;
+    for (uint32_t i = 1; i < counts[r]; ++i)
+      if (arrival_ns[r][i] < arrival_ns[r][i - 1]) return GVM_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GVM_EINVAL;
+  using clk = std::chrono::steady_clock;
+  std::atomic<int> err{GVM_OK};
+  auto fail = [&](int rc) {
+    int ok = GVM_OK;
+    err.compare_exchange_strong(ok, rc);
+  };
+  const clk::time_point t0 = clk::now() + std::chrono::milliseconds(2);
+  std::vector<clk::time_point> last(nranks, t0);
+  auto ns_since = [&](clk::time_point t) { return (double)std::chrono::duration_cast<std::chrono::nanoseconds>(t - t0).count(); };
+  auto body = [&](int r) {
+    cudaSetDevice(dev);
+    gvm_rank* rk = ranks[r];
+    const uint32_t n = counts[r];
+    std::vector<uint64_t> seq(n, 0);
+    uint32_t next = 0, done = 0;  // tasks submitted, tasks seen complete
+    auto seen = [&](uint32_t i) {
+      const clk::time_point t = clk::now();
+      if (latency_ns && latency_ns[r]) latency_ns[r][i] = ns_since(t) - (double)arrival_ns[r][i];
+      last[r] = t;
+    };
+    auto reap_ready = [&]() {
+      while (done < next) {
+        const int p = gvm_poll(rk, seq[done]);
+        if (p < 0) {
+          fail(p);
+          return;
+        }
+        if (p == 0) return;
+        seen(done++);
+      }
+    };
+    auto reap_one = [&]() {  // blocking: the oldest outstanding task
+      const int s = gvm_sync(rk, seq[done]);
+      if (s != GVM_OK) {
+        fail(s);
+        return;
+      }
+      seen(done++);
+    };
+    while (next < n && err.load() == GVM_OK) {
+      const clk::time_point due = t0 + std::chrono::nanoseconds(arrival_ns[r][next]);
+      // Until the arrival: collect completions, then wait (sleep when far).
+      for (;;) {
+        reap_ready();
+        const clk::time_point now = clk::now();
+        if (now >= due || err.load() != GVM_OK) break;
+        if (due - now > std::chrono::microseconds(200))
+          std::this_thread::sleep_for(std::chrono::microseconds(50));
+        else
+          std::this_thread::yield();
+      }
+      if (max_inflight && next - done >= max_inflight) reap_one();
+      for (;;) {
+        const int rc = gvm_submit(rk, &tasks[r][next], &seq[next]);
+        if (rc == GVM_OK) break;
+        if (rc != GVM_EAGAIN || done == next) {  // nothing of this rank left to wait for
+          fail(rc);
+          break;
+        }
+        reap_one();
+        if (err.load() != GVM_OK) break;
+      }
+      if (err.load() != GVM_OK) break;
+      ++next;
+    }
+    while (done < next && err.load() == GVM_OK) reap_one();
+  };
+  std::vector<std::thread> th;
+  th.reserve(nranks - 1);
+  for (int r = 1; r < nranks; ++r) th.emplace_back(body, r);
+  body(0);
+  for (auto& t : th) t.join();
+  clk::time_point end = t0;
+  for (const auto& t : last)
+    if (t > end) end = t;
+  *span_ns = ns_since(end);
+  return err.load();
+}

@@ -372,6 +372,24 @@ class Manager:
               "gvm_spmd_run_overlapped")
         return total.value, list(done)[:steps]
 
+    def open_loop_run(self, ranks, task_arrays, arrival_ns, max_inflight: int = 0):
+        """gvm_open_loop_run: rank i submits task_arrays[i][j] (ctypes arrays
+        of GvmTask) at arrival_ns[i][j] ns after a common start (one native
+        thread per rank). Returns (span seconds, per-rank latency lists in
+        seconds: completion seen minus scheduled arrival)."""
+        n = len(ranks)
+        hs = (c_void_p * n)(*[r.handle for r in ranks])
+        tp = (ctypes.POINTER(GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(GvmTask)) for a in task_arrays])
+        arr = [(ctypes.c_uint64 * max(len(a), 1))(*[int(x) for x in a]) for a in arrival_ns]
+        ap = (ctypes.POINTER(ctypes.c_uint64) * n)(*[ctypes.cast(a, ctypes.POINTER(ctypes.c_uint64)) for a in arr])
+        cnt = (ctypes.c_uint32 * n)(*[len(a) for a in task_arrays])
+        lat = [(ctypes.c_double * max(len(a), 1))() for a in task_arrays]
+        lp = (ctypes.POINTER(ctypes.c_double) * n)(*[ctypes.cast(x, ctypes.POINTER(ctypes.c_double)) for x in lat])
+        span = ctypes.c_double()
+        check(lib().gvm_open_loop_run(self.handle, hs, tp, ap, cnt, n, max_inflight, lp, byref(span)),
+              "gvm_open_loop_run")
+        return span.value / 1e9, [[v / 1e9 for v in list(l)[: len(a)]] for l, a in zip(lat, task_arrays)]
+
     def shutdown(self) -> None:
         if self.handle is not None:
             rc = lib().gvm_shutdown(self.handle)

@@ -525,6 +525,47 @@ def test_spmd_overlapped_steps(gvm, mode):
             check_result(spec, (ins[0].numpy(), ins[1].numpy()), out)
 
 
+@pytest.mark.parametrize("max_inflight", [1, 3])
+def test_open_loop_harness(gvm, max_inflight):
+    """gvm_open_loop_run (continuous mode): paced arrivals, at most
+    max_inflight tasks per rank outstanding; every result equals the
+    oracle's, every latency is non-negative, the span covers the arrivals."""
+    R, per = 4, 6
+    w = synth.stress_mix(ranks=R, per_rank=per, vadd_median=4096, side_median=96, rate_per_rank_hz=5000.0)
+    with gvm.Manager(R, ring_depth=8, mode="continuous", sgemm_path="split3", slice_bytes=16 << 20) as mgr:
+        ranks = [mgr.attach(r) for r in range(R)]
+        by_rank = w.by_rank()
+        arrays, arrivals, keep = [], [], []
+        for r in range(R):
+            arr = (gvm.GvmTask * per)()
+            for i, spec in enumerate(by_rank[r]):
+                t = arr[i]
+                seq, inputs, out = None, None, None
+                if spec.kind == synth.TASK_VADD:
+                    a, b = synth.vadd_inputs(spec.seed, spec.n)
+                    ins = (pinned(a), pinned(b))
+                    out = torch.full((spec.n,), float("nan")).pin_memory()
+                    t.type, t.n = gvm.GVM_TASK_VADD, spec.n
+                    inputs = (a, b)
+                else:
+                    A, B = synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
+                    ins = (pinned(A), pinned(B))
+                    out = torch.full((spec.m, spec.n), float("nan")).pin_memory()
+                    t.type, t.m, t.n, t.k = gvm.GVM_TASK_SGEMM, spec.m, spec.n, spec.k
+                    inputs = (A, B)
+                t.flags = 0
+                t.a, t.b, t.c = ins[0].data_ptr(), ins[1].data_ptr(), out.data_ptr()
+                keep.append((spec, inputs, ins, out))
+            arrays.append(arr)
+            arrivals.append([int(s.arrival_s * 1e9) for s in by_rank[r]])
+        span, lat = mgr.open_loop_run(ranks, arrays, arrivals, max_inflight=max_inflight)
+        assert span >= max(max(a) for a in arrivals) / 1e9
+        assert all(len(l) == per and all(x >= 0 for x in l) for l in lat)
+        assert mgr.stats()["device_status"] == 0
+    for spec, inputs, ins, out in keep:
+        check_result(spec, inputs, out)
+
+
 @pytest.mark.parametrize("slice_mb", [64, 2])
 def test_batch_from_contiguous_host_blocks(gvm, slice_mb):
     # A rank's operands in one pinned block (A then B per task) and its
