@@ -1056,8 +1056,8 @@ def stress_arm(args):
     continuous mode. Vector lengths are clamped to [2^10, 2^24] here: at 128
     ranks a rank's staging slice holds about half a gigabyte, and a 2^28
     vector add stages 3 GiB. First the capacity: every task arrives at once
-    (tasks/s over the whole run). Then the same task list at 0.8 x that
-    capacity (Poisson gaps), with p50/p99/p999 latency. Operands come from one
+    (tasks/s over the whole run). Then the same task list at 0.5, 0.8 and
+    0.95 x that capacity (Poisson gaps), each with p50/p99/p999 latency. Operands come from one
     seeded page-locked buffer per kind (a task reads a prefix of it as a dense
     operand); outputs share a pool of page-locked buffers, one per rank slot
     group (values are not checked here; the mix's parity is covered by the
@@ -1096,11 +1096,20 @@ def stress_arm(args):
 
     span0, _, moved0, _ = run(w0)
     capacity = len(w0.tasks) / span0
-    rate = 0.8 * capacity / R
-    w1 = synth.stress_mix(ranks=R, per_rank=P, rate_per_rank_hz=rate)
-    for t0, t1 in zip(w0.tasks, w1.tasks):
-        t1.n, t1.m, t1.k = t0.n, t0.m, t0.k  # same tasks, paced arrivals
-    span1, lat1, moved1, st1 = run(w1)
+    points = {}
+    for frac in (0.5, 0.8, 0.95):
+        w1 = synth.stress_mix(ranks=R, per_rank=P, rate_per_rank_hz=frac * capacity / R)
+        for t0, t1 in zip(w0.tasks, w1.tasks):
+            t1.n, t1.m, t1.k = t0.n, t0.m, t0.k  # the same tasks, paced arrivals
+        span1, lat1, moved1, st1 = run(w1)
+        points[f"at_{frac}_capacity"] = {
+            "offered_tasks_per_s": frac * capacity, "served_tasks_per_s": len(w1.tasks) / span1,
+            "last_arrival_s": max(t.arrival_s for t in w1.tasks), "span_s": span1,
+            "latency_us": {"p50": 1e6 * percentile(lat1, 50), "p99": 1e6 * percentile(lat1, 99),
+                           "p999": 1e6 * percentile(lat1, 99.9),
+                           "kind": "scheduled arrival -> completion seen by the rank"},
+            "host_link_gbs": moved1 / span1 / 1e9, "staged_peak_bytes": st1["staged_peak"],
+            "device_status": st1["device_status"]}
     return {
         "metric": METRIC + " (stress loop)",
         "value": capacity,
@@ -1113,14 +1122,7 @@ def stress_arm(args):
                    "[2^10, 2^24], 30% square SGEMM side 768 e^(0.7Z) in [64, 4096], cap 120 GiB",
                    "mode": "continuous", "sgemm_path": args.path, "ring_depth": depth},
         "capacity": {"tasks_per_s": capacity, "host_link_gbs": moved0 / span0 / 1e9, "seconds": span0},
-        "at_0.8_capacity": {
-            "offered_tasks_per_s": 0.8 * capacity, "served_tasks_per_s": len(w1.tasks) / span1,
-            "last_arrival_s": max(t.arrival_s for t in w1.tasks), "span_s": span1,
-            "latency_us": {"p50": 1e6 * percentile(lat1, 50), "p99": 1e6 * percentile(lat1, 99),
-                           "p999": 1e6 * percentile(lat1, 99.9),
-                           "kind": "scheduled arrival -> completion seen by the rank"},
-            "host_link_gbs": moved1 / span1 / 1e9, "staged_peak_bytes": st1["staged_peak"],
-            "device_status": st1["device_status"]},
+        **points,
     }
 
 

@@ -8,6 +8,14 @@ runs every rank's task -- input copy, kernel, output copy -- concurrently
 library ``_build/libgvm.so`` (C ABI in ``include/gvm.h``); this module only
 marshals arguments. PyTorch supplies device memory and streams.
 
+Entry points: ``Manager`` (one manager; modes "barrier", "continuous",
+"ps1", "ps2"; ``attach`` gives a ``Rank`` with ``submit_vadd``,
+``submit_vmul``, ``submit_sgemm``, their resident forms, ``sync``, ``poll``;
+``spmd_run``, ``spmd_run_overlapped`` and ``open_loop_run`` drive many ranks
+from native threads), ``IpcRegion`` / ``IpcServer`` / ``IpcClient`` (ranks
+in separate processes through shared memory), and the task kernels alone
+(``vadd_f32``, ``vmul_f32``, ``sgemm_f32``).
+
 There is no fallback: if the library is missing or no GPU is present, the
 calls raise.
 """
