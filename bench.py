@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--impl", choices=["gvm", "reference"], default="gvm")
     p.add_argument("--workload", choices=["sgemm512", "vadd_tiny", "serving", "grouped", "stress"], default="sgemm512")
     p.add_argument("--serving-tasks", type=int, default=0, help="serving workload: total tasks (default 4096)")
-    p.add_argument("--path", choices=["split3", "fma"], default="split3")
+    p.add_argument("--path", choices=["split3", "split3_wide", "fma"], default="split3")
     p.add_argument("--mode", choices=["barrier", "continuous"], default="barrier")
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
@@ -184,7 +184,7 @@ def peaks():
 
 # The sources the scheduler kernels are compiled from (host code does not
 # change their DRAM traffic per tile).
-KERNEL_SOURCES = ("gvm_sched.cu", "gvm_fused.cuh", "gvm_device.cuh", "gvm_internal.h")
+KERNEL_SOURCES = ("gvm_sched.cu", "gvm_fused.cuh", "gvm_wide.cuh", "gvm_device.cuh", "gvm_internal.h")
 
 
 def kernel_source_hash():
@@ -734,7 +734,7 @@ def gpu_arm(args, w, desc, rank, world):
     kmean = statistics.mean(t_kernel)
     if w.tasks[0].kind == synth.TASK_SGEMM:
         flops = sum(s.flops for s in w.tasks)
-        if args.path == "split3":
+        if args.path in ("split3", "split3_wide"):
             peak = pk["bf16_tflops"] / 3.0
             roof = {"bound": "tensor", "unit": "TFLOP/s",
                     "peak_basis": f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"}
@@ -748,7 +748,7 @@ def gpu_arm(args, w, desc, rank, world):
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "unit": "GB/s", "peak_basis": f"HBM copy {pk['hbm_gbs']} GB/s ({pk_kind})"}
         achieved = byts / kmean / 1e9
-    kname = "sched_fused_kernel" if args.path == "split3" else "sched_fma_kernel"
+    kname = {"split3": "sched_fused_kernel", "split3_wide": "sched_wide_kernel"}.get(args.path, "sched_fma_kernel")
     key = f"{kname}/{args.workload}"
     roof.update({"kernel": f"gvm::{kname}", "achieved": achieved, "peak": peak,
                  "frac": achieved / peak, "traffic": ncu_traffic(key), "launch_ms": kmean * 1e3})
@@ -777,7 +777,7 @@ def gpu_arm(args, w, desc, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16x3->f32" if args.path == "split3" else "f32",
+        "dtype": "bf16x3->f32" if args.path != "fma" else "f32",
         "data": "synthetic",
         "config": cfg,
         "gbps": {"hbm_operands": sum(sum(v) for v in sizes.values()) * args.steps * world / total_s / 1e9},
@@ -1036,7 +1036,7 @@ def serving_arm(args):
         "unit": "tasks/s",
         "n_gpus": 1,
         "higher_is_better": True,
-        "dtype": "bf16x3->f32" if args.path == "split3" else "f32",
+        "dtype": "bf16x3->f32" if args.path != "fma" else "f32",
         "data": "synthetic",
         "config": {"workload": f"serving mix: 16 ranks, {total} tasks, Poisson 20 us mean gap per rank, "
                    "50/50 vector add n~2^(16+8u) / square SGEMM {256,512,1024,2048}, cap 32 GiB",
@@ -1116,7 +1116,7 @@ def stress_arm(args):
         "unit": "tasks/s",
         "n_gpus": 1,
         "higher_is_better": True,
-        "dtype": "bf16x3->f32" if args.path == "split3" else "f32",
+        "dtype": "bf16x3->f32" if args.path != "fma" else "f32",
         "data": "synthetic",
         "config": {"workload": f"stress mix: {R} ranks x {P} tasks, 70% vector add n = 2^20 e^(1.5Z) in "
                    "[2^10, 2^24], 30% square SGEMM side 768 e^(0.7Z) in [64, 4096], cap 120 GiB",
@@ -1498,7 +1498,7 @@ def grouped_arm(args):
         errs.append(float(oracle.rel_fro_err(C[rows], oracle.sgemm64(A[rows], B))))
     mgr.shutdown()
     pk, pk_kind = peaks()
-    if args.path == "split3":
+    if args.path != "fma":
         peak = pk["bf16_tflops"] / 3.0
         basis = f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"
         bound = "tensor"
@@ -1516,14 +1516,16 @@ def grouped_arm(args):
         "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True,
-        "dtype": "bf16x3->f32" if args.path == "split3" else "f32",
+        "dtype": "bf16x3->f32" if args.path != "fma" else "f32",
         "data": "synthetic",
         "config": {"workload": f"grouped SGEMM: {R} ranks x {P} tasks, M, N, K each from {{128..2048}} step 64, "
                                "standard-normal operands drawn on the device, resident",
                    "sgemm_path": args.path, "mode": "barrier", "tflop_per_step": flops / 1e12},
         "roofline": {"bound": bound, "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                     "peak_basis": basis, "kernel": "gvm::sched_fused_kernel" if args.path == "split3"
-                     else "gvm::sched_fma_kernel", "launch_ms": kmean * 1e3},
+                     "peak_basis": basis,
+                     "kernel": "gvm::" + {"split3": "sched_fused_kernel",
+                                          "split3_wide": "sched_wide_kernel"}.get(args.path, "sched_fma_kernel"),
+                     "launch_ms": kmean * 1e3},
         "sched_timeline_last_launch": {
             "cta_ms": {"acquire": ph[0] / 1e6, "stage_wait": ph[2] / 1e6, "gemm": ph[3] / 1e6,
                        "mma_wait": ph[4] / 1e6, "epilogue": ph[8] / 1e6},

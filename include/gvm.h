@@ -78,6 +78,9 @@ extern "C" {
 #define GVM_SGEMM_SPLIT3_PAIR 3 /* gvm_sgemm_f32 only: split during staging on CTA pairs
                               (two-SM tcgen05 MMAs, 256 x 256 tiles); the same products
                               in the same order, bit-identical to GVM_SGEMM_SPLIT3 */
+#define GVM_SGEMM_SPLIT3_WIDE 4 /* split during staging on 256 x 256 tiles of one CTA (the
+                              two 128-row halves share each B stage; one accumulator);
+                              bit-identical to GVM_SGEMM_SPLIT3. Also a manager path */
 
 /* ---- manager modes ------------------------------------------------------ */
 #define GVM_MODE_BARRIER 0    /* Section 5 request barrier: gvm_flush runs the scheduler
@@ -106,7 +109,7 @@ typedef struct gvm_config {
   int32_t ring_depth;     /* task descriptors per rank; power of two, 2 .. 4096 */
   int32_t mode;           /* GVM_MODE_BARRIER, GVM_MODE_CONTINUOUS, GVM_MODE_PS1 or
                              GVM_MODE_PS2 */
-  int32_t sgemm_path;     /* GVM_SGEMM_FMA or GVM_SGEMM_SPLIT3 */
+  int32_t sgemm_path;     /* GVM_SGEMM_FMA, GVM_SGEMM_SPLIT3 or GVM_SGEMM_SPLIT3_WIDE */
   void* arena;            /* caller-owned device memory, 256-byte aligned. Split into
                              max_ranks equal slices (Section 5: one memory object per
                              process, so data of different processes coexist safely) */

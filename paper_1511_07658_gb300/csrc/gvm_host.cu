@@ -142,7 +142,8 @@ bool cfg_valid(const gvm_config* c) {
   if (c->mode != GVM_MODE_BARRIER && c->mode != GVM_MODE_CONTINUOUS && c->mode != GVM_MODE_PS1 &&
       c->mode != GVM_MODE_PS2)
     return false;
-  if (c->sgemm_path != GVM_SGEMM_FMA && c->sgemm_path != GVM_SGEMM_SPLIT3) return false;
+  if (c->sgemm_path != GVM_SGEMM_FMA && c->sgemm_path != GVM_SGEMM_SPLIT3 && c->sgemm_path != GVM_SGEMM_SPLIT3_WIDE)
+    return false;
   return true;
 }
 
@@ -376,7 +377,9 @@ int ps_issue_comp(gvm_rank* r, uint64_t s) {
   } else {
     // The fused split3 form needs no scratch and computes the same tiles as
     // the scheduler's split3 path.
-    const int path = ctx->path == kPathSplit3 ? GVM_SGEMM_SPLIT3_FUSED : GVM_SGEMM_FMA;
+    const int path = ctx->path == kPathSplit3       ? GVM_SGEMM_SPLIT3_FUSED
+                     : ctx->path == kPathSplit3Wide ? GVM_SGEMM_SPLIT3_WIDE
+                                                    : GVM_SGEMM_FMA;
     rc = gvm_sgemm_f32(A, B, C, b.m, (int32_t)b.n, b.k, path, nullptr, 0, r->in_stream);
   }
   if (rc == GVM_OK) ctx->launches.fetch_add(1);
@@ -508,7 +511,9 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   auto ctx = std::make_unique<gvm_ctx>();
   ctx->cfg = cfg;
   ctx->L = L;
-  ctx->path = cfg.sgemm_path == GVM_SGEMM_SPLIT3 ? kPathSplit3 : kPathFma;
+  ctx->path = cfg.sgemm_path == GVM_SGEMM_SPLIT3        ? kPathSplit3
+              : cfg.sgemm_path == GVM_SGEMM_SPLIT3_WIDE ? kPathSplit3Wide
+                                                        : kPathFma;
   ctx->slice_bytes = slice;
   ctx->device = dev;
   if (cfg.sched_stream) {
@@ -741,10 +746,11 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
     body->m = t->m;
     body->k = t->k;
     body->n = t->n;
-    // Split3: fused tiles (the bf16 split happens in the tile itself).
-    const int tm = ctx->path == kPathSplit3 ? kTcM : kFmaTile;
-    const int tn = ctx->path == kPathSplit3 ? kTcN : kFmaTile;
-    if (ctx->path == kPathSplit3) body->flags |= kFlagSplit3;
+    // Split3: fused tiles (the bf16 split happens in the tile itself),
+    // 128 x 256 or, in the wide form, 256 x 256.
+    const int tm = ctx->path == kPathSplit3 ? kTcM : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
+    const int tn = ctx->path == kPathSplit3 ? kTcN : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
+    if (ctx->path != kPathFma) body->flags |= kFlagSplit3;
     body->tiles_m = (uint32_t)((t->m + tm - 1) / tm);
     body->tiles_n = (uint32_t)((t->n + tn - 1) / tn);
     body->ntiles = body->tiles_m * body->tiles_n;

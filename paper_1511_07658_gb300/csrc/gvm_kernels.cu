@@ -11,6 +11,7 @@
 #include "gvm_device.cuh"
 #include "gvm_fused.cuh"
 #include "gvm_pair.cuh"
+#include "gvm_wide.cuh"
 #include "gvm_runtime.h"
 
 namespace gvm {
@@ -117,6 +118,58 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     __syncwarp();
   }
   fz_teardown(&fs);
+  if (threadIdx.x == 0 && abort_flag) atomicExch(&g_kernel_status, kStatusTimeout | (fail_where << 8));
+}
+
+// Wide form: 256 x 256 tiles, the same static tile order; a tile's
+// accumulator is drained by the converters right after their first k-step of
+// the next tile (one accumulator fills TMEM).
+__global__ void __launch_bounds__(kFzThreads, 1)
+    wd_sgemm_kernel(const float* A, const float* B, float* C, int m, int n, int k, uint64_t timeout_ns) {
+  __shared__ WdShared ws;
+  __shared__ uint32_t abort_flag, fail_where;
+  extern __shared__ uint8_t dyn_smem[];
+  uint8_t* big = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    fail_where = 0;
+  }
+  wd_init(&ws);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_n = (n + kWdN - 1) / kWdN;
+  const int ntiles = ((m + kWdM - 1) / kWdM) * tiles_n;
+  const uint32_t nkb = (uint32_t)((k + kTcBK - 1) / kTcBK);
+  uint32_t it = 0, tile_no = 0;
+  if (warp < kFzConvWarps) {
+    FzTile prev{};
+    bool pending = false, ok = true;
+    auto drain = [&]() -> bool {
+      if (!pending) return true;
+      pending = false;
+      return wd_epilogue(prev, &ws, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
+    };
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
+      ok = wd_convert(t, big, &ws, it, timeout_ns, &abort_flag, &fail_where, nullptr, drain);
+      if (ok) ok = drain();  // this group had no k-step of the tile
+      prev = t;
+      pending = true;
+      it += nkb;
+      ++tile_no;
+    }
+    if (ok) drain();
+  } else if (warp == kFzMmaWarp) {
+    if (lane == 0) {
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
+        if (!wd_mma(t, big, &ws, it, tile_no, timeout_ns, &abort_flag, &fail_where, nullptr)) break;
+        it += nkb;
+        ++tile_no;
+      }
+    }
+    __syncwarp();
+  }
+  wd_teardown(&ws);
   if (threadIdx.x == 0 && abort_flag) atomicExch(&g_kernel_status, kStatusTimeout | (fail_where << 8));
 }
 
@@ -290,6 +343,7 @@ extern "C" uint64_t gvm_sgemm_scratch_bytes(int32_t m, int32_t n, int32_t k, int
 static std::atomic<bool> fma_attr_set{false};
 static std::atomic<bool> tc_attr_set{false};
 static std::atomic<bool> fz_attr_set{false};
+static std::atomic<bool> wd_attr_set{false};
 
 extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m, int32_t n, int32_t k,
                              int32_t path, void* scratch, uint64_t scratch_bytes, void* stream) {
@@ -321,6 +375,21 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
     const int64_t ntiles = (int64_t)((m + kTcM - 1) / kTcM) * ((n + kTcN - 1) / kTcN);
     const int grid = (int)(ntiles < sms ? ntiles : sms);
     fz_sgemm_kernel<<<grid, kFzThreads, smem, s>>>(A, B, C, m, n, k, kStandaloneTimeoutNs);
+    return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
+  }
+  if (path == GVM_SGEMM_SPLIT3_WIDE) {
+    const size_t smem = (size_t)kWdStages * kWdStageBytes + 1024;
+    if (!wd_attr_set) {
+      if (cudaFuncSetAttribute(wd_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+        return GVM_EDEVICE;
+      wd_attr_set = true;
+    }
+    const int sms = sm_count();
+    if (sms <= 0) return GVM_ENODEV;
+    const int64_t ntiles = (int64_t)((m + kWdM - 1) / kWdM) * ((n + kWdN - 1) / kWdN);
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    wd_sgemm_kernel<<<grid, kFzThreads, smem, s>>>(A, B, C, m, n, k, kStandaloneTimeoutNs);
     return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
   }
   if (path == GVM_SGEMM_SPLIT3_PAIR) {

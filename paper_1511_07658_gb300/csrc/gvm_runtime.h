@@ -10,7 +10,7 @@
 
 namespace gvm {
 
-enum : int { kPathFma = 0, kPathSplit3 = 1 };
+enum : int { kPathFma = 0, kPathSplit3 = 1, kPathSplit3Wide = 2 };
 
 // Driver entry points, resolved once through the runtime (no link-time libcuda).
 struct DriverApi {

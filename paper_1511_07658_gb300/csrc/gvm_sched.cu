@@ -31,8 +31,11 @@
 // idle_poll_ns between polls); in barrier (drain) mode it exits once every
 // descriptor published before its launch has been taken.
 #include "gvm_device.cuh"
+#include <type_traits>
+
 #include "gvm_fused.cuh"
 #include "gvm_runtime.h"
+#include "gvm_wide.cuh"
 
 namespace gvm {
 
@@ -642,8 +645,11 @@ struct FzItem {
   uint64_t a, b, c;
 };
 
-struct alignas(128) FusedShared {
-  FzShared fz;
+// Shared state of a tensor-core scheduler CTA; Pipe is the tile form's
+// pipeline (FzShared: 128 x 256 tiles, WdShared: 256 x 256 tiles).
+template <class Pipe>
+struct alignas(128) TensorSchedShared {
+  Pipe fz;
   uint64_t item_full[kFzItems];   // control -> consumers (1 arrival)
   uint64_t item_empty[kFzItems];  // consumers -> control (converter warps + MMA warp)
   FzItem items[kFzItems];
@@ -657,7 +663,8 @@ struct alignas(128) FusedShared {
 
 // Records a failure seen by this CTA: the CTA flag stops its other warps'
 // waits, report_error stops the other CTAs and tells the host.
-__device__ void cta_fail(const SchedParams& p, FusedShared& sh, uint32_t where, uint32_t info) {
+template <class Sh>
+__device__ void cta_fail(const SchedParams& p, Sh& sh, uint32_t where, uint32_t info) {
   sh.fail_where = where;
   sh.abort = 1;
   report_error(p, kStatusTimeout, where, info);
@@ -666,8 +673,9 @@ __device__ void cta_fail(const SchedParams& p, FusedShared& sh, uint32_t where, 
 // A converter warp has written its share of item `seq` (a vector-add range or
 // a drained accumulator). The last of the kFzConvWarps warps completes the
 // tile. Lanes fence their own stores before lane 0 counts the warp.
-__device__ void conv_item_done(const SchedParams& p, FusedShared& sh, uint32_t seq, uint32_t task,
-                               uint32_t ntiles, uint32_t tag, uint32_t flags) {
+template <class Sh>
+__device__ void conv_item_done(const SchedParams& p, Sh& sh, uint32_t seq, uint32_t task, uint32_t ntiles,
+                               uint32_t tag, uint32_t flags) {
   // Results written into host memory must be visible to the host before the
   // task's completion word is.
   if (flags & kFlagDirectOut)
@@ -686,8 +694,11 @@ __device__ void conv_item_done(const SchedParams& p, FusedShared& sh, uint32_t s
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedParams p) {
-  __shared__ FusedShared sh;
+// The split3 scheduler CTA for either tile form (kWide: 256 x 256 tiles).
+template <bool kWide>
+__device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
+  using Pipe = typename std::conditional<kWide, WdShared, FzShared>::type;
+  __shared__ TensorSchedShared<Pipe> sh;
   extern __shared__ uint8_t dyn_smem[];
   uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -706,7 +717,11 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
     cl->hint = ld_relaxed_gpu64(&p.ctrl->first_entry);
     sched_enter(p);
   }
-  fz_init(&sh.fz);  // initialises the pipeline barriers, fences all inits, allocates TMEM
+  // initialises the pipeline barriers, fences all inits, allocates TMEM
+  if constexpr (kWide)
+    wd_init(&sh.fz);
+  else
+    fz_init(&sh.fz);
 
   if (warp == kFzCtlWarp) {
     // ---- control: claim tiles into the item ring.
@@ -767,11 +782,18 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
       if (kind == kItemExit) break;
       if (kind != kTaskSgemm) continue;
       uint32_t ok = 1;
-      if (lane == 0)
-        ok = fz_mma(t, stages, &sh.fz, it_k, tile_no, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
-                    &sh.prof[kProfMmaWait])
-                 ? 1u
-                 : 0u;
+      if (lane == 0) {
+        if constexpr (kWide)
+          ok = wd_mma(t, stages, &sh.fz, it_k, tile_no, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+                      &sh.prof[kProfMmaWait])
+                   ? 1u
+                   : 0u;
+        else
+          ok = fz_mma(t, stages, &sh.fz, it_k, tile_no, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+                      &sh.prof[kProfMmaWait])
+                   ? 1u
+                   : 0u;
+      }
       if (!__shfl_sync(0xffffffffu, ok, 0)) {
         if (lane == 0) report_error(p, kStatusTimeout, sh.fail_where, seq);
         break;
@@ -779,7 +801,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
       it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
       ++tile_no;
     }
-  } else {
+  } else if (warp < kFzConvWarps) {
     // ---- converters: stage GEMM tiles; after staging tile T, count tile
     // T-2 as finished (its stores were issued a tile ago, so the fence that
     // orders them before the count hardly waits) and drain tile T-1's
@@ -809,7 +831,12 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
       const FzPend& d = sh.pend[warp][no % 3u];
       const FzTile pt{nullptr, nullptr, reinterpret_cast<float*>(d.c), d.n, d.m, 0, (int)(d.tile / d.tiles_n),
                       (int)(d.tile % d.tiles_n)};
-      if (!fz_epilogue(pt, &sh.fz, no, p.wait_timeout_ns, &sh.abort, &sh.fail_where)) return false;
+      bool drained;
+      if constexpr (kWide)
+        drained = wd_epilogue(pt, &sh.fz, no, p.wait_timeout_ns, &sh.abort, &sh.fail_where);
+      else
+        drained = fz_epilogue(pt, &sh.fz, no, p.wait_timeout_ns, &sh.abort, &sh.fail_where);
+      if (!drained) return false;
       has_drain = false;
       has_done = true;
       done_no = no;
@@ -855,13 +882,22 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
           mbar_arrive(&sh.item_empty[slot]);
         }
         __syncwarp();
-        ok = fz_convert<true>(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
-                        tid == 0 ? &sh.prof[kProfStageWait] : nullptr);
-        it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
-        if (ok) {
-          count_done();
-          ok = drain();
+        if constexpr (kWide) {
+          // One accumulator: drain tile T-1 right after this group's first
+          // k-step of T (T's MMAs wait for it), then count T-1.
+          ok = wd_convert(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+                          tid == 0 ? &sh.prof[kProfStageWait] : nullptr, [&]() -> bool { return drain(); });
+          if (ok) ok = drain();  // the group had no k-step of T
+          if (ok) count_done();
+        } else {
+          ok = fz_convert<true>(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+                                tid == 0 ? &sh.prof[kProfStageWait] : nullptr);
+          if (ok) {
+            count_done();
+            ok = drain();
+          }
         }
+        it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
         has_drain = true;
         ++tile_no;
         if (tid == 0) sh.prof[kProfGemm] += globaltimer() - t0;
@@ -889,19 +925,34 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedP
     if (ok && !sh.abort) ok = flush();
     if (!ok && lane == 0) report_error(p, kStatusTimeout, sh.fail_where, 0);
   }
-  fz_teardown(&sh.fz);
+  if constexpr (kWide)
+    wd_teardown(&sh.fz);
+  else
+    fz_teardown(&sh.fz);
   if (tid == 0) sched_exit(p, sh.prof);
 }
 
+__global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedParams p) {
+  sched_tc_body<false>(p);
+}
+
+__global__ void __launch_bounds__(kFzThreads, 1) sched_wide_kernel(const SchedParams p) {
+  sched_tc_body<true>(p);
+}
+
 static size_t dyn_smem_bytes(int path) {
-  return (path == kPathSplit3 ? (size_t)kTcStages * kTcStageBytes : sizeof(FmaSmem)) + 1024;
+  if (path == kPathSplit3) return (size_t)kTcStages * kTcStageBytes + 1024;
+  if (path == kPathSplit3Wide) return (size_t)kWdStages * kWdStageBytes + 1024;
+  return sizeof(FmaSmem) + 1024;
 }
 
 static const void* sched_fn(int path) {
-  return path == kPathSplit3 ? (const void*)sched_fused_kernel : (const void*)sched_fma_kernel;
+  if (path == kPathSplit3) return (const void*)sched_fused_kernel;
+  if (path == kPathSplit3Wide) return (const void*)sched_wide_kernel;
+  return (const void*)sched_fma_kernel;
 }
 
-static int sched_threads(int path) { return path == kPathSplit3 ? kFzThreads : kThreads; }
+static int sched_threads(int path) { return path == kPathFma ? kThreads : kFzThreads; }
 
 cudaError_t scheduler_setup(int path, int* blocks_per_sm, size_t* smem_bytes) {
   const size_t smem = dyn_smem_bytes(path);
@@ -919,6 +970,8 @@ cudaError_t scheduler_setup(int path, int* blocks_per_sm, size_t* smem_bytes) {
 cudaError_t launch_scheduler(int path, const SchedParams& p, int grid, size_t smem, cudaStream_t stream) {
   if (path == kPathSplit3) {
     sched_fused_kernel<<<grid, kFzThreads, smem, stream>>>(p);
+  } else if (path == kPathSplit3Wide) {
+    sched_wide_kernel<<<grid, kFzThreads, smem, stream>>>(p);
   } else {
     sched_fma_kernel<<<grid, kThreads, smem, stream>>>(p);
   }

@@ -1,0 +1,318 @@
+// Split3 SGEMM with the split fused into operand staging, on 256 x 256 tiles
+// of one CTA ("wide" tiles).
+//
+// The arithmetic is the fused form's (gvm_fused.cuh): per 16-wide k slice
+// AlBh, AhBl, AhBh into one fp32 TMEM accumulator, k in order, so every
+// element of C is bitwise the same as with 128 x 256 tiles. What changes is
+// the work per staged byte: a k-step stages A (256 x 32) and B (32 x 256)
+// and feeds 2 x 3 MMAs of 128 x 256 x 16 per k slice (the two 128-row halves
+// of A share the B stage), twice the MMA work of a 128 x 256 tile for 4/3 of
+// its operand bytes. The staging warps are bound by load latency (one k-step
+// of loads per thread in flight), so more work per k-step is more work per
+// latency.
+//
+// The accumulator of a 256 x 256 tile is all of TMEM (512 columns: rows
+// 0..127 in columns 0..255, rows 128..255 in 256..511), so there is one
+// accumulator: the converters drain tile T-1 right after staging their first
+// k-step of tile T, and the MMAs of tile T start once it is drained.
+//
+// CTA roles as in the fused form (10 warps: 8 converters in two groups, MMA,
+// control). A converter keeps 128 floats of loads in flight (8 items of A, 8
+// of B). With 10 warps two SM sub-partitions hold three warps each, which
+// caps a thread at 168 registers, so the compiler keeps part of that in
+// local memory.
+//
+// Stage layout (64 KB, three stages): A hi, A lo [256 rows][32 k] K-major with
+// the 64-byte swizzle on 8-row atoms (rows 128..255 start 8 KB in, where the
+// second MMA half's descriptor points); B hi, B lo [32 k][256 n] MN-major, as
+// in the fused form.
+#pragma once
+
+#include "gvm_fused.cuh"
+
+namespace gvm {
+
+constexpr int kWdM = 256;
+constexpr int kWdN = 256;
+constexpr int kWdStages = 3;
+constexpr uint32_t kWdAOff = 0;                       // A hi [256][32] bf16
+constexpr uint32_t kWdAlOff = kWdM * kTcBK * 2;       // A lo
+constexpr uint32_t kWdBOff = 2 * kWdM * kTcBK * 2;    // B hi [32][256] bf16, MN-major
+constexpr uint32_t kWdBlOff = kWdBOff + kWdN * kTcBK * 2;  // B lo
+constexpr uint32_t kWdStageBytes = kWdBlOff + kWdN * kTcBK * 2;
+static_assert(kWdStageBytes == 65536, "wide stage layout");
+constexpr uint32_t kWdHalfA = 128 * kTcBK * 2;  // bytes of 128 rows of an A plane
+constexpr uint32_t kWdTmemCols = 512;
+struct WdShared {
+  uint64_t full[kWdStages];   // converters -> MMA: one arrival per warp of a group
+  uint64_t empty[kWdStages];  // MMA -> converters: tcgen05.commit
+  uint64_t acc_full;          // MMA -> epilogue: the accumulator holds a finished tile
+  uint64_t acc_empty;         // epilogue -> MMA: one arrival per converter warp
+  uint32_t tmem_base;
+  uint32_t pad;
+};
+
+__device__ __forceinline__ void wd_init(WdShared* ws) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWdStages; ++s) {
+      mbar_init(&ws->full[s], kFzGroupWarps);
+      mbar_init(&ws->empty[s], 1);
+    }
+    mbar_init(&ws->acc_full, 1);
+    mbar_init(&ws->acc_empty, kFzConvWarps);
+    mbar_fence_init();
+  }
+  if ((threadIdx.x >> 5) == kFzMmaWarp) tmem_alloc(&ws->tmem_base, kWdTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ __forceinline__ void wd_teardown(WdShared* ws) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == kFzMmaWarp) tmem_dealloc(ws->tmem_base, kWdTmemCols);
+}
+
+// Thread (w, lane) of a group stages k-step kb of a wide tile:
+//   A item j (j = 0..7): row 8 w + (lane >> 2) + 32 j, 8 values from k = 32 kb + 8 (lane & 3);
+//   B item j (j = 0..7): as in the fused form (k = 32 kb + 8 (j >> 1) + (lane >> 2),
+//                        columns 32 (2 w + (j & 1)) + 8 (lane & 3)).
+// Out-of-range elements are 0 (ragged m, n, k).
+__device__ __forceinline__ void wd_load_a(const FzTile& t, int kb, int w, int lane, int j, int avec,
+                                          float (&v)[8]) {
+  const int r = t.tm * kWdM + 8 * w + (lane >> 2) + 32 * j;
+  const int kk = kb * kTcBK + 8 * (lane & 3);
+  const float* src = t.A + (int64_t)r * t.k + kk;
+  if (r < t.m && avec == 2 && kk + 8 <= t.k) {
+    ld_cg_v8(src, v);
+  } else if (r < t.m && avec && kk + 8 <= t.k) {
+    const float4 x0 = __ldcg(reinterpret_cast<const float4*>(src));
+    const float4 x1 = __ldcg(reinterpret_cast<const float4*>(src + 4));
+    v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+    v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = (r < t.m && kk + e < t.k) ? __ldcg(src + e) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void wd_load_b(const FzTile& t, int kb, int w, int lane, int j, int bvec,
+                                          float (&v)[8]) {
+  const int kk = kb * kTcBK + 8 * (j >> 1) + (lane >> 2);
+  const int64_t c = (int64_t)t.tn * kWdN + 32 * (2 * w + (j & 1)) + 8 * (lane & 3);
+  const float* src = t.B + (int64_t)kk * t.n + c;
+  if (kk < t.k && bvec == 2 && c + 8 <= t.n) {
+    ld_cg_v8(src, v);
+  } else if (kk < t.k && bvec && c + 8 <= t.n) {
+    const float4 x0 = __ldcg(reinterpret_cast<const float4*>(src));
+    const float4 x1 = __ldcg(reinterpret_cast<const float4*>(src + 4));
+    v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+    v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = (kk < t.k && c + e < t.n) ? __ldcg(src + e) : 0.f;
+  }
+}
+
+// Converter warps: stage the k-steps of wide tile t that belong to this
+// warp's group, loads one group k-step ahead and issued after each stage's
+// proxy fence (as the scheduler's fused form). after_first() runs once,
+// after the group's first k-step of the tile (the previous tile's drain).
+// Returns false when a wait ran out (*cta_abort set).
+template <bool kFast, class AfterFirst>
+__device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, WdShared* ws, uint32_t it,
+                                                int avec, int bvec, uint64_t timeout_ns,
+                                                volatile uint32_t* cta_abort, uint32_t* fail_where,
+                                                uint64_t* wait_acc, AfterFirst& after_first) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int par = warp / kFzGroupWarps, w = warp % kFzGroupWarps;
+  const int nkb = (t.k + kTcBK - 1) / kTcBK;
+  const int kb0 = (int)((it + (uint32_t)par) & 1u);
+  if (kb0 >= nkb) return true;
+  const float* pa = t.A + (int64_t)(t.tm * kWdM + 8 * w + (lane >> 2)) * t.k + 8 * (lane & 3);
+  const float* pb = t.B + (int64_t)(lane >> 2) * t.n + (int64_t)t.tn * kWdN + 64 * w + 8 * (lane & 3);
+  const int64_t a_row32 = 32 * (int64_t)t.k, b_row8 = 8 * t.n, b_step = (int64_t)kTcBK * t.n;
+  auto load_a = [&](int kb, int j, float (&v)[8]) {
+    if (kFast) ld_cg_v8(pa + kb * kTcBK + j * a_row32, v);
+    else wd_load_a(t, kb, w, lane, j, avec, v);
+  };
+  auto load_b = [&](int kb, int j, float (&v)[8]) {
+    if (kFast) ld_cg_v8(pb + kb * b_step + (j >> 1) * b_row8 + 32 * (j & 1), v);
+    else wd_load_b(t, kb, w, lane, j, bvec, v);
+  };
+  float va[8][8], vb[8][8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) load_a(kb0, j, va[j]);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) load_b(kb0, j, vb[j]);
+  const uint32_t a_off = (uint32_t)(8 * w) * 64u + swz64((uint32_t)(lane >> 2), (uint32_t)(lane & 3));
+  const uint32_t b_off = swz64((uint32_t)(lane >> 2), (uint32_t)(lane & 3));
+  bool first = true;
+  for (int kb = kb0; kb < nkb; kb += 2) {
+    const uint32_t q = it + (uint32_t)kb, s = q % kWdStages, ph = (q / kWdStages) & 1u;
+    uint64_t t0 = 0;
+    if (wait_acc != nullptr && warp == 0 && lane == 0) t0 = globaltimer();
+    if (!mbar_wait(&ws->empty[s], ph ^ 1u, timeout_ns, cta_abort)) {
+      if (lane == 0) {
+        *fail_where = kWhereEmptyBarrier;
+        *cta_abort = 1;
+      }
+      return false;
+    }
+    if (t0) *wait_acc += globaltimer() - t0;
+    const uint32_t st = base + s * kWdStageBytes;
+    const bool more = kb + 2 < nkb;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      // Row 8 w + (lane >> 2) + 32 j: its swizzle phase depends on the row
+      // within its 8-row atom only, so every j shares a_off.
+      const uint32_t off = a_off + (uint32_t)(32 * j) * 64u;
+      uint4 hi, lo;
+      split8_x2(va[j], hi, lo);
+      st_shared_v4(st + kWdAOff + off, hi);
+      st_shared_v4(st + kWdAlOff + off, lo);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t off = (uint32_t)(j >> 1) * kFzBAtomK + (uint32_t)(2 * w + (j & 1)) * kFzBAtomN + b_off;
+      uint4 hi, lo;
+      split8_x2(vb[j], hi, lo);
+      st_shared_v4(st + kWdBOff + off, hi);
+      st_shared_v4(st + kWdBlOff + off, lo);
+    }
+    fence_proxy_async_shared();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ws->full[s]);
+    if (more) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) load_a(kb + 2, j, va[j]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) load_b(kb + 2, j, vb[j]);
+    }
+    if (first) {
+      first = false;
+      if (!after_first()) return false;
+    }
+  }
+  return true;
+}
+
+template <class AfterFirst>
+__device__ __forceinline__ bool wd_convert(const FzTile& t, uint8_t* stages, WdShared* ws, uint32_t it,
+                                           uint64_t timeout_ns, volatile uint32_t* cta_abort,
+                                           uint32_t* fail_where, uint64_t* wait_acc, AfterFirst after_first) {
+  const int avec = ((t.k & 7) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 31) == 0)   ? 2
+                   : ((t.k & 3) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 15) == 0) ? 1
+                                                                                      : 0;
+  const int bvec = ((t.n & 7) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 31) == 0)   ? 2
+                   : ((t.n & 3) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 15) == 0) ? 1
+                                                                                      : 0;
+  const bool fast = avec == 2 && bvec == 2 && (t.k % kTcBK) == 0 && (t.tm + 1) * kWdM <= t.m &&
+                    (int64_t)(t.tn + 1) * kWdN <= t.n;
+  const uint32_t base = smem_u32(stages);
+  return fast ? wd_convert_loop<true>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
+                                      after_first)
+              : wd_convert_loop<false>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
+                                       after_first);
+}
+
+// Converter warps: drain the accumulator of wide tile t (the tile_no-th of
+// this CTA) into C. Warp w reads TMEM lanes 32 (w & 3) .. +31 of both halves
+// (rows 32 (w & 3) + lane and 128 + 32 (w & 3) + lane of the tile), columns
+// 128 (w >> 2) .. +127 of each half, 32 at a time, and stores whole 32-byte
+// sectors (16-byte or single stores when n does not allow). Then frees the
+// accumulator.
+__device__ __forceinline__ bool wd_epilogue(const FzTile& t, WdShared* ws, uint32_t tile_no, uint64_t timeout_ns,
+                                            volatile uint32_t* cta_abort, uint32_t* fail_where) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!mbar_wait(&ws->acc_full, tile_no & 1u, timeout_ns, cta_abort)) {
+    if (lane == 0) {
+      *fail_where = kWhereAccumBarrier;
+      *cta_abort = 1;
+    }
+    return false;
+  }
+  tc_fence_after();
+  const int q = warp & 3, cq = warp >> 2;
+  const uintptr_t ca = reinterpret_cast<uintptr_t>(t.C);
+  const int vec = ((t.n & 7) == 0 && (ca & 31) == 0) ? 2 : ((t.n & 3) == 0 && (ca & 15) == 0) ? 1 : 0;
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int row = t.tm * kWdM + h * 128 + q * 32 + lane;
+#pragma unroll 1
+    for (int ch = 0; ch < 4; ++ch) {
+      const int chunk = cq * 4 + ch;
+      uint32_t r[32];
+      tmem_ld_32x32b_x32(ws->tmem_base + (uint32_t)(h * kWdN) + ((uint32_t)(q * 32) << 16) + (uint32_t)(chunk * 32),
+                         r);
+      tmem_ld_wait();
+      const int64_t c0 = (int64_t)t.tn * kWdN + chunk * 32;
+      if (row < t.m && c0 < t.n) {
+        float* dst = t.C + (int64_t)row * t.n + c0;
+        if (vec == 2 && c0 + 32 <= t.n) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) st_v8(dst + 8 * j, r + 8 * j);
+        } else if (vec == 1 && c0 + 32 <= t.n) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            reinterpret_cast<uint4*>(dst)[j] = make_uint4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < t.n) dst[j] = __uint_as_float(r[j]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&ws->acc_empty);
+  return true;
+}
+
+// One elected lane of the MMA warp: accumulate wide tile t (the tile_no-th
+// of this CTA) once the previous tile's accumulator has been drained.
+__device__ __forceinline__ bool wd_mma(const FzTile& t, uint8_t* stages, WdShared* ws, uint32_t it,
+                                       uint32_t tile_no, uint64_t timeout_ns, volatile uint32_t* cta_abort,
+                                       uint32_t* fail_where, uint64_t* wait_acc) {
+  if (!mbar_wait(&ws->acc_empty, (tile_no & 1u) ^ 1u, timeout_ns, cta_abort)) {
+    *fail_where = kWhereAccumBarrier;
+    *cta_abort = 1;
+    return false;
+  }
+  tc_fence_after();
+  const int nkb = (t.k + kTcBK - 1) / kTcBK;
+  for (int kb = 0; kb < nkb; ++kb) {
+    const uint32_t q = it + (uint32_t)kb, s = q % kWdStages, ph = (q / kWdStages) & 1u;
+    const uint64_t t0 = wait_acc ? globaltimer() : 0;
+    if (!mbar_wait(&ws->full[s], ph, timeout_ns, cta_abort)) {
+      *fail_where = kWhereFullBarrier;
+      *cta_abort = 1;
+      return false;
+    }
+    if (wait_acc) *wait_acc += globaltimer() - t0;
+    tc_fence_after();
+    const uint32_t sb = smem_u32(stages + s * kWdStageBytes);
+    const uint64_t dBh = sdesc_mn64b(sb + kWdBOff), dBl = sdesc_mn64b(sb + kWdBlOff);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t tmem = ws->tmem_base + (uint32_t)(h * kWdN);
+      const uint64_t dAh = sdesc_k64b(sb + kWdAOff + h * kWdHalfA), dAl = sdesc_k64b(sb + kWdAlOff + h * kWdHalfA);
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 16; ++kk) {
+        const uint64_t adv_a = (uint64_t)(kk * 32) >> 4;             // 16 bf16 = 32 bytes along a K-major row
+        const uint64_t adv_b = (uint64_t)(kk * 2 * kFzBAtomK) >> 4;  // two 8-row k groups of B
+        umma_bf16(tmem, dAl + adv_a, dBh + adv_b, kFzIdesc, (kb | kk) ? 1u : 0u);
+        umma_bf16(tmem, dAh + adv_a, dBl + adv_b, kFzIdesc, 1u);
+        umma_bf16(tmem, dAh + adv_a, dBh + adv_b, kFzIdesc, 1u);
+      }
+    }
+    umma_commit(&ws->empty[s]);
+  }
+  umma_commit(&ws->acc_full);
+  return true;
+}
+
+}  // namespace gvm

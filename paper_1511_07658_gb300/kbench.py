@@ -117,7 +117,7 @@ def main(argv) -> None:
     elif what == "link":
         link()
     elif what.isdigit():
-        sgemm(int(what), paths=("split3", "split3_fused", "split3_pair"))
+        sgemm(int(what), paths=("split3", "split3_fused", "split3_pair", "split3_wide"))
     else:
         for side in (512, 2048, 4096):
             sgemm(side)

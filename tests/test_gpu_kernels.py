@@ -120,7 +120,7 @@ def run_sgemm(gvm, A, B, path):
     return tC.cpu().numpy()
 
 
-@pytest.mark.parametrize("path", ["fma", "split3", "split3_fused", "split3_pair"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_fused", "split3_pair", "split3_wide"])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_sgemm_normal_inputs(gvm, path, shape):
     m, n, k = shape
@@ -132,7 +132,7 @@ def test_sgemm_normal_inputs(gvm, path, shape):
     assert kernel_status() == 0
 
 
-@pytest.mark.parametrize("path", ["fma", "split3", "split3_fused"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_fused", "split3_wide"])
 @pytest.mark.parametrize("shape", [(9, 11, 64), (130, 260, 100), (256, 256, 256)])
 def test_sgemm_integer_exact(gvm, path, shape):
     # |x| <= 16 and K <= 256: every product and partial sum is an integer
@@ -177,6 +177,26 @@ def test_split3_fused_equals_prepass(gvm, shape):
     A, B = synth.sgemm_inputs(synth.task_seed(7, m % 1000), m, n, k)
     C1 = run_sgemm(gvm, A, B, "split3")
     C2 = run_sgemm(gvm, A, B, "split3_fused")
+    assert np.array_equal(bits(C1), bits(C2)), shape
+    from paper_1511_07658_gb300.manager import kernel_status
+
+    assert kernel_status() == 0
+
+
+@pytest.mark.parametrize(
+    "shape",
+    [(256, 256, 32), (257, 130, 67), (512, 512, 512), (129, 257, 513), (300, 1001, 77),
+     (130, 260, 100), (1000, 520, 2052), (4096, 2048, 96), (2500, 3000, 40), (256, 256, 1)],
+)
+def test_split3_wide_equals_prepass(gvm, shape):
+    # 256 x 256 tiles of one CTA (two 128-row MMA halves sharing each B stage,
+    # one accumulator drained after the next tile's first k-step): the same
+    # products in the same order per element, so the pre-pass result bit for
+    # bit. k = 1 and k = 32 leave one group without a k-step of a tile.
+    m, n, k = shape
+    A, B = synth.sgemm_inputs(synth.task_seed(11, m % 1000), m, n, k)
+    C1 = run_sgemm(gvm, A, B, "split3")
+    C2 = run_sgemm(gvm, A, B, "split3_wide")
     assert np.array_equal(bits(C1), bits(C2)), shape
     from paper_1511_07658_gb300.manager import kernel_status
 

@@ -94,14 +94,14 @@ def test_vadd_tiny_config_bitexact(gvm, mode):
     run_workload(gvm, synth.vadd_tiny(), mode=mode)
 
 
-@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
 def test_sgemm_shared_subset(gvm, path):
     """16 ranks sharing the GPU, SGEMM 512^3 (two tasks per rank here; the
     full 64-per-rank configuration runs in test_gpu_fullsize)."""
     run_workload(gvm, synth.sgemm_square(ranks=16, per_rank=2), path=path, slice_mb=64)
 
 
-@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
 def test_mixed_ragged_tasks(gvm, path):
     w = synth.Workload("mixed", 3)
     shapes = [(1, 1, 1), (64, 64, 64), (130, 257, 65), (5, 300, 17)]
@@ -118,7 +118,7 @@ def test_mixed_ragged_tasks(gvm, path):
 
 
 @pytest.mark.parametrize("mode", ["barrier", "continuous"])
-@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
 def test_vmul_tasks_in_mix(gvm, mode, path):
     """Vector-multiply tasks (the paper's VecMult, 15 products) shared with
     vector adds and matrix multiplies, ragged lengths, host mode."""
@@ -175,7 +175,7 @@ def _ps_mix():
 
 
 @pytest.mark.parametrize("mode", ["ps1", "ps2"])
-@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
 def test_paper_stream_modes(gvm, mode, path):
     """PS-1 / PS-2 (the host issues each task's copies and kernel at the
     request barrier): oracle parity, and bitwise the same results as the
@@ -281,7 +281,7 @@ def test_paper_stream_modes_barrier_rules(gvm, mode):
     assert np.array_equal(bits(out2.numpy()), bits(oracle.vmul(a, b, 15)))
 
 
-@pytest.mark.parametrize("path", ["fma", "split3"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
 def test_solo_equals_mix_bitwise(gvm, path):
     """A task's result alone on the GPU equals its result in the mix, bit for
     bit (the tile shape is a function of the task's shape only)."""
@@ -633,7 +633,8 @@ def test_batch_from_contiguous_host_blocks(gvm, slice_mb):
         assert mgr.stats()["device_status"] == 0
 
 
-@pytest.mark.parametrize("mode,path", [("barrier", "split3"), ("continuous", "split3"), ("barrier", "fma")])
+@pytest.mark.parametrize("mode,path", [("barrier", "split3"), ("continuous", "split3"), ("barrier", "fma"),
+                                       ("barrier", "split3_wide"), ("continuous", "split3_wide")])
 def test_stress_mix_ragged_sizes(gvm, mode, path):
     # The stress config's shape mix (70% vector adds with lognormal lengths,
     # 30% square SGEMMs with lognormal sides; most sizes odd, none aligned)
