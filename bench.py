@@ -1067,7 +1067,7 @@ def stress_arm(args):
     import paper_1511_07658_gb300 as g
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    R, P, depth = 128, args.per_rank or 16, 2
+    R, P, depth = 128, args.per_rank or 48, 2
     w0 = synth.stress_mix(ranks=R, per_rank=P, rate_per_rank_hz=1e9)
     for t in w0.tasks:  # the clamp of this leg
         if t.kind == synth.TASK_VADD:
