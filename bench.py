@@ -785,6 +785,11 @@ def gpu_arm(args, w, desc, rank, world):
         "wall_tasks_per_s": tasks_per_step * args.steps / wall,
         "roofline": roof,
         "sched_timeline_last_launch": timeline,
+        "step_ms_distribution": {
+            "step": {"min": 1e3 * min(t_step), "median": 1e3 * statistics.median(t_step), "max": 1e3 * max(t_step)},
+            "launch": {"min": 1e3 * min(t_kernel), "median": 1e3 * statistics.median(t_kernel),
+                       "max": 1e3 * max(t_kernel)},
+            "kind": "CUDA events on the scheduler stream per timed step (step: submit to sync; launch: the flush)"},
         "e2e": e2e,
         "gpu_launches": args.steps if not cont else 1,
         "clocks": clocks,

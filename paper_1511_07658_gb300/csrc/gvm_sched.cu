@@ -31,6 +31,7 @@
 // idle_poll_ns between polls); in barrier (drain) mode it exits once every
 // descriptor published before its launch has been taken.
 #include "gvm_device.cuh"
+#include <cstddef>
 #include <type_traits>
 
 #include "gvm_fused.cuh"
@@ -177,21 +178,24 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
       tidx[i] = idx;
       tsplit[i] = tmain[i] = 0;
       DevTask* dt = &p.tasks[idx];
-      const uint4* src = reinterpret_cast<const uint4*>(&p.host_desc[idx]);
-      uint4* dst = reinterpret_cast<uint4*>(&dt->body);
+      // The task fields: the descriptor's last 128 bytes, in one round trip
+      // (its first 256, the pre-pass form's tensor maps, are not used here).
+      constexpr int kFieldsAt = offsetof(TaskBody, type) / 16;
+      static_assert(offsetof(TaskBody, type) == 256 && sizeof(TaskBody) == 384, "TaskBody fields");
+      static_assert(offsetof(TaskBody, flags) == 260 && offsetof(TaskBody, tag) == 272 &&
+                        offsetof(TaskBody, ntiles) == 276 && offsetof(TaskBody, nsplit) == 280,
+                    "TaskBody header words");
+      const uint4* src = reinterpret_cast<const uint4*>(&p.host_desc[idx]) + kFieldsAt;
+      uint4* dst = reinterpret_cast<uint4*>(&dt->body) + kFieldsAt;
+      uint4 v[8];
 #pragma unroll
-      for (int blk = 0; blk < 3; ++blk) {
-        uint4 v[8];
+      for (int j = 0; j < 8; ++j) v[j] = ld_volatile_v4(src + j);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = ld_volatile_v4(src + blk * 8 + j);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) st_cg_v4(dst + blk * 8 + j, v[j]);
-      }
-      const TaskBody* hb = &p.host_desc[idx];
-      const uint32_t tag = ld_volatile_u32(&hb->tag);
-      const uint32_t ntiles = ld_volatile_u32(&hb->ntiles);
-      const uint32_t nsplit = ld_volatile_u32(&hb->nsplit);
-      const uint32_t flags = ld_volatile_u32(&hb->flags);
+      for (int j = 0; j < 8; ++j) st_cg_v4(dst + j, v[j]);
+      const uint32_t flags = v[0].y;
+      const uint32_t tag = v[1].x;
+      const uint32_t ntiles = v[1].y;
+      const uint32_t nsplit = v[1].z;
       if (tag != s + 1u || nsplit > ntiles) {
         bad = true;
         continue;
