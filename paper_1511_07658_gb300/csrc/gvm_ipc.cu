@@ -247,7 +247,7 @@ bool ingest(gvm_ipc_server* sv, RankServe& r) {
 }
 
 // Publishes completions in order. Returns true if anything moved.
-bool reap_done(gvm_ipc_server* sv, RankServe& r) {
+bool reap_done(RankServe& r) {
   bool moved = false;
   while (r.done < r.submitted) {
     const int p = gvm_poll(r.rank, r.done);
@@ -324,7 +324,7 @@ void serve_loop(gvm_ipc_server* sv) {
     }
     uint64_t comp = 0;
     for (auto& r : sv->rs) {
-      moved |= reap_done(sv, r);
+      moved |= reap_done(r);
       comp += r.done;
     }
     sv->completed.store(comp);
