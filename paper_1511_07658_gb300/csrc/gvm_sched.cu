@@ -155,6 +155,8 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
     if (2u * lanes * quantum > space) quantum = space / (2u * lanes);
 
     uint32_t r = 0, t = 0, take = 0, avail = 0;
+    uint32_t tidx[kMaxQuantum], tsplit[kMaxQuantum], tmain[kMaxQuantum];
+    uint32_t nsplit_e = 0, nmain_e = 0, split_tiles = 0, main_tiles = 0;
     const bool valid = (g + lane) < p.ranks;
     if (valid) {
       r = (rr + g + lane) % p.ranks;
@@ -162,63 +164,57 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
       t = ld_relaxed_gpu(&p.tail[r]);
       avail = h - t;
       const uint32_t lim = min(avail, quantum);
-      for (; take < lim; ++take) {
-        const uint32_t s = t + take;
-        const uint32_t idx = r * p.depth + (s & (p.depth - 1));
-        const uint32_t flags = ld_volatile_u32(&p.host_desc[idx].flags);
-        if ((flags & kFlagNeedsReady) && ld_acquire_gpu(&p.ready[idx]) != s + 1u) break;
-      }
-    }
-
-    uint32_t tidx[kMaxQuantum], tsplit[kMaxQuantum], tmain[kMaxQuantum];
-    uint32_t nsplit_e = 0, nmain_e = 0, split_tiles = 0, main_tiles = 0;
-    for (uint32_t i = 0; i < take; ++i) {
-      const uint32_t s = t + i;
-      const uint32_t idx = r * p.depth + (s & (p.depth - 1));
-      tidx[i] = idx;
-      tsplit[i] = tmain[i] = 0;
-      DevTask* dt = &p.tasks[idx];
-      // The task fields: the descriptor's last 128 bytes, in one round trip
-      // (its first 256, the pre-pass form's tensor maps, are not used here).
+      // The task fields are the descriptor's last 128 bytes (its first 256, the
+      // pre-pass form's tensor maps, are not used here). One read of them from
+      // host memory gives both the readiness rule and the fields to copy.
       constexpr int kFieldsAt = offsetof(TaskBody, type) / 16;
       static_assert(offsetof(TaskBody, type) == 256 && sizeof(TaskBody) == 384, "TaskBody fields");
       static_assert(offsetof(TaskBody, flags) == 260 && offsetof(TaskBody, tag) == 272 &&
                         offsetof(TaskBody, ntiles) == 276 && offsetof(TaskBody, nsplit) == 280,
                     "TaskBody header words");
-      const uint4* src = reinterpret_cast<const uint4*>(&p.host_desc[idx]) + kFieldsAt;
-      uint4* dst = reinterpret_cast<uint4*>(&dt->body) + kFieldsAt;
-      uint4 v[8];
+      for (; take < lim; ++take) {
+        const uint32_t s = t + take;
+        const uint32_t idx = r * p.depth + (s & (p.depth - 1));
+        const uint4* src = reinterpret_cast<const uint4*>(&p.host_desc[idx]) + kFieldsAt;
+        uint4 v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = ld_volatile_v4(src + j);
+        for (int j = 0; j < 8; ++j) v[j] = ld_volatile_v4(src + j);
+        const uint32_t flags = v[0].y;
+        if ((flags & kFlagNeedsReady) && ld_acquire_gpu(&p.ready[idx]) != s + 1u) break;
+        DevTask* dt = &p.tasks[idx];
+        uint4* dst = reinterpret_cast<uint4*>(&dt->body) + kFieldsAt;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) st_cg_v4(dst + j, v[j]);
-      const uint32_t flags = v[0].y;
-      const uint32_t tag = v[1].x;
-      const uint32_t ntiles = v[1].y;
-      const uint32_t nsplit = v[1].z;
-      if (tag != s + 1u || nsplit > ntiles) {
-        bad = true;
-        continue;
-      }
-      atomicExch(&dt->tiles_done, 0u);
-      atomicExch(&dt->split_done, 0u);
-      *reinterpret_cast<volatile uint64_t*>(&dt->t_ingest) = now;
-      if (ntiles == 0) {
-        __threadfence();
-        complete_task(p, idx, tag, flags, now);
-        continue;
-      }
-      tsplit[i] = nsplit;
-      tmain[i] = ntiles - nsplit;
-      if (nsplit) {
-        ++nsplit_e;
-        split_tiles += nsplit;
-      }
-      if (ntiles > nsplit) {
-        ++nmain_e;
-        main_tiles += ntiles - nsplit;
+        for (int j = 0; j < 8; ++j) st_cg_v4(dst + j, v[j]);
+        const uint32_t tag = v[1].x;
+        const uint32_t ntiles = v[1].y;
+        const uint32_t nsplit = v[1].z;
+        tidx[take] = idx;
+        tsplit[take] = tmain[take] = 0;
+        if (tag != s + 1u || nsplit > ntiles) {
+          bad = true;
+          continue;
+        }
+        atomicExch(&dt->tiles_done, 0u);
+        atomicExch(&dt->split_done, 0u);
+        *reinterpret_cast<volatile uint64_t*>(&dt->t_ingest) = now;
+        if (ntiles == 0) {
+          __threadfence();
+          complete_task(p, idx, tag, flags, now);
+          continue;
+        }
+        tsplit[take] = nsplit;
+        tmain[take] = ntiles - nsplit;
+        if (nsplit) {
+          ++nsplit_e;
+          split_tiles += nsplit;
+        }
+        if (ntiles > nsplit) {
+          ++nmain_e;
+          main_tiles += ntiles - nsplit;
+        }
       }
     }
+
     // Split entries of this pass first, then main entries, each group in lane
     // order: the split3 pre-pass of a task is handed out well ahead of its GEMM.
     const uint32_t ie_s = warp_incl_scan(nsplit_e), ie_m = warp_incl_scan(nmain_e);
