@@ -47,3 +47,56 @@ def check_sgemm(C, A, B, R=None):
     if C.size >= FRO_MIN_ELEMENTS:
         assert err <= FRO_TOL, f"relative Frobenius error {err:.3g} > {FRO_TOL}"
     return err
+
+
+def sample_indices(rng, size: int, count: int) -> np.ndarray:
+    """`count` distinct sorted indices of range(size), always holding the
+    first and the last (the edges of the last, ragged tile)."""
+    if size <= count:
+        return np.arange(size)
+    inner = rng.choice(np.arange(1, size - 1), count - 2, replace=False)
+    return np.sort(np.concatenate([[0, size - 1], inner]))
+
+
+class SampledCheck:
+    """The acceptance rule on sampled outputs of many results, for sizes
+    where the full binary64 product is too slow: each block C[rows][:, cols]
+    is compared elementwise with the oracle's product A[rows] @ B[:, cols]
+    (the same dot products the full product would form), and the relative
+    Frobenius error is taken over all blocks together."""
+
+    def __init__(self):
+        self.C = []
+        self.R = []
+        self.worst = 0.0
+
+    def add(self, C, A, B, rows, cols, label=""):
+        self.add_block(np.asarray(C, dtype=np.float32)[np.ix_(rows, cols)], A, B, rows, cols, label)
+
+    def add_block(self, Cs, A, B, rows, cols, label=""):
+        """Cs = the result's entries at rows x cols, already gathered."""
+        A = np.asarray(A, dtype=np.float32)
+        B = np.asarray(B, dtype=np.float32)
+        Ar = np.ascontiguousarray(A[rows])
+        Bc = np.ascontiguousarray(B[:, cols])
+        R = oracle.sgemm64(Ar, Bc)
+        Cs = np.asarray(Cs, dtype=np.float32).reshape(len(rows), len(cols))
+        k = A.shape[1]
+        S = np.abs(Ar).astype(np.float64) @ np.abs(Bc).astype(np.float64)
+        bound = gamma(k) * S + k * 2.0 ** -149
+        worst = float(np.max(np.abs(Cs.astype(np.float64) - R) / bound)) if Cs.size else 0.0
+        assert worst <= 1.0, f"{label}: elementwise split bound exceeded: worst |C - R| / bound = {worst:.3g}"
+        self.worst = max(self.worst, worst)
+        self.C.append(np.ascontiguousarray(Cs).reshape(-1))
+        self.R.append(R.reshape(-1))
+
+    def finish(self) -> float:
+        """Relative Frobenius error over every sample (checked from 256)."""
+        C = np.concatenate(self.C) if self.C else np.zeros(0, np.float32)
+        R = np.concatenate(self.R) if self.R else np.zeros(0)
+        if C.size == 0:
+            return 0.0
+        err = oracle.rel_fro_err(C, R)
+        if C.size >= FRO_MIN_ELEMENTS:
+            assert err <= FRO_TOL, f"relative Frobenius error over {C.size} samples {err:.3g} > {FRO_TOL}"
+        return err

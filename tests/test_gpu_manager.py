@@ -97,7 +97,7 @@ def test_vadd_tiny_config_bitexact(gvm, mode):
 @pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
 def test_sgemm_shared_subset(gvm, path):
     """16 ranks sharing the GPU, SGEMM 512^3 (two tasks per rank here; the
-    full 64-per-rank configuration runs in test_gpu_fullsize)."""
+    full 64-per-rank configuration runs in test_gpu_sizes)."""
     run_workload(gvm, synth.sgemm_square(ranks=16, per_rank=2), path=path, slice_mb=64)
 
 

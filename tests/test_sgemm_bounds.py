@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from sgemm_bounds import check_sgemm, gamma
+from sgemm_bounds import SampledCheck, check_sgemm, gamma, sample_indices
 
 
 def rn_bf16(x):
@@ -85,3 +85,31 @@ def test_rule_rejects_transposed_and_sign_errors():
         check_sgemm(C.T.copy(), A, B)
     with pytest.raises(AssertionError):
         check_sgemm(-C, A, B)
+
+
+def test_sampled_rule_accepts_split_results_and_keeps_edges():
+    rng = np.random.default_rng(5)
+    chk = SampledCheck()
+    for seed, (m, n, k) in enumerate([(40, 36, 64), (130, 257, 65), (3, 300, 17)]):
+        A, B = synth.sgemm_inputs(9100 + seed, m, n, k)
+        C = split3_emulated(A, B)
+        rows, cols = sample_indices(rng, m, 8), sample_indices(rng, n, 8)
+        assert rows[0] == 0 and rows[-1] == m - 1 and cols[0] == 0 and cols[-1] == n - 1
+        assert len(set(rows)) == len(rows) == min(m, 8)
+        chk.add(C, A, B, rows, cols)
+    assert chk.finish() < 1e-5
+
+
+def test_sampled_rule_rejects_a_wrong_sample_and_a_transpose():
+    rng = np.random.default_rng(6)
+    A, B = synth.sgemm_inputs(9200, 24, 24, 32)
+    C = split3_emulated(A, B)
+    rows, cols = sample_indices(rng, 24, 6), sample_indices(rng, 24, 6)
+    bad = C.copy()
+    bad[rows[2], cols[3]] *= 1.001
+    with pytest.raises(AssertionError):
+        SampledCheck().add(bad, A, B, rows, cols)
+    with pytest.raises(AssertionError):
+        SampledCheck().add(C.T.copy(), A, B, rows, cols)
+    with pytest.raises(AssertionError):
+        SampledCheck().add(split3_emulated(A, B, products=("hh",)), A, B, rows, cols)
