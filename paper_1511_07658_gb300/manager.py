@@ -393,7 +393,7 @@ class Manager:
         return span.value / 1e9, [[v / 1e9 for v in list(l)[: len(a)]] for l, a in zip(lat, task_arrays)]
 
     def shutdown(self) -> None:
-        if self.handle is not None:
+        if getattr(self, "handle", None) is not None:
             rc = lib().gvm_shutdown(self.handle)
             self.handle = None
             check(rc, "gvm_shutdown")
@@ -403,6 +403,15 @@ class Manager:
 
     def __exit__(self, *exc):
         self.shutdown()
+
+    def __del__(self):
+        # The arena and control block are torch allocations: a manager dropped
+        # without shutdown (a resident scheduler still running) must stop
+        # before the caching allocator can hand that memory to other tensors.
+        try:
+            self.shutdown()
+        except Exception:
+            pass
 
 
 def vadd_f32(a: torch.Tensor, b: torch.Tensor, c: torch.Tensor, stream=None) -> None:
