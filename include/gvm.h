@@ -287,7 +287,8 @@ GVM_API int gvm_detach(gvm_rank* rank);
 /* Stops the scheduler after in-flight work, waits for the streams, frees the
    rings and the handle. Tasks never taken from a ring report GVM_ECANCELED
    through gvm_sync from then on (the handle is gone, so callers must not sync
-   after shutdown). */
+   after shutdown). GVM_ESTATE, with nothing stopped or freed, while a
+   gvm_ipc server serves this manager: gvm_ipc_stop it first. */
 GVM_API int gvm_shutdown(gvm_ctx* ctx);
 
 GVM_API int gvm_stats_get(gvm_ctx* ctx, gvm_stats* out);

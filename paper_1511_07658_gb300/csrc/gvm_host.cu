@@ -121,6 +121,7 @@ struct gvm_ctx {
   uint32_t launch_gen = 0;
   std::atomic<uint64_t> staged{0}, staged_peak{0}, submitted{0}, completed{0}, h2d{0}, d2h{0}, launches{0};
   bool shut = false;
+  std::atomic<int> ipc_servers{0};  // gvm_ipc servers using this manager
   int device = 0;
   std::vector<cudaStream_t> owned_streams;  // created by gvm_init, destroyed by gvm_shutdown
   ~gvm_ctx() {
@@ -131,6 +132,7 @@ struct gvm_ctx {
 namespace gvm {
 int ctx_mode(const gvm_ctx* ctx) { return ctx->cfg.mode; }
 int ctx_max_ranks(const gvm_ctx* ctx) { return ctx->cfg.max_ranks; }
+void ctx_servers_add(gvm_ctx* ctx, int delta) { ctx->ipc_servers.fetch_add(delta, std::memory_order_acq_rel); }
 }  // namespace gvm
 
 namespace {
@@ -1123,6 +1125,8 @@ int gvm_detach(gvm_rank* r) {
 
 int gvm_shutdown(gvm_ctx* ctx) {
   if (!ctx) return GVM_EINVAL;
+  // A serving thread of gvm_ipc still drives this manager's ranks.
+  if (ctx->ipc_servers.load(std::memory_order_acquire) > 0) return GVM_ESTATE;
   bind_device(ctx);
   int rc = GVM_OK;
   {

@@ -501,6 +501,7 @@ int gvm_ipc_serve(gvm_ctx* ctx, gvm_ipc_region* reg, gvm_ipc_server** out) {
     rs.s->server_pid.store(pid, std::memory_order_release);
   }
   reg->served = true;
+  gvm::ctx_servers_add(ctx, 1);
   sv->th = std::thread(serve_loop, sv);
   *out = sv;
   return GVM_OK;
@@ -535,6 +536,7 @@ int gvm_ipc_stop(gvm_ipc_server* sv) {
     if (d != GVM_OK && rc == GVM_OK) rc = d;
   }
   sv->region->served = false;
+  gvm::ctx_servers_add(sv->ctx, -1);
   delete sv;
   return rc;
 }

@@ -36,5 +36,7 @@ cudaError_t launch_scheduler(int path, const SchedParams& p, int grid, size_t sm
 // Configuration of a manager, for the library's other host modules.
 int ctx_mode(const gvm_ctx* ctx);
 int ctx_max_ranks(const gvm_ctx* ctx);
+// Counts the gvm_ipc servers using a manager (gvm_shutdown refuses while any is).
+void ctx_servers_add(gvm_ctx* ctx, int delta);
 
 }  // namespace gvm

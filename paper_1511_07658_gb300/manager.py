@@ -395,7 +395,8 @@ class Manager:
     def shutdown(self) -> None:
         if getattr(self, "handle", None) is not None:
             rc = lib().gvm_shutdown(self.handle)
-            self.handle = None
+            if rc != _abi.GVM_ESTATE:  # an IPC server still serves it: nothing was freed
+                self.handle = None
             check(rc, "gvm_shutdown")
 
     def __enter__(self):

@@ -70,3 +70,22 @@ def test_refused_task_and_a_client_that_vanishes(gvm):
     # its process has ended); rank 2 runs its mix to completion.
     counts = run_clients(gvm, "barrier", ["bad", "vanish", "mix"])
     assert counts["completed"] >= 1 + 8
+
+
+def test_shutdown_refused_while_served(gvm):
+    # The serving thread drives the manager's ranks: gvm_shutdown refuses
+    # (GVM_ESTATE, nothing freed) until gvm_ipc_stop, then succeeds.
+    name = f"gvmg-guard-{os.getpid()}"
+    region = gvm.IpcRegion.create(name, 2, 4 << 20, 4)
+    try:
+        mgr = gvm.Manager(2, ring_depth=4, mode="barrier", slice_bytes=16 << 20)
+        server = gvm.IpcServer(mgr, region)
+        with pytest.raises(gvm.GvmError) as e:
+            mgr.shutdown()
+        assert e.value.code == gvm.GVM_ESTATE
+        assert mgr.handle is not None
+        server.stop()
+        mgr.shutdown()
+        assert mgr.handle is None
+    finally:
+        region.destroy()
