@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -127,3 +128,22 @@ def test_no_oracle_on_product_path():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library every entry point raises; nothing falls back."""
+    code = (
+        "import paper_1511_07658_gb300 as g\n"
+        "import torch\n"
+        "for call in (lambda: g._abi.lib(), lambda: g.vadd_f32(torch.ones(4), torch.ones(4), torch.ones(4), 0)):\n"
+        "    try:\n"
+        "        call()\n"
+        "    except RuntimeError as e:\n"
+        "        assert 'libgvm.so not found' in str(e), e\n"
+        "    else:\n"
+        "        raise SystemExit('no error')\n"
+        "print('ok')\n"
+    )
+    env = dict(os.environ, GVM_LIB=str(tmp_path / "absent" / "libgvm.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, env=env, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr[-2000:]
