@@ -291,6 +291,8 @@ GVM_API int gvm_detach(gvm_rank* rank);
    gvm_ipc server serves this manager: gvm_ipc_stop it first. */
 GVM_API int gvm_shutdown(gvm_ctx* ctx);
 
+/* Copies the manager's counters (gvm_stats above) into *out (caller-owned).
+   GVM_EINVAL for a NULL argument; callable at any time before gvm_shutdown. */
 GVM_API int gvm_stats_get(gvm_ctx* ctx, gvm_stats* out);
 
 /* Device timestamps (globaltimer, ns) of task seq of this rank: when the
@@ -346,6 +348,8 @@ GVM_API int gvm_open_loop_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_ta
                               const uint64_t* const* arrival_ns, const uint32_t* counts, int32_t nranks,
                               uint32_t max_inflight, double* const* latency_ns, double* span_ns);
 
+/* A static, NUL-terminated description of a GVM_* return code ("unknown
+   error" for other values); never NULL, needs no handle. */
 GVM_API const char* gvm_strerror(int code);
 
 /* ---- the task kernels alone -------------------------------------------- */
