@@ -1185,6 +1185,13 @@ def model_check(args, w):
     else:
         t_comp = timed(lambda: g.vadd_f32(din[0], din[1], dout, stream=s))
     cls = model.classify(t_in, t_comp, t_out)
+    # Tiles of one task in the scheduler (one CTA per SM runs them): 128 x 256
+    # for split3, 128 x 128 for the FMA path; a vector task is one wave.
+    if spec.kind == synth.TASK_SGEMM:
+        tn = 128 if args.path == "fma" else 256
+        tiles = -(-spec.m // 128) * -(-spec.n // tn)
+    else:
+        tiles = 1
     rows = []
     for N in (1, 2, 4, 8, 16):
         mgr = g.Manager(N, ring_depth=4, sgemm_path=args.path, slice_bytes=64 << 20)
@@ -1215,7 +1222,7 @@ def model_check(args, w):
             "measured_s": shared,
             "eq2_or_eq7_s": pred,
             "deviation": model.deviation(shared, pred),
-            "duplex_s": model.shared_time_duplex(N, t_in, t_comp, t_out, 1),
+            "duplex_s": model.shared_time_duplex(N, t_in, t_comp, t_out, model.waves(N, tiles, GB300_SMS, 1)),
             "eq1_no_init_s": model.t_total_no_vt(N, 0.0, t_in, t_comp, t_out, 0.0),
         })
     return {"t_in_s": t_in, "t_comp_s": t_comp, "t_out_s": t_out, "class": cls, "rows": rows,

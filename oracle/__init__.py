@@ -75,8 +75,6 @@ def _load():
             lib.oracle_sgemm_f64.restype = None
             lib.oracle_rel_fro_err.argtypes = [f32p, f64p, i64]
             lib.oracle_rel_fro_err.restype = ctypes.c_double
-            lib.oracle_max_rel_err.argtypes = [f32p, f64p, i64]
-            lib.oracle_max_rel_err.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -133,13 +131,6 @@ def rel_fro_err(C, R) -> float:
     if C.size != R.size:
         raise ValueError("rel_fro_err size mismatch")
     return float(_load().oracle_rel_fro_err(_ptr(C, ctypes.c_float), _ptr(R, ctypes.c_double), C.size))
-
-
-def max_rel_err(C, R) -> float:
-    """max |C - R| / max |R| (diagnostic)."""
-    C = _f32(C)
-    R = np.ascontiguousarray(R, dtype=np.float64)
-    return float(_load().oracle_max_rel_err(_ptr(C, ctypes.c_float), _ptr(R, ctypes.c_double), C.size))
 
 
 def run_task(spec):

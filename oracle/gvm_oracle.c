@@ -77,15 +77,3 @@ double oracle_rel_fro_err(const float* C, const double* R, int64_t count) {
   if (den == 0.0) return num == 0.0 ? 0.0 : INFINITY;
   return sqrt(num) / sqrt(den);
 }
-
-/* Largest |C - R| / max|R| over all elements (diagnostic companion). */
-double oracle_max_rel_err(const float* C, const double* R, int64_t count) {
-  double mx = 0.0, rmax = 0.0;
-  for (int64_t i = 0; i < count; ++i) {
-    const double d = fabs((double)C[i] - R[i]);
-    if (d > mx) mx = d;
-    if (fabs(R[i]) > rmax) rmax = fabs(R[i]);
-  }
-  if (rmax == 0.0) return mx == 0.0 ? 0.0 : INFINITY;
-  return mx / rmax;
-}

@@ -16,11 +16,10 @@ design notes):
 * Eq. 2 assumes every kernel overlaps completely and that copies in opposite
   directions do not overlap (Section 4.2.3). ``shared_time_duplex`` is an
   added variant for a link that carries both directions at once and for
-  kernels that need more than one wave of the GPU.
+  kernels that need more than one wave of the GPU: the longer of the
+  pipeline's copy chain (Eq. 7's form) and its compute chain.
 """
 from __future__ import annotations
-
-import math
 
 
 def t_total_no_vt(n, t_init, t_in, t_comp, t_out, t_ctx):
@@ -102,16 +101,40 @@ def shared_time(n, t_in, t_comp, t_out):
 
 
 def shared_time_duplex(n, t_in, t_comp_wave, t_out, waves):
-    """Variant for a duplex host link and kernels that need ``waves`` waves:
-    the longer copy direction streams N times, the compute of all tasks takes
-    ``waves * t_comp_wave``, and one copy of the shorter direction stays
-    exposed."""
-    return max(n * max(t_in, t_out), waves * t_comp_wave) + min(t_in, t_out)
+    """Variant of Eq. 7 for a host link that carries both directions at once
+    and for a compute phase that needs ``waves`` waves of the GPU.
+
+    Each task runs input copy, kernel, output copy; input copies of different
+    tasks share one direction of the link, output copies the other, and the
+    kernels of different tasks run side by side, ``t_comp_wave`` per wave.
+    The shared time is the longer of two chains of that pipeline:
+
+    * the copy chain: the longer direction streams all N copies, with one
+      task's kernel and one copy of the shorter direction exposed at the ends,
+      ``n max(t_in, t_out) + t_comp_wave + min(t_in, t_out)`` (Eq. 7's form);
+    * the compute chain: the first input, every wave, the last output,
+      ``t_in + waves t_comp_wave + t_out``.
+
+    Neither chain can be shortened, so the value is a lower bound on the
+    pipeline's makespan; with one wave it is the makespan itself, and equals
+    Eq. 7. At N = 1 with one wave it is T_in + T_comp + T_out.
+    """
+    if n <= 0:
+        return 0.0
+    copy_chain = n * max(t_in, t_out) + t_comp_wave + min(t_in, t_out)
+    compute_chain = t_in + waves * t_comp_wave + t_out
+    return max(copy_chain, compute_chain)
 
 
 def waves(n_tasks, ctas_per_task, sms, ctas_per_sm):
-    """Number of full-GPU waves for n_tasks kernels of ctas_per_task blocks."""
-    return math.ceil(n_tasks * ctas_per_task / (sms * ctas_per_sm))
+    """Number of full-GPU waves for n_tasks kernels of ctas_per_task blocks,
+    with ``sms * ctas_per_sm`` blocks resident at once: the ceiling of blocks
+    over slots (0 for no tasks)."""
+    if sms <= 0 or ctas_per_sm <= 0:
+        raise ValueError("waves: no block slots")
+    blocks = n_tasks * ctas_per_task
+    slots = sms * ctas_per_sm
+    return (blocks + slots - 1) // slots
 
 
 def deviation(measured, predicted):

@@ -347,6 +347,94 @@ def test_model_sequential_exceeds_shared():
             assert seq > model.shared_time(n, t_in, t_comp, t_out)
 
 
+def _pipeline_makespan(n, t_in, t_comp, t_out, servers):
+    """Brute force: n identical tasks through input link -> kernel -> output
+    link. Each link carries one copy at a time in task order; a kernel starts
+    once its input has landed and one of ``servers`` kernel slots is free
+    (slots taken in task order). Returns the time the last output lands."""
+    free_in = 0.0
+    slots = [0.0] * servers
+    free_out = 0.0
+    for j in range(n):
+        landed = free_in + t_in
+        free_in = landed
+        s = min(range(servers), key=lambda i: slots[i])
+        done = max(landed, slots[s]) + t_comp
+        slots[s] = done
+        free_out = max(free_out, done) + t_out
+    return free_out
+
+
+def test_model_duplex_closed_cases():
+    # One task, one wave: its own chain, nothing overlaps.
+    for t_init, t_in, t_comp, t_out, t_ctx in _params(6, 100):
+        assert math.isclose(model.shared_time_duplex(1, t_in, t_comp, t_out, 1), t_in + t_comp + t_out, rel_tol=1e-12)
+    # Compute-bound limit: no copies, every wave in turn.
+    assert model.shared_time_duplex(16, 0.0, 3.0, 0.0, 5) == 15.0
+    # Link-bound limit: no compute, the longer direction streams, one copy of
+    # the shorter one is exposed.
+    assert model.shared_time_duplex(8, 1.0, 0.0, 2.5, 1) == 8 * 2.5 + 1.0
+    # Hand cases (worked by drawing the pipeline).
+    assert model.shared_time_duplex(4, 1.0, 3.0, 2.0, 2) == 12.0
+    assert model.shared_time_duplex(6, 1.0, 5.0, 1.0, 3) == 17.0
+    assert model.shared_time_duplex(0, 1.0, 5.0, 1.0, 0) == 0.0
+
+
+def test_model_duplex_against_pipeline_brute_force():
+    # With one wave the variant is the makespan of the simulated pipeline and
+    # equals Eq. 7; with several waves it is a lower bound on it.
+    for t_init, t_in, t_comp, t_out, t_ctx in _params(7, 120):
+        for n in (1, 2, 3, 8, 16):
+            sim = _pipeline_makespan(n, t_in, t_comp, t_out, servers=n)
+            duplex = model.shared_time_duplex(n, t_in, t_comp, t_out, 1)
+            assert math.isclose(duplex, sim, rel_tol=1e-12)
+            assert math.isclose(duplex, model.t_total_ioi_ps2(n, t_in, t_comp, t_out), rel_tol=1e-12)
+            assert duplex <= model.t_total_ioi_ps1(n, t_in, t_comp, t_out) + 1e-12
+            for servers in (1, 2, 5):
+                w = model.waves(n, 1, servers, 1)
+                sim = _pipeline_makespan(n, t_in, t_comp, t_out, servers)
+                bound = model.shared_time_duplex(n, t_in, t_comp, t_out, w)
+                assert bound <= sim + 1e-9
+                # every resource's total busy time fits under it
+                assert bound >= max(n * t_in, n * t_out, w * t_comp) - 1e-12
+    # One slot serialises the kernels; with kernels longer than both copies
+    # the compute chain is then the whole makespan.
+    assert math.isclose(model.shared_time_duplex(5, 1.0, 4.0, 1.0, 5), _pipeline_makespan(5, 1.0, 4.0, 1.0, 1))
+
+
+def test_model_duplex_pins_catch_mutants():
+    def additive(n, t_in, t_c, t_out, w):
+        return n * max(t_in, t_out) + w * t_c + min(t_in, t_out)
+
+    def max_inside(n, t_in, t_c, t_out, w):
+        return max(n * max(t_in, t_out), w * t_c) + min(t_in, t_out)
+
+    for mut in (additive, max_inside):
+        assert (mut(1, 1.0, 2.0, 3.0, 1) != 6.0 or mut(4, 1.0, 3.0, 2.0, 2) != 12.0
+                or mut(6, 1.0, 5.0, 1.0, 3) != 17.0)
+
+
+def test_model_waves_exact_ceiling():
+    assert model.waves(0, 8, 152, 1) == 0
+    assert model.waves(1, 1, 152, 1) == 1
+    assert model.waves(19, 8, 152, 1) == 1  # 152 blocks: exactly one wave
+    assert model.waves(20, 8, 152, 1) == 2  # 160 blocks: one over
+    assert model.waves(152, 1, 152, 1) == 1
+    assert model.waves(153, 1, 152, 1) == 2
+    assert model.waves(304, 1, 152, 2) == 1
+    assert model.waves(305, 1, 152, 2) == 2
+    assert model.waves(1024, 8, 152, 1) == 54  # 8192 tiles of the 16 x 64 SGEMM 512^3 step
+    with pytest.raises(ValueError):
+        model.waves(1, 1, 0, 1)
+    # brute force: the smallest w with w * slots >= blocks
+    for blocks in range(0, 40):
+        for slots in range(1, 9):
+            w = 0
+            while w * slots < blocks:
+                w += 1
+            assert model.waves(blocks, 1, slots, 1) == w
+
+
 # ---------------------------------------------------------------- workloads
 
 
