@@ -391,8 +391,10 @@ GVM_API int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m, i
    4 * (m + n) * kp bytes (kp = k rounded up to 8) must fit, e.g. up to
    m = n = k = 2048; larger shapes return GVM_ENOMEM and launch nothing.
    The first call on a device looks up the array's device address
-   (cudaGetSymbolAddress, with that device current) and caches it; make that
-   first call before any stream capture.
+   (cudaGetSymbolAddress, with that device current) and caches it with the
+   id of the device's context; make that first call before any stream
+   capture. A call in a new context of the device (after cudaDeviceReset)
+   repeats the lookup, so make it before any capture too.
 
    Every call shares the one array, and the array keeps the previous call's
    contents (each call rewrites every byte it reads, so nothing needs

@@ -256,12 +256,32 @@ const DriverApi* driver_api() {
             cudaSuccess ||
         q != cudaDriverEntryPointSuccess)
       return;
+    void* f4 = nullptr;
+    void* f5 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f4, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f5, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return;
+    g_api.ctx_get_current = reinterpret_cast<decltype(g_api.ctx_get_current)>(f4);
+    g_api.ctx_get_id = reinterpret_cast<decltype(g_api.ctx_get_id)>(f5);
     g_api.write_value32 = reinterpret_cast<decltype(g_api.write_value32)>(f1);
     g_api.wait_value32 = reinterpret_cast<decltype(g_api.wait_value32)>(f2);
     g_api.encode_tiled = reinterpret_cast<decltype(g_api.encode_tiled)>(f3);
     g_api_ok = true;
   });
   return g_api_ok ? &g_api : nullptr;
+}
+
+uint64_t current_ctx_id() {
+  const DriverApi* api = driver_api();
+  if (!api) return 0;
+  CUcontext c = nullptr;
+  if (api->ctx_get_current(&c) != CUDA_SUCCESS || c == nullptr) return 0;
+  unsigned long long id = 0;
+  if (api->ctx_get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return (uint64_t)id;
 }
 
 CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUtensorMap* tmA, CUtensorMap* tmB) {
@@ -339,11 +359,15 @@ extern "C" uint64_t gvm_sgemm_scratch_bytes(int32_t m, int32_t n, int32_t k, int
   return path == GVM_SGEMM_SPLIT3 ? split_scratch_bytes(m, n, k) : 0;
 }
 
-// Set once per process; the attribute call is idempotent, so racing first calls are harmless.
-static std::atomic<bool> fma_attr_set{false};
-static std::atomic<bool> tc_attr_set{false};
-static std::atomic<bool> fz_attr_set{false};
-static std::atomic<bool> wd_attr_set{false};
+// The large-shared-memory attribute is set on every call, as for the
+// scheduler: it belongs to the function in the current context, so a flag
+// kept per process would skip it on a second device or after a reset.
+template <typename F>
+static int allow_smem(F* fn, size_t smem) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess
+             ? GVM_OK
+             : GVM_EDEVICE;
+}
 
 extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m, int32_t n, int32_t k,
                              int32_t path, void* scratch, uint64_t scratch_bytes, void* stream) {
@@ -352,24 +376,14 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (path == GVM_SGEMM_FMA) {
     const size_t smem = sizeof(FmaSmem);
-    if (!fma_attr_set) {
-      if (cudaFuncSetAttribute(fma_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
-        return GVM_EDEVICE;
-      fma_attr_set = true;
-    }
+    if (allow_smem(fma_sgemm_kernel, smem) != GVM_OK) return GVM_EDEVICE;
     dim3 grid((n + kFmaTile - 1) / kFmaTile, (m + kFmaTile - 1) / kFmaTile);
     fma_sgemm_kernel<<<grid, kThreads, smem, s>>>(A, B, C, m, n, k);
     return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
   }
   if (path == GVM_SGEMM_SPLIT3_FUSED) {
     const size_t smem = (size_t)kTcStages * kTcStageBytes + 1024;
-    if (!fz_attr_set) {
-      if (cudaFuncSetAttribute(fz_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
-        return GVM_EDEVICE;
-      fz_attr_set = true;
-    }
+    if (allow_smem(fz_sgemm_kernel, smem) != GVM_OK) return GVM_EDEVICE;
     const int sms = sm_count();
     if (sms <= 0) return GVM_ENODEV;
     const int64_t ntiles = (int64_t)((m + kTcM - 1) / kTcM) * ((n + kTcN - 1) / kTcN);
@@ -379,12 +393,7 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
   }
   if (path == GVM_SGEMM_SPLIT3_WIDE) {
     const size_t smem = (size_t)kWdStages * kWdStageBytes + 1024;
-    if (!wd_attr_set) {
-      if (cudaFuncSetAttribute(wd_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
-        return GVM_EDEVICE;
-      wd_attr_set = true;
-    }
+    if (allow_smem(wd_sgemm_kernel, smem) != GVM_OK) return GVM_EDEVICE;
     const int sms = sm_count();
     if (sms <= 0) return GVM_ENODEV;
     const int64_t ntiles = (int64_t)((m + kWdM - 1) / kWdM) * ((n + kWdN - 1) / kWdN);
@@ -418,12 +427,7 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
                                            reinterpret_cast<__nv_bfloat16*>(pb), m, n, k, kp);
   if (cudaGetLastError() != cudaSuccess) return GVM_EDEVICE;
   const size_t smem = (size_t)kTcStages * kTcStageBytes + 1024;
-  if (!tc_attr_set) {
-    if (cudaFuncSetAttribute(tc_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return GVM_EDEVICE;
-    tc_attr_set = true;
-  }
+  if (allow_smem(tc_sgemm_kernel, smem) != GVM_OK) return GVM_EDEVICE;
   dim3 grid((n + kTcN - 1) / kTcN, (m + kTcM - 1) / kTcM);
   tc_sgemm_kernel<<<grid, kThreads, smem, s>>>(tmA, tmB, C, m, n, k, kStandaloneTimeoutNs);
   return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;

@@ -15,13 +15,16 @@
 // cannot use the array's name as a device address (it names a host-side
 // stand-in), so the first call on each device asks the runtime for the
 // array's device address with cudaGetSymbolAddress while that device is
-// current, checks the result, and caches it for that device.
+// current, checks the result, and caches it for that device together with
+// the id of the context it belongs to. A call in a different context of the
+// same device (after cudaDeviceReset) looks the address up again.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "gvm.h"
 #include "gvm_internal.h"
+#include "gvm_runtime.h"
 
 namespace {
 
@@ -30,11 +33,16 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
+struct ScratchCache {
+  uint64_t ctx_id;
+  void* ptr;
+};
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+ScratchCache g_cache[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (set-up on the
-// first call per device). Returns nullptr if the runtime cannot provide it.
+// Device address of g_noalloc_scratch in the current device's context (set-up
+// on the first call per device and context). Returns nullptr if the runtime
+// cannot provide it.
 void* scratch_for_current_device(int* err) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -42,15 +50,17 @@ void* scratch_for_current_device(int* err) {
     return nullptr;
   }
   std::lock_guard<std::mutex> g(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  const uint64_t id = gvm::current_ctx_id();
+  if (id == 0 || g_cache[dev].ctx_id != id || !g_cache[dev].ptr) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       *err = GVM_EDEVICE;
       return nullptr;
     }
-    g_scratch_ptr[dev] = p;
+    // The lookup made the device's primary context current if none was.
+    g_cache[dev] = ScratchCache{gvm::current_ctx_id(), p};
   }
-  return g_scratch_ptr[dev];
+  return g_cache[dev].ptr;
 }
 
 }  // namespace

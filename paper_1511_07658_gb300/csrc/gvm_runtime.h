@@ -19,9 +19,15 @@ struct DriverApi {
   CUresult (*encode_tiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                            const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                            CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  CUresult (*ctx_get_current)(CUcontext*);
+  CUresult (*ctx_get_id)(CUcontext, unsigned long long*);
 };
 // Returns nullptr if the driver or an entry point is unavailable.
 const DriverApi* driver_api();
+
+// Process-unique id of the calling thread's current CUDA context (a context
+// created after cudaDeviceReset gets a new id); 0 if there is none.
+uint64_t current_ctx_id();
 
 // Encodes the two tensor maps of a split3 task whose bf16 planes start at
 // `scratch` (A planes, then B^T planes at scratch + split_a_bytes).
