@@ -68,7 +68,9 @@ def parse():
     p.add_argument("--mode", choices=["barrier", "continuous"], default="barrier")
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
-    p.add_argument("--plain", action="store_true", help="also time the plain one-context-per-rank form")
+    p.add_argument("--skip-plain", action="store_true", help="skip the plain one-context-per-rank forms")
+    p.add_argument("--skip-extra", action="store_true",
+                   help="skip the FMA, vector-add and plain-form legs of the default workload")
     p.add_argument("--model", action="store_true", help="also check timings against Eqs. 1, 2 and 7")
     p.add_argument("--e2e-overlap", type=int, choices=[1, 2], default=1,
                    help="end-to-end leg: steps in flight per rank (2: gvm_spmd_run_overlapped, own manager)")
@@ -108,9 +110,16 @@ def task_inputs(spec):
     return synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
 
 
+_INPUTS = {}
+
+
 def gen_inputs(w):
-    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
-        return list(ex.map(task_inputs, w.tasks))
+    """Every task's operands, generated once per workload and process."""
+    key = (w.name, w.ranks, len(w.tasks))
+    if key not in _INPUTS:
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            _INPUTS[key] = list(ex.map(task_inputs, w.tasks))
+    return _INPUTS[key]
 
 
 # --------------------------------------------------------------- clocks
@@ -534,7 +543,9 @@ def gpu_arm(args, w, desc, rank, world):
 
     native = args.harness == "native"
 
-    def native_steps(arrays, steps):
+    host_lat = []  # host-clock latency of every timed task (s), when the harness records it
+
+    def native_steps(arrays, steps, latency=False):
         # One native thread per rank (gvm_spmd_run). The resident scheduler of
         # continuous mode holds the scheduler stream, so no events there.
         if cont:
@@ -543,10 +554,15 @@ def gpu_arm(args, w, desc, rank, world):
             tp = (ctypes.POINTER(g.GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(g.GvmTask)) for a in arrays])
             cnt = (ctypes.c_uint32 * n)(*[len(a) for a in arrays])
             host = (ctypes.c_double * max(steps, 1))()
-            rc = g._abi.lib().gvm_spmd_run(mgr.handle, hs, tp, cnt, n, steps, None, None, host)
+            rc = g._abi.lib().gvm_spmd_run(mgr.handle, hs, tp, cnt, n, steps, None, None, host, None)
             g._abi.check(rc, "gvm_spmd_run")
             return [h / 1e3 for h in list(host)[:steps]], [h / 1e3 for h in list(host)[:steps]]
-        dev, launch, _ = mgr.spmd_run(ranks, arrays, steps)
+        if latency:
+            dev, launch, _, lat = mgr.spmd_run(ranks, arrays, steps, latency=True)
+            for x in lat:
+                host_lat.extend(x)
+        else:
+            dev, launch, _ = mgr.spmd_run(ranks, arrays, steps)
         return [d / 1e3 for d in dev], [x / 1e3 for x in launch]
 
     if native:
@@ -566,7 +582,7 @@ def gpu_arm(args, w, desc, rank, world):
             st0 = torch.cuda.Event(enable_timing=True)
             st1 = torch.cuda.Event(enable_timing=True)
             st0.record(mgr.sched_stream)
-        t_step, t_kernel = native_steps(res_arrays, args.steps)
+        t_step, t_kernel = native_steps(res_arrays, args.steps, latency=not cont)
         # Sequence numbers are per rank, from 0: warm-up steps, then timed ones.
         lasts = [(args.warmup + args.steps) * len(res_arrays[r]) - 1 for r in range(R)]
         if not cont:
@@ -781,7 +797,12 @@ def gpu_arm(args, w, desc, rank, world):
         "data": "synthetic",
         "config": cfg,
         "gbps": {"hbm_operands": sum(sum(v) for v in sizes.values()) * args.steps * world / total_s / 1e9},
-        "latency_us": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "kind": "device ingest->done, last step"},
+        "latency_us": ({"p50": 1e6 * percentile(host_lat, 50), "p99": 1e6 * percentile(host_lat, 99),
+                        "p999": 1e6 * percentile(host_lat, 99.9), "tasks": len(host_lat),
+                        "kind": "host clock, the rank's submit call -> completion seen by the rank "
+                                "(gvm_sync per task), every timed task"} if host_lat else None),
+        "device_latency_us": {"p50": percentile(lat, 50), "p99": percentile(lat, 99),
+                              "kind": "device ingest->done, last step"},
         "wall_tasks_per_s": tasks_per_step * args.steps / wall,
         "roofline": roof,
         "sched_timeline_last_launch": timeline,
@@ -799,6 +820,99 @@ def gpu_arm(args, w, desc, rank, world):
     if paper_modes is not None:
         out["paper_modes"] = paper_modes
     return out
+
+
+def resident_leg(args, w, inputs, path, steps, warmup, label):
+    """A device-resident leg of its own: a manager on ``path``, every task's
+    operands written into its rank's resident region, ``warmup`` then
+    ``steps`` SPMD steps (gvm_spmd_run), CUDA events around each scheduler
+    launch. Returns tasks/s, the mean launch time, the roofline of the launch
+    against the path's bound and a parity spot check of the first and last
+    task (vector adds bit-exact in full, SGEMM sampled rows against the
+    binary64 oracle)."""
+    import torch
+
+    import oracle
+    import paper_1511_07658_gb300 as g
+
+    R = w.ranks
+    per_rank = len(w.tasks) // R
+    res_offs, need, sizes = {}, [0] * R, {}
+    for spec in w.tasks:
+        if spec.kind == synth.TASK_VADD:
+            la = lb = lc = 4 * spec.n
+        else:
+            la, lb, lc = 4 * spec.m * spec.k, 4 * spec.k * spec.n, 4 * spec.m * spec.n
+        off = need[spec.rank]
+        res_offs[(spec.rank, spec.index)] = (off, off + la, off + la + lb)
+        need[spec.rank] = off + (la + lb + lc + 255) // 256 * 256
+        sizes[(spec.rank, spec.index)] = (la, lb, lc)
+    resident = max(need)
+    slice_bytes = (resident + (64 << 20) + (1 << 20) - 1) // (1 << 20) * (1 << 20)
+    mgr = g.Manager(R, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), sgemm_path=path,
+                    slice_bytes=slice_bytes, resident_bytes=resident, ingest_quantum=args.quantum)
+    try:
+        ranks = [mgr.attach(r) for r in range(R)]
+        for spec, (a, b) in zip(w.tasks, inputs):
+            oa, ob, _ = res_offs[(spec.rank, spec.index)]
+            ranks[spec.rank].write(oa, torch.from_numpy(np.ascontiguousarray(a)).reshape(-1))
+            ranks[spec.rank].write(ob, torch.from_numpy(np.ascontiguousarray(b)).reshape(-1))
+        arrays = build_tasks(w, inputs, True, {"res_offs": res_offs})
+        mgr.spmd_run(ranks, arrays, warmup)
+        torch.cuda.synchronize()
+        dev, launch, _ = mgr.spmd_run(ranks, arrays, steps)
+        torch.cuda.synchronize()
+        spot = []
+        for spec in (w.tasks[0], w.tasks[-1]):
+            inp = inputs[w.tasks.index(spec)]
+            _, _, oc = res_offs[(spec.rank, spec.index)]
+            if spec.kind == synth.TASK_SGEMM:
+                C = torch.empty(spec.m, spec.n)
+                ranks[spec.rank].read(oc, C)
+                rows = np.arange(0, spec.m, 37)
+                spot.append(oracle.rel_fro_err(C.numpy()[rows], oracle.sgemm64(inp[0][rows], inp[1])))
+            else:
+                c = torch.empty(spec.n)
+                ranks[spec.rank].read(oc, c)
+                same = np.array_equal(c.numpy().view(np.uint32), oracle.vadd(*inp).view(np.uint32))
+                spot.append(0.0 if same else 1.0)
+        stats = mgr.stats()
+    finally:
+        mgr.shutdown()
+    total_s = sum(dev) / 1e3
+    kmean = statistics.mean(launch) / 1e3
+    pk, pk_kind = peaks()
+    if w.tasks[0].kind == synth.TASK_SGEMM:
+        flops = sum(s.flops for s in w.tasks)
+        if path == "fma":
+            peak = GB300_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "unit": "TFLOP/s", "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+        else:
+            peak = pk["bf16_tflops"] / 3.0
+            roof = {"bound": "tensor", "unit": "TFLOP/s",
+                    "peak_basis": f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"}
+        achieved = flops / kmean / 1e12
+    else:
+        byts = sum(12 * s.n for s in w.tasks)
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "unit": "GB/s", "peak_basis": f"HBM copy {pk['hbm_gbs']} GB/s ({pk_kind})",
+                "bytes_per_launch": byts}
+        achieved = byts / kmean / 1e9
+    kname = {"fma": "sched_fma_kernel", "split3_wide": "sched_wide_kernel"}.get(path, "sched_fused_kernel")
+    roof.update({"kernel": f"gvm::{kname}", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": ncu_traffic(f"{kname}/{label}"), "launch_ms": kmean * 1e3})
+    return {
+        "workload": label,
+        "value": len(w.tasks) * steps / total_s,
+        "unit": "tasks/s",
+        "steps": steps,
+        "warmup": warmup,
+        "ms_per_step": 1e3 * total_s / steps,
+        "sgemm_path": path,
+        "roofline": roof,
+        "parity_spot_rel_err": max(spot),
+        "device_status": stats["device_status"],
+    }
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -885,68 +999,139 @@ def reference_arm(args, w, desc):
 # --------------------------------------------------------------- plain form
 
 
-def _plain_worker(args_tuple):
-    """One rank in its own process and CUDA context (the conventional,
-    non-virtualized sharing of Section 4.1): default stream, synchronous
-    copies, one task after another."""
-    (rank, per_rank, m, n, k, path, barrier, q) = args_tuple
-    t_import = time.perf_counter()
-    import torch
+def plain_per_rank(w, inputs, path, mode, timeout_s=300.0):
+    """The plain, non-virtualized form (Section 4.1, Eq. 1): each rank is a
+    process of its own (``gvm_plain_rank``, a C client of the library) with
+    its own CUDA context on the default stream, running its tasks one after
+    another through the same standalone task kernel (``path``: "fma" or
+    "split3", the fused split3 kernel). Each process is pinned to its own
+    core, as the paper pins its processes. Modes: "resident" (operands on
+    the device before the start, kernel + synchronize per task), "copy"
+    (synchronous copies of A, B in and C out around every kernel), and
+    "copy_init" (as copy, with context creation, device allocation and
+    page-locking inside the timed region: T_init of Eq. 1).
 
-    import paper_1511_07658_gb300 as g
+    All processes are started, initialised (except in copy_init) and told to
+    go at once; the turnaround is from the first process's start to the last
+    one's end (CLOCK_MONOTONIC, shared by the processes). The last task of
+    the first and last rank is checked against the oracle on sampled rows."""
+    import shutil
+    import tempfile
 
-    A, B = synth.sgemm_inputs(synth.task_seed(rank, 0), m, n, k)
-    hA = torch.from_numpy(A)
-    hB = torch.from_numpy(B)
-    barrier.wait()
-    t0 = time.time()
-    torch.cuda.init()
-    dA = torch.empty(m, k, device="cuda")
-    dB = torch.empty(k, n, device="cuda")
-    dC = torch.empty(m, n, device="cuda")
-    hA = hA.pin_memory()
-    hB = hB.pin_memory()
-    hC = torch.empty(m, n).pin_memory()
-    torch.cuda.synchronize()
-    t_init = time.time() - t0
-    for _ in range(per_rank):
-        dA.copy_(hA)
-        dB.copy_(hB)
-        g.sgemm_f32(dA, dB, dC, path="fma")
-        hC.copy_(dC)
-        torch.cuda.synchronize()
-    t1 = time.time()
-    q.put((rank, t0, t1, t_init, time.perf_counter() - t_import))
+    import oracle
+    from paper_1511_07658_gb300 import build as gb
 
-
-def plain_per_rank(w):
-    import multiprocessing as mp
-
-    ctx = mp.get_context("spawn")
+    exe = gb.build_plain()
     R = w.ranks
-    per_rank = len(w.tasks) // R
-    spec = w.tasks[0]
-    barrier = ctx.Barrier(R)
-    q = ctx.Queue()
-    procs = [ctx.Process(target=_plain_worker, args=((r, per_rank, spec.m, spec.n, spec.k, "fma", barrier, q),))
-             for r in range(R)]
-    for p in procs:
-        p.start()
-    res = [q.get(timeout=600) for _ in range(R)]
-    for p in procs:
-        p.join(timeout=60)
-    t0 = min(r[1] for r in res)
-    t1 = max(r[2] for r in res)
-    init = statistics.mean(r[3] for r in res)
-    turnaround = t1 - t0
+    specs = [[] for _ in range(R)]
+    for spec, inp in zip(w.tasks, inputs):
+        specs[spec.rank].append((spec, inp))
+    per_rank = len(specs[0])
+    m, n, k = specs[0][0][0].m, specs[0][0][0].n, specs[0][0][0].k
+    path_no = {"fma": 0, "split3": 2}[path]
+    tmp = tempfile.mkdtemp(prefix="gvm_plain_", dir="/dev/shm" if os.path.isdir("/dev/shm") else None)
+    cores = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
+    procs = []
+    try:
+        for r in range(R):
+            with open(os.path.join(tmp, f"{r}.in"), "wb") as f:
+                for _, (A, B) in specs[r]:
+                    f.write(np.ascontiguousarray(A, dtype=np.float32).tobytes())
+                    f.write(np.ascontiguousarray(B, dtype=np.float32).tobytes())
+        deadline = time.time() + timeout_s
+
+        def readline(p):
+            # one line of a rank's stdout, or an error once the deadline passes
+            import select
+
+            buf = b""
+            fd = p.stdout.fileno()
+            while not buf.endswith(b"\n"):
+                left = deadline - time.time()
+                if left <= 0 or not select.select([fd], [], [], left)[0]:
+                    raise RuntimeError("plain rank timed out")
+                chunk = os.read(fd, 1)
+                if not chunk:
+                    raise RuntimeError(f"plain rank exited with code {p.wait()}")
+                buf += chunk
+            return buf
+
+        t_spawn = time.perf_counter()
+        for r in range(R):
+            core = cores[r % len(cores)] if cores else -1
+            procs.append(subprocess.Popen(
+                [exe, str(per_rank), str(m), str(n), str(k), str(path_no), mode, os.path.join(tmp, f"{r}.in"),
+                 os.path.join(tmp, f"{r}.out"), str(core)],
+                stdin=subprocess.PIPE, stdout=subprocess.PIPE))
+        spawn_to_ready = []
+        for p in procs:
+            if readline(p).strip() != b"ready":
+                raise RuntimeError("plain rank did not get ready")
+            spawn_to_ready.append(time.perf_counter() - t_spawn)
+        for p in procs:
+            p.stdin.write(b"g")
+            p.stdin.flush()
+        res = []
+        for p in procs:
+            line = readline(p).split()
+            if len(line) != 4:
+                raise RuntimeError("plain rank gave no result")
+            res.append((int(line[0]), int(line[1]), int(line[2]), int(line[3])))
+            p.wait(timeout=max(1.0, deadline - time.time()))
+        bad = [r for r, x in enumerate(res) if x[3] != 0]
+        if bad:
+            raise RuntimeError(f"plain ranks {bad} failed with codes {[res[r][3] for r in bad]}")
+        spot = []
+        for r in (0, R - 1):
+            spec, (A, B) = specs[r][-1]
+            C = np.fromfile(os.path.join(tmp, f"{r}.out"), dtype=np.float32).reshape(m, n)
+            rows = np.arange(0, m, 37)
+            spot.append(oracle.rel_fro_err(C[rows], oracle.sgemm64(A[rows], B)))
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+                p.wait()
+        shutil.rmtree(tmp, ignore_errors=True)
+    t0 = min(x[0] for x in res)
+    t1 = max(x[1] for x in res)
+    turnaround = (t1 - t0) / 1e9
+    t_init = [x[2] / 1e9 for x in res]
     return {
         "value": len(w.tasks) / turnaround,
-        "value_excl_init": len(w.tasks) / max(1e-9, turnaround - max(r[3] for r in res)),
         "unit": "tasks/s",
         "turnaround_s": turnaround,
-        "mean_t_init_s": init,
-        "form": f"{R} processes, one CUDA context each, default stream, synchronous copies, FMA SGEMM",
+        "t_init_s": {"mean": statistics.mean(t_init), "max": max(t_init),
+                     "kind": "context creation + device allocation + page-locking, per process, "
+                             + ("inside the timed region" if mode == "copy_init" else "before the start")},
+        "spawn_to_ready_s_max": max(spawn_to_ready),
+        "parity_spot_rel_err": max(spot),
+        "form": f"{R} processes (one core each), one CUDA context each, default stream, "
+                f"{'operands resident' if mode == 'resident' else 'synchronous copies per task'}, "
+                f"{'FMA' if path == 'fma' else 'split3 (fused)'} SGEMM kernel alone per task",
     }
+
+
+def plain_forms(w, out):
+    """The plain per-rank forms beside the shared ones, like for like: the
+    resident plain form against ``value`` (operands in HBM on both sides),
+    the copying plain form against ``e2e`` (host buffers on both sides), the
+    copying form with T_init inside its timed region (Eq. 1 as the paper
+    states it), and the FMA kernel on both sides."""
+    inputs = gen_inputs(w)
+    res = {"split3": {}, "fma": {}}
+    for mode in ("resident", "copy", "copy_init"):
+        res["split3"][mode] = plain_per_rank(w, inputs, "split3", mode)
+    for mode in ("resident", "copy"):
+        res["fma"][mode] = plain_per_rank(w, inputs, "fma", mode)
+    ratios = {"shared_over_plain_resident": out["value"] / res["split3"]["resident"]["value"]}
+    if out.get("e2e"):
+        ratios["shared_e2e_over_plain_copy"] = out["e2e"]["value"] / res["split3"]["copy"]["value"]
+        ratios["shared_e2e_over_plain_copy_with_init"] = out["e2e"]["value"] / res["split3"]["copy_init"]["value"]
+    if out.get("fma"):
+        ratios["fma_shared_over_plain_resident"] = out["fma"]["value"] / res["fma"]["resident"]["value"]
+    res["ratios"] = ratios
+    return res
 
 
 # --------------------------------------------------------------- serving loop
@@ -1593,10 +1778,22 @@ def main():
         dist.init_process_group("nccl")
     out = gpu_arm(args, w, desc, rank, world)
     if rank == 0:
+        extras = world == 1 and not args.skip_extra and args.workload == "sgemm512"
+        if extras and args.path != "fma":
+            # The plain FP32-FMA path on the same workload (the precision
+            # baseline of the headline's split3 arithmetic).
+            out["fma"] = resident_leg(args, w, gen_inputs(w), "fma", max(3, args.steps // 2), args.warmup, "sgemm512")
+        if extras:
+            # Vector adds through the scheduler at a size far beyond L2: the
+            # HBM roofline of the elementwise task kernel on the product path.
+            wv = synth.vadd_tiny(ranks=16, per_rank=4, n=1 << 22)
+            out["vadd_hbm"] = resident_leg(args, wv, gen_inputs(wv), "split3", max(5, args.steps), args.warmup,
+                                           "vadd16x4_2p22")
+            out["vadd_hbm"]["workload"] = "vector add n=2^22, 16 ranks x 4 tasks (3.2 GB of HBM traffic a step)"
+        if extras and not args.skip_plain:
+            out["plain_per_rank"] = plain_forms(w, out)
         if not args.skip_cpu:
             out["cpu_baseline"] = cpu_baseline(w)
-        if args.plain and w.tasks[0].kind == synth.TASK_SGEMM:
-            out["plain_per_rank"] = plain_per_rank(w)
         if args.cross_process:
             out["cross_process"] = cross_process_check(args, w)
         if args.model:

@@ -314,11 +314,17 @@ GVM_API int gvm_task_times(gvm_rank* rank, uint64_t seq, uint64_t* t_ingest_ns, 
    scheduler stream from before the first submit of step i to after its last
    sync; launch_ms_device[i] the same around step i's gvm_flush (its
    scheduler launch; 0 in continuous mode); step_ms_host[i] the step on the
-   host clock. Returns GVM_OK or the first error any rank saw (the remaining
-   steps are skipped). */
+   host clock. latency_ns (may be NULL, as may any latency_ns[r]) asks for
+   each task's latency as the rank sees it: rank r then collects its batch
+   task by task in submission order (gvm_sync on each), and
+   latency_ns[r][i * counts[r] + j] (steps * counts[r] doubles) is the host
+   time from the rank's gvm_submit_many call of step i to the moment
+   gvm_sync showed task j of that batch complete (ns, CLOCK_MONOTONIC).
+   Returns GVM_OK or the first error any rank saw (the remaining steps are
+   skipped). The batch submit call counts as each of its tasks' submit. */
 GVM_API int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks,
                          const uint32_t* counts, int32_t nranks, int32_t steps, float* step_ms_device,
-                         float* launch_ms_device, double* step_ms_host);
+                         float* launch_ms_device, double* step_ms_host, double* const* latency_ns);
 
 /* The same pattern with two steps in flight per rank: a rank submits step i
    + 1 (and, in barrier mode, thread 0 flushes it) before it collects the

@@ -144,7 +144,7 @@ PROTOTYPES = {
     "gvm_spmd_run": (
         c_int,
         [c_void_p, POINTER(c_void_p), POINTER(POINTER(GvmTask)), POINTER(c_uint32), c_int32, c_int32,
-         POINTER(c_float), POINTER(c_float), POINTER(c_double)],
+         POINTER(c_float), POINTER(c_float), POINTER(c_double), POINTER(POINTER(c_double))],
     ),
     "gvm_spmd_run_overlapped": (
         c_int,

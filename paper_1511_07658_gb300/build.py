@@ -53,6 +53,30 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+PLAIN_SRC = os.path.join(CSRC, "gvm_plain_rank.c")
+PLAIN_EXE = os.path.join(OUT_DIR, "gvm_plain_rank")
+
+
+def build_plain(force: bool = False) -> str:
+    """The plain-form rank program (one process and context per rank), a C
+    client of libgvm.so and the CUDA runtime, built with gcc."""
+    if not force and os.path.exists(PLAIN_EXE) and os.path.getmtime(PLAIN_EXE) >= max(
+            os.path.getmtime(PLAIN_SRC), os.path.getmtime(LIB)):
+        return PLAIN_EXE
+    cuda = os.path.dirname(os.path.dirname(os.path.realpath(nvcc())))
+    tmp = PLAIN_EXE + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-I",
+           os.path.join(cuda, "include"), PLAIN_SRC, "-o", tmp, "-L", OUT_DIR, "-lgvm",
+           "-Wl,-rpath," + OUT_DIR, "-L", os.path.join(cuda, "lib64"), "-lcudart",
+           "-Wl,-rpath," + os.path.join(cuda, "lib64")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("gcc failed for the plain-form rank program")
+    os.replace(tmp, PLAIN_EXE)
+    return PLAIN_EXE
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -87,6 +111,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
         os.replace(tmp, LIB)
+    build_plain(force)
     return LIB
 
 

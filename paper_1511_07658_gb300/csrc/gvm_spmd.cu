@@ -70,7 +70,7 @@ int submit_batch(gvm_rank* r, const gvm_task* tasks, uint32_t count, uint64_t* l
 
 extern "C" int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks,
                             const uint32_t* counts, int32_t nranks, int32_t steps, float* step_ms_device,
-                            float* launch_ms_device, double* step_ms_host) {
+                            float* launch_ms_device, double* step_ms_host, double* const* latency_ns) {
   if (!ctx || !ranks || !tasks || !counts || nranks <= 0 || steps < 0) return GVM_EINVAL;
   for (int r = 0; r < nranks; ++r)
     if (!ranks[r] || (counts[r] && !tasks[r])) return GVM_EINVAL;
@@ -93,6 +93,7 @@ extern "C" int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task
   std::vector<std::chrono::steady_clock::time_point> t0(steps), t1(steps);
   auto body = [&](int r) {
     cudaSetDevice(dev);
+    double* lat = latency_ns ? latency_ns[r] : nullptr;
     for (int i = 0; i < steps; ++i) {
       if (r == 0) {
         t0[i] = std::chrono::steady_clock::now();
@@ -100,6 +101,7 @@ extern "C" int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task
       }
       bar.wait();
       uint64_t last = 0;
+      const auto t_submit = std::chrono::steady_clock::now();
       int rc = err.load() == GVM_OK && counts[r] ? submit_batch(ranks[r], tasks[r], counts[r], &last) : GVM_OK;
       if (rc != GVM_OK) {
         int ok = GVM_OK;
@@ -116,7 +118,22 @@ extern "C" int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task
         }
       }
       bar.wait();
-      if (err.load() == GVM_OK && counts[r]) {
+      if (err.load() == GVM_OK && counts[r] && lat) {
+        // Collect the batch task by task, in submission order, recording
+        // when each completion becomes visible to the rank.
+        const uint64_t first = last + 1 - counts[r];
+        for (uint32_t j = 0; j < counts[r] && err.load() == GVM_OK; ++j) {
+          rc = gvm_sync(ranks[r], first + j);
+          if (rc != GVM_OK) {
+            int ok = GVM_OK;
+            err.compare_exchange_strong(ok, rc);
+            break;
+          }
+          lat[(size_t)i * counts[r] + j] =
+              (double)std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t_submit)
+                  .count();
+        }
+      } else if (err.load() == GVM_OK && counts[r]) {
         rc = gvm_sync(ranks[r], last);
         if (rc != GVM_OK) {
           int ok = GVM_OK;

@@ -340,12 +340,14 @@ class Manager:
         out["launch_phase"] = list(s.launch_phase)
         return out
 
-    def spmd_run(self, ranks, task_arrays, steps: int) -> tuple[list[float], list[float], list[float]]:
+    def spmd_run(self, ranks, task_arrays, steps: int, latency: bool = False):
         """Runs ``steps`` SPMD steps natively (gvm_spmd_run): one thread per
         rank submits ``task_arrays[i]`` (a ctypes array of GvmTask) for
         ``ranks[i]``, then flush and sync. Returns per-step times in ms:
         (step, scheduler launch) by CUDA events on the scheduler stream, and
-        the step on the host clock."""
+        the step on the host clock. With ``latency``, a fourth item: per rank,
+        the host-clock latency in seconds of every task of every step, from
+        the rank's submit call to the moment the rank saw it complete."""
         n = len(ranks)
         hs = (c_void_p * n)(*[r.handle for r in ranks])
         tp = (ctypes.POINTER(GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(GvmTask)) for a in task_arrays])
@@ -353,8 +355,15 @@ class Manager:
         dev = (ctypes.c_float * max(steps, 1))()
         launch = (ctypes.c_float * max(steps, 1))()
         host = (ctypes.c_double * max(steps, 1))()
-        check(lib().gvm_spmd_run(self.handle, hs, tp, cnt, n, steps, dev, launch, host), "gvm_spmd_run")
-        return list(dev)[:steps], list(launch)[:steps], list(host)[:steps]
+        lat = lp = None
+        if latency:
+            lat = [(ctypes.c_double * max(steps * len(a), 1))() for a in task_arrays]
+            lp = (ctypes.POINTER(ctypes.c_double) * n)(*[ctypes.cast(x, ctypes.POINTER(ctypes.c_double)) for x in lat])
+        check(lib().gvm_spmd_run(self.handle, hs, tp, cnt, n, steps, dev, launch, host, lp), "gvm_spmd_run")
+        out = (list(dev)[:steps], list(launch)[:steps], list(host)[:steps])
+        if latency:
+            out += ([[v / 1e9 for v in list(x)[:steps * len(a)]] for x, a in zip(lat, task_arrays)],)
+        return out
 
     def spmd_run_overlapped(self, ranks, arrays_even, arrays_odd, steps: int) -> tuple[float, list[float]]:
         """gvm_spmd_run_overlapped: like spmd_run with two steps in flight per

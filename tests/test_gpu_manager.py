@@ -461,11 +461,20 @@ def test_spmd_harness_steps(gvm, mode):
             t.a, t.b, t.c = ins[0].data_ptr(), ins[1].data_ptr(), out.data_ptr()
             keep.append((spec, ins, out, ref))
         if mode != "continuous":
-            dev, launch, host = mgr.spmd_run(ranks, arrays, 3)
+            dev, launch, host, lat = mgr.spmd_run(ranks, arrays, 3, latency=True)
             assert all(x > 0 for x in dev)
             if mode == "barrier":
                 assert all(x > 0 for x in launch)
                 assert all(l <= d for l, d in zip(launch, dev))
+            # host-clock latency of every task: positive, in submission order
+            # within a step (collected in order), never longer than its step
+            for r in range(w.ranks):
+                assert len(lat[r]) == 3 * 6
+                for i in range(3):
+                    step = lat[r][6 * i:6 * i + 6]
+                    assert all(x > 0 for x in step)
+                    assert step == sorted(step)
+                    assert step[-1] * 1e3 <= host[i] + 1e-6
         else:
             n = len(ranks)
             import ctypes
@@ -474,7 +483,7 @@ def test_spmd_harness_steps(gvm, mode):
             tp = (ctypes.POINTER(gvm.GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(gvm.GvmTask)) for a in arrays])
             cnt = (ctypes.c_uint32 * n)(*[6] * n)
             host = (ctypes.c_double * 3)()
-            rc = gvm._abi.lib().gvm_spmd_run(mgr.handle, hs, tp, cnt, n, 3, None, None, host)
+            rc = gvm._abi.lib().gvm_spmd_run(mgr.handle, hs, tp, cnt, n, 3, None, None, host, None)
             assert rc == 0, rc
             host = list(host)
         assert all(x > 0 for x in host)
