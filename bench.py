@@ -582,7 +582,7 @@ def gpu_arm(args, w, desc, rank, world):
             st0 = torch.cuda.Event(enable_timing=True)
             st1 = torch.cuda.Event(enable_timing=True)
             st0.record(mgr.sched_stream)
-        t_step, t_kernel = native_steps(res_arrays, args.steps, latency=not cont)
+        t_step, t_kernel = native_steps(res_arrays, args.steps)
         # Sequence numbers are per rank, from 0: warm-up steps, then timed ones.
         lasts = [(args.warmup + args.steps) * len(res_arrays[r]) - 1 for r in range(R)]
         if not cont:
@@ -626,6 +626,13 @@ def gpu_arm(args, w, desc, rank, world):
         for s in range(lasts[r] - per_rank + 1, lasts[r] + 1):
             t0, t1 = rk.task_times(s)
             lat.append((t1 - t0) / 1e3)
+    # Host-clock latency (the rank's submit call -> the completion it sees)
+    # over a few more steps in which every rank collects its tasks one by one
+    # (collecting them one by one adds host time between steps, so these
+    # steps are not part of the timed ones).
+    lat_steps = min(5, args.steps)
+    if native and not cont:
+        native_steps(res_arrays, lat_steps, latency=True)
     tasks_per_step = len(w.tasks)
     if world > 1:
         total_s = max_over_ranks(total_s, world)
@@ -799,8 +806,9 @@ def gpu_arm(args, w, desc, rank, world):
         "gbps": {"hbm_operands": sum(sum(v) for v in sizes.values()) * args.steps * world / total_s / 1e9},
         "latency_us": ({"p50": 1e6 * percentile(host_lat, 50), "p99": 1e6 * percentile(host_lat, 99),
                         "p999": 1e6 * percentile(host_lat, 99.9), "tasks": len(host_lat),
-                        "kind": "host clock, the rank's submit call -> completion seen by the rank "
-                                "(gvm_sync per task), every timed task"} if host_lat else None),
+                        "kind": f"host clock, the rank's submit call -> completion seen by the rank "
+                                f"(gvm_sync per task), every task of {lat_steps} steps after the timed ones"}
+                       if host_lat else None),
         "device_latency_us": {"p50": percentile(lat, 50), "p99": percentile(lat, 99),
                               "kind": "device ingest->done, last step"},
         "wall_tasks_per_s": tasks_per_step * args.steps / wall,
@@ -999,22 +1007,24 @@ def reference_arm(args, w, desc):
 # --------------------------------------------------------------- plain form
 
 
-def plain_per_rank(w, inputs, path, mode, timeout_s=300.0):
+def plain_per_rank(w, inputs, phases, init="before", timeout_s=300.0):
     """The plain, non-virtualized form (Section 4.1, Eq. 1): each rank is a
     process of its own (``gvm_plain_rank``, a C client of the library) with
     its own CUDA context on the default stream, running its tasks one after
-    another through the same standalone task kernel (``path``: "fma" or
-    "split3", the fused split3 kernel). Each process is pinned to its own
-    core, as the paper pins its processes. Modes: "resident" (operands on
-    the device before the start, kernel + synchronize per task), "copy"
-    (synchronous copies of A, B in and C out around every kernel), and
-    "copy_init" (as copy, with context creation, device allocation and
-    page-locking inside the timed region: T_init of Eq. 1).
+    another through the same standalone task kernel. Each process is pinned
+    to its own core, as the paper pins its processes. ``phases`` is a list of
+    (path, mode): path "fma" or "split3" (the fused split3 kernel), mode
+    "resident" (operands on the device before the start, kernel +
+    synchronize per task) or "copy" (synchronous copies of A, B in and C out
+    around every kernel). ``init`` "before": context creation, device
+    allocation and page-locking happen before the first start; "timed":
+    inside the first phase's timed region (T_init of Eq. 1).
 
-    All processes are started, initialised (except in copy_init) and told to
-    go at once; the turnaround is from the first process's start to the last
-    one's end (CLOCK_MONOTONIC, shared by the processes). The last task of
+    Every process is started and told to go at once, phase after phase; a
+    phase's turnaround is from the first process's start to the last one's
+    end (CLOCK_MONOTONIC, shared by the processes). Each phase's last task of
     the first and last rank is checked against the oracle on sampled rows."""
+    import select
     import shutil
     import tempfile
 
@@ -1028,88 +1038,100 @@ def plain_per_rank(w, inputs, path, mode, timeout_s=300.0):
         specs[spec.rank].append((spec, inp))
     per_rank = len(specs[0])
     m, n, k = specs[0][0][0].m, specs[0][0][0].n, specs[0][0][0].k
-    path_no = {"fma": 0, "split3": 2}[path]
+    path_no = {"fma": 0, "split3": 2}
     tmp = tempfile.mkdtemp(prefix="gvm_plain_", dir="/dev/shm" if os.path.isdir("/dev/shm") else None)
     cores = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
     procs = []
+    deadline = time.time() + timeout_s
+
+    def readline(p):
+        # one line of a rank's stdout, or an error once the deadline passes
+        buf = b""
+        fd = p.stdout.fileno()
+        while not buf.endswith(b"\n"):
+            left = deadline - time.time()
+            if left <= 0 or not select.select([fd], [], [], left)[0]:
+                raise RuntimeError("plain rank timed out")
+            chunk = os.read(fd, 1)
+            if not chunk:
+                raise RuntimeError(f"plain rank exited with code {p.wait()}")
+            buf += chunk
+        return buf
+
+    out = []
     try:
         for r in range(R):
             with open(os.path.join(tmp, f"{r}.in"), "wb") as f:
                 for _, (A, B) in specs[r]:
                     f.write(np.ascontiguousarray(A, dtype=np.float32).tobytes())
                     f.write(np.ascontiguousarray(B, dtype=np.float32).tobytes())
-        deadline = time.time() + timeout_s
-
-        def readline(p):
-            # one line of a rank's stdout, or an error once the deadline passes
-            import select
-
-            buf = b""
-            fd = p.stdout.fileno()
-            while not buf.endswith(b"\n"):
-                left = deadline - time.time()
-                if left <= 0 or not select.select([fd], [], [], left)[0]:
-                    raise RuntimeError("plain rank timed out")
-                chunk = os.read(fd, 1)
-                if not chunk:
-                    raise RuntimeError(f"plain rank exited with code {p.wait()}")
-                buf += chunk
-            return buf
-
         t_spawn = time.perf_counter()
         for r in range(R):
             core = cores[r % len(cores)] if cores else -1
             procs.append(subprocess.Popen(
-                [exe, str(per_rank), str(m), str(n), str(k), str(path_no), mode, os.path.join(tmp, f"{r}.in"),
-                 os.path.join(tmp, f"{r}.out"), str(core)],
+                [exe, str(per_rank), str(m), str(n), str(k), os.path.join(tmp, f"{r}.in"),
+                 os.path.join(tmp, f"{r}.out"), str(core), init]
+                + [f"{path_no[p]}:{mode}" for p, mode in phases],
                 stdin=subprocess.PIPE, stdout=subprocess.PIPE))
-        spawn_to_ready = []
+        ready = []
         for p in procs:
-            if readline(p).strip() != b"ready":
+            f = readline(p).split()
+            if len(f) != 4 or f[0] != b"ready":
                 raise RuntimeError("plain rank did not get ready")
-            spawn_to_ready.append(time.perf_counter() - t_spawn)
+            ready.append((time.perf_counter() - t_spawn, int(f[1]) / 1e9, int(f[2]) / 1e9, int(f[3]) / 1e9))
+        for i, (path, mode) in enumerate(phases):
+            for p in procs:
+                p.stdin.write(b"g")
+                p.stdin.flush()
+            res = []
+            for p in procs:
+                f = readline(p).split()
+                if len(f) != 4:
+                    raise RuntimeError("plain rank gave no result")
+                res.append((int(f[0]), int(f[1]), int(f[2]), int(f[3])))
+            bad = [r for r, x in enumerate(res) if x[3] != 0]
+            if bad:
+                raise RuntimeError(f"plain ranks {bad} failed with codes {[res[r][3] for r in bad]}")
+            spot = []
+            for r in (0, R - 1):
+                spec, (A, B) = specs[r][-1]
+                C = np.fromfile(os.path.join(tmp, f"{r}.out.{i}"), dtype=np.float32).reshape(m, n)
+                rows = np.arange(0, m, 37)
+                spot.append(oracle.rel_fro_err(C[rows], oracle.sgemm64(A[rows], B)))
+            turnaround = (max(x[1] for x in res) - min(x[0] for x in res)) / 1e9
+            rec = {
+                "value": len(w.tasks) / turnaround,
+                "unit": "tasks/s",
+                "turnaround_s": turnaround,
+                "parity_spot_rel_err": max(spot),
+                "form": f"{R} processes (one core each), one CUDA context each, default stream, "
+                        f"{'operands resident' if mode == 'resident' else 'synchronous copies per task'}, "
+                        f"{'FMA' if path == 'fma' else 'split3 (fused)'} SGEMM kernel alone per task",
+            }
+            if init == "timed" and i == 0:
+                ti = [x[2] / 1e9 for x in res]
+                rec["t_init_s"] = {"mean": statistics.mean(ti), "max": max(ti),
+                                   "kind": "context creation + device allocation + page-locking per process, "
+                                           "all processes at once, inside the timed region"}
+            out.append(rec)
         for p in procs:
-            p.stdin.write(b"g")
-            p.stdin.flush()
-        res = []
-        for p in procs:
-            line = readline(p).split()
-            if len(line) != 4:
-                raise RuntimeError("plain rank gave no result")
-            res.append((int(line[0]), int(line[1]), int(line[2]), int(line[3])))
             p.wait(timeout=max(1.0, deadline - time.time()))
-        bad = [r for r, x in enumerate(res) if x[3] != 0]
-        if bad:
-            raise RuntimeError(f"plain ranks {bad} failed with codes {[res[r][3] for r in bad]}")
-        spot = []
-        for r in (0, R - 1):
-            spec, (A, B) = specs[r][-1]
-            C = np.fromfile(os.path.join(tmp, f"{r}.out"), dtype=np.float32).reshape(m, n)
-            rows = np.arange(0, m, 37)
-            spot.append(oracle.rel_fro_err(C[rows], oracle.sgemm64(A[rows], B)))
     finally:
         for p in procs:
             if p.poll() is None:
                 p.kill()
                 p.wait()
         shutil.rmtree(tmp, ignore_errors=True)
-    t0 = min(x[0] for x in res)
-    t1 = max(x[1] for x in res)
-    turnaround = (t1 - t0) / 1e9
-    t_init = [x[2] / 1e9 for x in res]
-    return {
-        "value": len(w.tasks) / turnaround,
-        "unit": "tasks/s",
-        "turnaround_s": turnaround,
-        "t_init_s": {"mean": statistics.mean(t_init), "max": max(t_init),
-                     "kind": "context creation + device allocation + page-locking, per process, "
-                             + ("inside the timed region" if mode == "copy_init" else "before the start")},
-        "spawn_to_ready_s_max": max(spawn_to_ready),
-        "parity_spot_rel_err": max(spot),
-        "form": f"{R} processes (one core each), one CUDA context each, default stream, "
-                f"{'operands resident' if mode == 'resident' else 'synchronous copies per task'}, "
-                f"{'FMA' if path == 'fma' else 'split3 (fused)'} SGEMM kernel alone per task",
-    }
+    init_rec = None
+    if init == "before":
+        init_rec = {"mean_s": statistics.mean(x[1] + x[2] + x[3] for x in ready),
+                    "max_s": max(x[1] + x[2] + x[3] for x in ready),
+                    "context_mean_s": statistics.mean(x[1] for x in ready),
+                    "alloc_mean_s": statistics.mean(x[2] for x in ready),
+                    "page_lock_mean_s": statistics.mean(x[3] for x in ready),
+                    "spawn_to_ready_max_s": max(x[0] for x in ready),
+                    "kind": "per process, all processes initialising at once, before the start"}
+    return out, init_rec
 
 
 def plain_forms(w, out):
@@ -1117,17 +1139,21 @@ def plain_forms(w, out):
     resident plain form against ``value`` (operands in HBM on both sides),
     the copying plain form against ``e2e`` (host buffers on both sides), the
     copying form with T_init inside its timed region (Eq. 1 as the paper
-    states it), and the FMA kernel on both sides."""
+    states it), and the FMA kernel on both sides. One set of processes runs
+    the four forms whose initialisation comes before the start; a second
+    set, the one that initialises inside the timed region."""
     inputs = gen_inputs(w)
-    res = {"split3": {}, "fma": {}}
-    for mode in ("resident", "copy", "copy_init"):
-        res["split3"][mode] = plain_per_rank(w, inputs, "split3", mode)
-    for mode in ("resident", "copy"):
-        res["fma"][mode] = plain_per_rank(w, inputs, "fma", mode)
+    phases = [("split3", "resident"), ("split3", "copy"), ("fma", "resident"), ("fma", "copy")]
+    recs, init = plain_per_rank(w, inputs, phases, init="before")
+    res = {"split3": {"resident": recs[0], "copy": recs[1]}, "fma": {"resident": recs[2], "copy": recs[3]},
+           "t_init": init}
+    recs, _ = plain_per_rank(w, inputs, [("split3", "copy")], init="timed")
+    res["split3"]["copy_with_init"] = recs[0]
     ratios = {"shared_over_plain_resident": out["value"] / res["split3"]["resident"]["value"]}
     if out.get("e2e"):
         ratios["shared_e2e_over_plain_copy"] = out["e2e"]["value"] / res["split3"]["copy"]["value"]
-        ratios["shared_e2e_over_plain_copy_with_init"] = out["e2e"]["value"] / res["split3"]["copy_init"]["value"]
+        ratios["shared_e2e_over_plain_copy_with_init"] = (out["e2e"]["value"]
+                                                          / res["split3"]["copy_with_init"]["value"])
     if out.get("fma"):
         ratios["fma_shared_over_plain_resident"] = out["fma"]["value"] / res["fma"]["resident"]["value"]
     res["ratios"] = ratios
