@@ -82,6 +82,10 @@ def parse():
     p.add_argument("--paper-modes", action="store_true",
                    help="also run the workload in the paper's host-issued PS-1 / PS-2 modes")
     p.add_argument("--quantum", type=int, default=8)
+    p.add_argument("--tile-n", type=int, choices=[128, 192, 256], default=None,
+                   help="split3: fixed tile width (default: per task from the tuned cost table)")
+    p.add_argument("--l2-prefetch", type=int, choices=[0, 1], default=None,
+                   help="split3: prefetch the next queued tile's operands into L2 (default: the tuned choice)")
     p.add_argument("--harness", choices=["native", "python"], default="native",
                    help="rank threads: native (gvm_spmd_run) or Python threads calling the API")
     p.add_argument("--ranks", type=int, default=0, help="smaller case for profiling (not a bench line)")
@@ -481,6 +485,7 @@ def gpu_arm(args, w, desc, rank, world):
         R, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode=args.mode, sgemm_path=args.path,
         slice_bytes=slice_bytes, resident_bytes=resident, ingest_quantum=args.quantum,
         direct_output=None if args.direct_output is None else bool(args.direct_output),
+        l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch), sgemm_tile_n=args.tile_n,
     )
     direct_output_used = mgr.cfg.direct_output
     ranks = [mgr.attach(r) for r in range(R)]
@@ -783,6 +788,7 @@ def gpu_arm(args, w, desc, rank, world):
         "sgemm_path": args.path,
         "mode": args.mode,
         "direct_output": bool(direct_output_used),
+        "l2_prefetch": bool(mgr.cfg.l2_prefetch),
         "operands": "resident in HBM for value; pinned host buffers for e2e",
         "l2": "inputs larger than L2 (2 GiB of operands per step)" if args.workload == "sgemm512"
         else "inputs smaller than L2; latency-bound",
@@ -1676,7 +1682,9 @@ def grouped_arm(args):
         need[spec.rank] += al256(4 * spec.m * spec.n)
     resident = max(need)
     mgr = g.Manager(R, ring_depth=max(2, 1 << (P - 1).bit_length()), mode="barrier", sgemm_path=args.path,
-                    slice_bytes=resident + (4 << 20), resident_bytes=resident, ingest_quantum=args.quantum)
+                    slice_bytes=resident + (4 << 20), resident_bytes=resident, ingest_quantum=args.quantum,
+                    l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
+                    sgemm_tile_n=args.tile_n)
     ranks = [mgr.attach(r) for r in range(R)]
     gen = torch.Generator(device="cuda")
     for r in range(R):

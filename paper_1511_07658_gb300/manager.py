@@ -249,7 +249,7 @@ class Manager:
         *,
         ring_depth: int = 64,
         mode: str = "barrier",
-        sgemm_path: str = "split3",
+        sgemm_path: str | None = None,
         slice_bytes: int = 64 << 20,
         resident_bytes: int = 0,
         admission_cap_bytes: int = 0,
@@ -260,6 +260,8 @@ class Manager:
         copy_run_bytes: int | None = None,
         vadd_tile: int | None = None,
         direct_output: bool | None = None,
+        sgemm_tile_n: int | None = None,
+        l2_prefetch: bool | None = None,
         device: int | None = None,
     ):
         if not torch.cuda.is_available():
@@ -275,6 +277,8 @@ class Manager:
         cfg.max_ranks = ranks
         cfg.ring_depth = ring_depth
         cfg.mode = _MODES[mode]
+        if sgemm_path is None:  # the autotuner's form, else the fused split3 tiles
+            sgemm_path = tuning().get("sgemm_form", "split3")
         cfg.sgemm_path = _PATHS[sgemm_path]
         ctrl_bytes = L.gvm_ctrl_bytes(byref(cfg))
         if ctrl_bytes == 0:
@@ -302,6 +306,13 @@ class Manager:
         cfg.copy_run_bytes = int(tuned.get("copy_run_bytes", 0) if copy_run_bytes is None else copy_run_bytes)
         cfg.vadd_tile = int(tuned.get("vadd_tile", 0) if vadd_tile is None else vadd_tile)
         cfg.direct_output = int(bool(tuned.get("direct_output", 0) if direct_output is None else direct_output))
+        cfg.l2_prefetch = int(bool(tuned.get("l2_prefetch", 0) if l2_prefetch is None else l2_prefetch))
+        # split3 tile width: fixed, or per task from the autotuner's cost table
+        cfg.sgemm_tile_n = int(sgemm_tile_n or 0)
+        cost = tuned.get("sgemm_tile_cost") if sgemm_tile_n is None else None
+        if cost:
+            for i, w in enumerate((128, 192, 256)):
+                cfg.sgemm_tile_cost[i] = float(cost.get(str(w), 0.0))
         self.cfg = cfg
         h = c_void_p()
         with torch.cuda.device(self.device):
