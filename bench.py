@@ -32,6 +32,7 @@ import argparse
 import ctypes
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -64,6 +65,9 @@ def parse():
     p.add_argument("--impl", choices=["gvm", "reference"], default="gvm")
     p.add_argument("--workload", choices=["sgemm512", "vadd_tiny", "serving", "grouped", "stress"], default="sgemm512")
     p.add_argument("--serving-tasks", type=int, default=0, help="serving workload: total tasks (default 4096)")
+    p.add_argument("--repeats", type=int, default=3, help="serving and stress: runs per load point")
+    p.add_argument("--duration", type=float, default=10.0,
+                   help="stress: seconds of arrivals per load point (the configuration's is 60)")
     p.add_argument("--path", choices=["split3", "split3_wide", "fma"], default="split3")
     p.add_argument("--mode", choices=["barrier", "continuous"], default="barrier")
     p.add_argument("--skip-e2e", action="store_true")
@@ -82,8 +86,6 @@ def parse():
     p.add_argument("--paper-modes", action="store_true",
                    help="also run the workload in the paper's host-issued PS-1 / PS-2 modes")
     p.add_argument("--quantum", type=int, default=8)
-    p.add_argument("--tile-n", type=int, choices=[128, 192, 256], default=None,
-                   help="split3: fixed tile width (default: per task from the tuned cost table)")
     p.add_argument("--l2-prefetch", type=int, choices=[0, 1], default=None,
                    help="split3: prefetch the next queued tile's operands into L2 (default: the tuned choice)")
     p.add_argument("--harness", choices=["native", "python"], default="native",
@@ -485,7 +487,7 @@ def gpu_arm(args, w, desc, rank, world):
         R, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode=args.mode, sgemm_path=args.path,
         slice_bytes=slice_bytes, resident_bytes=resident, ingest_quantum=args.quantum,
         direct_output=None if args.direct_output is None else bool(args.direct_output),
-        l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch), sgemm_tile_n=args.tile_n,
+        l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
     )
     direct_output_used = mgr.cfg.direct_output
     ranks = [mgr.attach(r) for r in range(R)]
@@ -1211,6 +1213,42 @@ def _open_loop(mgr, w, depth, vin, gin, outs):
     return span, sorted(x for l in lat for x in l), moved
 
 
+def _lat_summary(runs):
+    """Per-run latency percentiles (us) and their spread over repeated runs."""
+    out = {}
+    for q, name in ((50, "p50"), (99, "p99"), (99.9, "p999")):
+        vals = [1e6 * percentile(lat, q) for lat in runs]
+        out[name] = {"median": statistics.median(vals), "min": min(vals), "max": max(vals)}
+    out["kind"] = "scheduled arrival -> completion seen by the rank; median, min and max over repeated runs"
+    return out
+
+
+def _load_points(run_w, make_w, capacity, fracs, repeats, extra=None):
+    """Runs the workload make_w(frac) `repeats` times at each offered load
+    (fraction of capacity), plus the named extra workloads; returns one
+    record per point: offered and served tasks/s, latency spread."""
+    points = {}
+    todo = [(f"at_{f}_capacity", f, make_w(f)) for f in fracs] + list(extra or [])
+    for name, frac, w1 in todo:
+        spans, lats, moved = [], [], 0
+        for _ in range(repeats):
+            span1, lat1, moved, st1 = run_w(w1)
+            if st1["device_status"]:
+                raise RuntimeError(f"device status {st1['device_status']} at {name}")
+            spans.append(span1)
+            lats.append(lat1)
+        last_arrival = max(t.arrival_s for t in w1.tasks)
+        points[name] = {
+            "offered_tasks_per_s": len(w1.tasks) / last_arrival if last_arrival > 0 else None,
+            "offered_fraction_of_capacity": frac,
+            "served_tasks_per_s": [len(w1.tasks) / x for x in spans],
+            "tasks": len(w1.tasks), "last_arrival_s": last_arrival, "repeats": repeats,
+            "latency_us": _lat_summary(lats),
+            "host_link_gbs": moved / statistics.median(spans) / 1e9,
+        }
+    return points
+
+
 def serving_arm(args):
     """Open-loop serving: 16 ranks, 4096 tasks, Poisson arrivals with a mean
     gap of 20 us per rank, half vector adds (n = floor(2^(16+8u))) and half
@@ -1220,18 +1258,23 @@ def serving_arm(args):
 
     Ranks run as native threads (gvm_open_loop_run). Latency of a task = the
     moment its rank observes completion minus its scheduled arrival time (so
-    a rank that falls behind does not hide queueing delay). Operands: per size, one seeded input set shared by every task of
-    that size (the latency and throughput do not depend on values; parity of
-    the mix is covered by the GPU tests); outputs go to per-rank pinned
-    buffers, one per in-flight slot.
+    a rank that falls behind does not hide queueing delay). First the
+    capacity (every task arrives at once; tasks/s over the run), then the same
+    tasks paced at 0.5 and 0.8 x capacity and at the configured 20 us gap
+    (an overload), each point run `--repeats` times for the spread. Operands:
+    per size, one seeded input set shared by every task of that size (the
+    latency and throughput do not depend on values; parity of the mix is
+    covered by the GPU tests); outputs go to per-rank pinned buffers, one per
+    in-flight slot.
     """
     import torch
 
     import paper_1511_07658_gb300 as g
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    w = synth.serving_mix(ranks=16, total=args.serving_tasks or 4096)
-    R = w.ranks
+    total = args.serving_tasks or 4096
+    R = 16
+    w = synth.serving_mix(ranks=R, total=total)
     depth = 8
     vmax = max(t.n for t in w.tasks if t.kind == synth.TASK_VADD)
     a, b = synth.vadd_inputs(4242, vmax)
@@ -1245,16 +1288,33 @@ def serving_arm(args):
     outs = [[torch.empty(out_elems).pin_memory() for _ in range(depth)] for _ in range(R)]
     smax = max(sd for sd in sides)
     per_task = max(12 * vmax, 12 * smax * smax + g.sgemm_scratch_bytes(smax, smax, smax, args.path)) + (1 << 20)
-    mgr = g.Manager(R, ring_depth=depth, mode="continuous", sgemm_path=args.path,
-                    slice_bytes=per_task * 2 + (64 << 20), admission_cap_bytes=32 << 30,
-                    ingest_quantum=args.quantum)
-    span, all_lat, moved = _open_loop(mgr, w, depth, (va, vb), lambda sd: gin[sd], outs)
-    st = mgr.stats()
-    mgr.shutdown()
-    total = len(w.tasks)
+
+    def run_w(w1):
+        mgr = g.Manager(R, ring_depth=depth, mode="continuous", sgemm_path=args.path,
+                        slice_bytes=per_task * 2 + (64 << 20), admission_cap_bytes=32 << 30,
+                        ingest_quantum=args.quantum)
+        try:
+            span, lat, moved = _open_loop(mgr, w1, depth, (va, vb), lambda sd: gin[sd], outs)
+            st = mgr.stats()
+        finally:
+            mgr.shutdown()
+        return span, lat, moved, st
+
+    w_cap = synth.serving_mix(ranks=R, total=total, gap_us=1e-6)
+    cap_runs = [run_w(w_cap) for _ in range(args.repeats)]
+    capacity = statistics.median(total / x[0] for x in cap_runs)
+    moved = cap_runs[0][2]
+
+    def make_w(frac):  # mean gap per rank for an offered total rate of frac x capacity
+        return synth.serving_mix(ranks=R, total=total, gap_us=1e6 * R / (frac * capacity))
+
+    points = _load_points(run_w, make_w, capacity, (0.5, 0.8), args.repeats,
+                          extra=[("configured_20us_gap", None, w)])
+    cfgd = points["configured_20us_gap"]
+    cfgd["offered_fraction_of_capacity"] = cfgd["offered_tasks_per_s"] / capacity
     return {
         "metric": METRIC + " (serving loop)",
-        "value": total / span,
+        "value": capacity,
         "unit": "tasks/s",
         "n_gpus": 1,
         "higher_is_better": True,
@@ -1262,12 +1322,12 @@ def serving_arm(args):
         "data": "synthetic",
         "config": {"workload": f"serving mix: 16 ranks, {total} tasks, Poisson 20 us mean gap per rank, "
                    "50/50 vector add n~2^(16+8u) / square SGEMM {256,512,1024,2048}, cap 32 GiB",
-                   "mode": "continuous", "sgemm_path": args.path, "ring_depth": depth},
-        "latency_us": {"p50": 1e6 * percentile(all_lat, 50), "p99": 1e6 * percentile(all_lat, 99),
-                       "p999": 1e6 * percentile(all_lat, 99.9), "kind": "scheduled arrival -> completion seen by the rank"},
-        "host_link_gbs": moved / span / 1e9,
-        "staged_peak_bytes": st["staged_peak"],
-        "device_status": st["device_status"],
+                   "mode": "continuous", "sgemm_path": args.path, "ring_depth": depth,
+                   "repeats": args.repeats},
+        "capacity": {"tasks_per_s": capacity, "runs_tasks_per_s": [total / x[0] for x in cap_runs],
+                     "host_link_gbs": moved / statistics.median(x[0] for x in cap_runs) / 1e9,
+                     "kind": "every task arrives at once; tasks over the time to the last completion"},
+        **points,
     }
 
 
@@ -1275,27 +1335,33 @@ def stress_arm(args):
     """Open-loop stress (the lognormal mix): 128 ranks, 70% vector add with n
     = round(2^20 e^(1.5 Z)) and 30% square SGEMM with side round(768
     e^(0.7 Z)) in [64, 4096], Poisson arrivals, admission capped at 120 GiB,
-    continuous mode. Vector lengths are clamped to [2^10, 2^24] here: at 128
-    ranks a rank's staging slice holds about half a gigabyte, and a 2^28
-    vector add stages 3 GiB. First the capacity: every task arrives at once
-    (tasks/s over the whole run). Then the same task list at 0.5, 0.8 and
-    0.95 x that capacity (Poisson gaps), each with p50/p99/p999 latency. Operands come from one
-    seeded page-locked buffer per kind (a task reads a prefix of it as a dense
-    operand); outputs share a pool of page-locked buffers, one per rank slot
-    group (values are not checked here; the mix's parity is covered by the
-    GPU tests)."""
+    continuous mode. Vector lengths are clamped to [2^10, 2^24] here: the
+    manager gives every rank an equal slice of the device arena, and a 2^28
+    vector add stages 3 GiB, so 128 ranks holding one each would need 384
+    GiB of HBM. First the capacity: 48 tasks a rank, every task arriving at
+    once (tasks/s over the whole run). Then, at 0.5, 0.8 and 0.95 x that
+    capacity, Poisson arrivals for `--duration` seconds (the task count per
+    rank follows from the rate), each point run `--repeats` times, with
+    p50/p99/p999 latency. Operands come from one seeded page-locked buffer per
+    kind (a task reads a prefix of it as a dense operand); outputs share a
+    pool of page-locked buffers, one per rank slot group (values are not
+    checked here; the mix's parity is covered by the GPU tests)."""
     import torch
 
     import paper_1511_07658_gb300 as g
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     R, P, depth = 128, args.per_rank or 48, 2
-    w0 = synth.stress_mix(ranks=R, per_rank=P, rate_per_rank_hz=1e9)
-    for t in w0.tasks:  # the clamp of this leg
-        if t.kind == synth.TASK_VADD:
-            t.n = min(t.n, 1 << 24)
-    vmax = max(t.n for t in w0.tasks if t.kind == synth.TASK_VADD)
-    smax = max(t.m for t in w0.tasks if t.kind == synth.TASK_SGEMM)
+
+    def clamp(w):  # the clamp of this leg
+        for t in w.tasks:
+            if t.kind == synth.TASK_VADD:
+                t.n = min(t.n, 1 << 24)
+        return w
+
+    w0 = clamp(synth.stress_mix(ranks=R, per_rank=P, rate_per_rank_hz=1e9))
+    vmax = 1 << 24
+    smax = 4096
     a, b = synth.vadd_inputs(5151, vmax)
     vin = (torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory())
     A, B = synth.sgemm_inputs(6161, smax, smax, smax)
@@ -1305,7 +1371,7 @@ def stress_arm(args):
     outs = [[pool[(r * depth + s) % len(pool)] for s in range(depth)] for r in range(R)]
     per_task = max(12 * vmax, 12 * smax * smax) + (1 << 20)
 
-    def run(w):
+    def run_w(w):
         mgr = g.Manager(R, ring_depth=depth, mode="continuous", sgemm_path=args.path,
                         slice_bytes=per_task * depth + (16 << 20), admission_cap_bytes=120 << 30,
                         ingest_quantum=args.quantum)
@@ -1316,22 +1382,15 @@ def stress_arm(args):
             mgr.shutdown()
         return span, lat, moved, st
 
-    span0, _, moved0, _ = run(w0)
+    span0, _, moved0, _ = run_w(w0)
     capacity = len(w0.tasks) / span0
-    points = {}
-    for frac in (0.5, 0.8, 0.95):
-        w1 = synth.stress_mix(ranks=R, per_rank=P, rate_per_rank_hz=frac * capacity / R)
-        for t0, t1 in zip(w0.tasks, w1.tasks):
-            t1.n, t1.m, t1.k = t0.n, t0.m, t0.k  # the same tasks, paced arrivals
-        span1, lat1, moved1, st1 = run(w1)
-        points[f"at_{frac}_capacity"] = {
-            "offered_tasks_per_s": frac * capacity, "served_tasks_per_s": len(w1.tasks) / span1,
-            "last_arrival_s": max(t.arrival_s for t in w1.tasks), "span_s": span1,
-            "latency_us": {"p50": 1e6 * percentile(lat1, 50), "p99": 1e6 * percentile(lat1, 99),
-                           "p999": 1e6 * percentile(lat1, 99.9),
-                           "kind": "scheduled arrival -> completion seen by the rank"},
-            "host_link_gbs": moved1 / span1 / 1e9, "staged_peak_bytes": st1["staged_peak"],
-            "device_status": st1["device_status"]}
+
+    def make_w(frac):
+        rate = frac * capacity / R
+        per = max(1, int(math.ceil(rate * args.duration)))
+        return clamp(synth.stress_mix(ranks=R, per_rank=per, rate_per_rank_hz=rate))
+
+    points = _load_points(run_w, make_w, capacity, (0.5, 0.8, 0.95), args.repeats)
     return {
         "metric": METRIC + " (stress loop)",
         "value": capacity,
@@ -1340,10 +1399,12 @@ def stress_arm(args):
         "higher_is_better": True,
         "dtype": "bf16x3->f32" if args.path != "fma" else "f32",
         "data": "synthetic",
-        "config": {"workload": f"stress mix: {R} ranks x {P} tasks, 70% vector add n = 2^20 e^(1.5Z) in "
+        "config": {"workload": f"stress mix: {R} ranks, 70% vector add n = 2^20 e^(1.5Z) in "
                    "[2^10, 2^24], 30% square SGEMM side 768 e^(0.7Z) in [64, 4096], cap 120 GiB",
-                   "mode": "continuous", "sgemm_path": args.path, "ring_depth": depth},
-        "capacity": {"tasks_per_s": capacity, "host_link_gbs": moved0 / span0 / 1e9, "seconds": span0},
+                   "mode": "continuous", "sgemm_path": args.path, "ring_depth": depth,
+                   "arrivals_s_per_point": args.duration, "repeats": args.repeats},
+        "capacity": {"tasks_per_s": capacity, "host_link_gbs": moved0 / span0 / 1e9, "seconds": span0,
+                     "tasks": len(w0.tasks)},
         **points,
     }
 
@@ -1683,8 +1744,7 @@ def grouped_arm(args):
     resident = max(need)
     mgr = g.Manager(R, ring_depth=max(2, 1 << (P - 1).bit_length()), mode="barrier", sgemm_path=args.path,
                     slice_bytes=resident + (4 << 20), resident_bytes=resident, ingest_quantum=args.quantum,
-                    l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
-                    sgemm_tile_n=args.tile_n)
+                    l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch))
     ranks = [mgr.attach(r) for r in range(R)]
     gen = torch.Generator(device="cuda")
     for r in range(R):

@@ -146,16 +146,6 @@ typedef struct gvm_config {
                                device mapping (page-locked memory the GPU can address;
                                a buffer without one uses the staged path), so outputs
                                take no staging and no copy */
-  int32_t sgemm_tile_n;     /* GVM_SGEMM_SPLIT3: columns of C per tile, 128, 192 or 256
-                               for every task; 0 = chosen per task from
-                               sgemm_tile_cost (a function of the task's n only) */
-  float sgemm_tile_cost[3]; /* GVM_SGEMM_SPLIT3 with sgemm_tile_n = 0: relative time of
-                               one tile 128, 192 and 256 columns wide at equal m and k
-                               (measured by the project's autotuner). A task of n
-                               columns gets the width w minimising ceil(n / w) * cost(w),
-                               the wider on ties. All zero: 256. Not a split of the
-                               sum: each element of C is computed the same way at any
-                               width */
   int32_t l2_prefetch;      /* GVM_SGEMM_SPLIT3: 1 = when a CTA starts a GEMM tile, it
                                asks L2 for the operands of the next tile it has queued
                                (bulk prefetch; a hint, no result depends on it); 0 = off */

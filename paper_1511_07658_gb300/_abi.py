@@ -56,8 +56,6 @@ class GvmConfig(ctypes.Structure):
         ("copy_run_bytes", c_uint64),
         ("vadd_tile", c_int64),
         ("direct_output", c_int32),
-        ("sgemm_tile_n", c_int32),
-        ("sgemm_tile_cost", ctypes.c_float * 3),
         ("l2_prefetch", c_int32),
     ]
 

@@ -11,16 +11,15 @@ and keeps the fastest:
   one pinned block (8 steps);
 * ``vadd_tile`` (elements per vector-add tile; 0 = per task, n / CTAs): 16
   ranks x 8 resident vector adds of n = 2^22 (10 steps);
-* ``sgemm_tile_cost`` (the split3 SGEMM tile shape): the time of one tile
-  128 x w for each width w in 128, 192, 256, from resident SGEMMs whose n
-  (768) every width divides, so no tile is padded: 16 ranks x 16 tasks of
-  512 x 768 x 512 at each fixed width (8 steps). The manager then gives a
-  task of n columns the width minimising ceil(n / w) * cost(w), a pure
-  function of the shape (a task's result is the same alone and in any mix);
-* ``sgemm_form``: the same workload and the 16 x 64 SGEMM 512^3 step with
-  the wide form (256 x 256 tiles of one CTA) against the fused 128-row form,
-  recorded for the table; the manager's default path stays the fused form
-  unless the wide one wins both.
+* ``sgemm_form`` (the split3 SGEMM tile shape): fused 128 x 256 tiles
+  against wide 256 x 256 tiles of one CTA, on square 512^3 (16 x 64 tasks),
+  on 512 x 768 x 512 (16 x 16) and on 2048^3 (16 x 1), resident; the wide
+  form becomes the manager's default only if it wins every one. A tile
+  shape per task inside one launch would need both forms in one kernel,
+  whose converters then spill (measured); so the shape is chosen per
+  manager, and a task's result is the same alone and in any mix;
+* ``l2_prefetch`` (split3: the next queued tile's operands prefetched into
+  L2): on against off on the same three workloads, kept if it wins all.
 
 The table it writes (``tuning.json`` beside this file: the choice, the device
 and every timing) is what ``Manager`` uses when the caller passes neither
@@ -102,17 +101,14 @@ def time_vadd_tile(tile: int, ranks: int = 16, per_rank: int = 8, n: int = 1 << 
         mgr.shutdown()
 
 
-TILE_WIDTHS = (128, 192, 256)
-
-
 def time_sgemm(m: int, n: int, k: int, ranks: int = 16, per_rank: int = 16, steps: int = 8,
-               path: str = "split3", tile_n: int | None = None) -> float:
+               path: str = "split3", prefetch: bool = False) -> float:
     """Median step time (s) of resident SGEMMs, every task m x n x k."""
     la, lb, lc = 4 * m * k, 4 * k * n, 4 * m * n
     per_task = _al(la) + _al(lb) + _al(lc)
     mgr = Manager(ranks, ring_depth=per_rank, mode="barrier", sgemm_path=path,
                   slice_bytes=per_task * per_rank + (4 << 20), resident_bytes=per_task * per_rank,
-                  sgemm_tile_n=tile_n)
+                  l2_prefetch=prefetch)
     try:
         rk = [mgr.attach(r) for r in range(ranks)]
         gen = torch.Generator(device="cuda")
@@ -136,53 +132,45 @@ def time_sgemm(m: int, n: int, k: int, ranks: int = 16, per_rank: int = 16, step
         mgr.shutdown()
 
 
-def tile_costs(step_s: dict, m: int = 512, n: int = 768, tasks: int = 256) -> dict:
-    """Time of one tile per width, relative to the 256-wide tile, from the
-    step times of the unpadded workload (tasks x (m / 128) x (n / w) tiles)."""
-    per_tile = {w: step_s[str(w)] / (tasks * (m // 128) * (n // w)) for w in TILE_WIDTHS}
-    return {str(w): per_tile[w] / per_tile[256] for w in TILE_WIDTHS}
+SGEMM_SHAPES = ((512, 512, 512, 64), (512, 768, 512, 16), (2048, 2048, 2048, 1))  # m, n, k, tasks a rank
 
 
-def choose_width(n: int, cost: dict) -> int:
-    """The manager's rule: the width minimising ceil(n / w) * cost(w), the
-    wider on ties (the same rule as the library's sgemm_tile_width)."""
-    best, best_t = 256, None
-    for w in sorted(TILE_WIDTHS, reverse=True):
-        t = -(-n // w) * cost[str(w)]
-        if best_t is None or t < best_t:
-            best, best_t = w, t
-    return best
+def _shape_key(m, n, k):
+    return f"{m}x{n}x{k}"
+
+
+def choose_sgemm(form_t: dict, pf_t: dict) -> dict:
+    """The wide form and the prefetch are kept only where they win every
+    workload timed (step times in seconds, keyed by shape)."""
+    wide = all(t["split3_wide"] < t["split3"] for t in form_t.values())
+    pf = all(t["1"] < t["0"] for t in pf_t.values())
+    return {"sgemm_form": "split3_wide" if wide else "split3", "l2_prefetch": int(pf)}
 
 
 def run(path: str = _m.TUNING_FILE) -> dict:
     torch.cuda.set_device(0)
     copy_t = {str(c): time_copy_run(c) for c in COPY_RUNS}
     vadd_t = {str(v): time_vadd_tile(v) for v in VADD_TILES}
-    tile_t = {str(w): time_sgemm(512, 768, 512, tile_n=w) for w in TILE_WIDTHS}
-    form_t = {
-        "split3 512x768x512": tile_t["256"],
-        "split3_wide 512x768x512": time_sgemm(512, 768, 512, path="split3_wide"),
-        "split3 512^3": time_sgemm(512, 512, 512, per_rank=64),
-        "split3_wide 512^3": time_sgemm(512, 512, 512, per_rank=64, path="split3_wide"),
-    }
-    wide_wins = (form_t["split3_wide 512x768x512"] < form_t["split3 512x768x512"]
-                 and form_t["split3_wide 512^3"] < form_t["split3 512^3"])
+    form_t, pf_t = {}, {}
+    for m, n, k, per in SGEMM_SHAPES:
+        key = _shape_key(m, n, k)
+        form_t[key] = {f: time_sgemm(m, n, k, per_rank=per, path=f) for f in ("split3", "split3_wide")}
+        pf_t[key] = {str(int(on)): time_sgemm(m, n, k, per_rank=per, prefetch=on) for on in (False, True)}
     choice = {
         "copy_run_bytes": int(min(copy_t, key=copy_t.get)),
         "vadd_tile": int(min(vadd_t, key=vadd_t.get)),
-        "sgemm_tile_cost": tile_costs(tile_t),
-        "sgemm_form": "split3_wide" if wide_wins else "split3",
+        **choose_sgemm(form_t, pf_t),
     }
     out = {
         "device": torch.cuda.get_device_name(0),
         "choice": choice,
-        "step_s": {"copy_run_bytes": copy_t, "vadd_tile": vadd_t, "sgemm_tile_n": tile_t, "sgemm_form": form_t},
+        "step_s": {"copy_run_bytes": copy_t, "vadd_tile": vadd_t, "sgemm_form": form_t, "l2_prefetch": pf_t},
         "workloads": {
             "copy_run_bytes": "end-to-end leg, 16 ranks x 16 SGEMM 512^3, operands in one pinned block per rank",
             "vadd_tile": "16 ranks x 8 resident vector adds, n = 2^22",
-            "sgemm_tile_n": "16 ranks x 16 resident SGEMM 512 x 768 x 512 at each fixed tile width",
-            "sgemm_form": "fused 128-row tiles against wide 256 x 256 tiles: 16 x 16 SGEMM 512 x 768 x 512 and "
-                          "16 x 64 SGEMM 512^3, resident",
+            "sgemm_form": "resident SGEMM, 16 ranks x (64 of 512^3, 16 of 512 x 768 x 512, 1 of 2048^3): "
+                          "fused 128 x 256 tiles against wide 256 x 256 tiles",
+            "l2_prefetch": "the same SGEMM workloads, fused tiles, next-tile L2 prefetch off (0) and on (1)",
         },
     }
     with open(path, "w") as f:

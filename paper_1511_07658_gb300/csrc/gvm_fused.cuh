@@ -52,9 +52,7 @@ struct FzShared {
   uint32_t pad;
 };
 
-// One GEMM tile as the converters and the MMA warp see it. bn is the tile's
-// width (128, 192 or 256 columns of C; the task's tile shape): tile (tm, tn)
-// covers rows 128 tm .. and columns bn tn .. of C.
+// One GEMM tile as the converters and the MMA warp see it.
 struct FzTile {
   const float* A;
   const float* B;
@@ -64,16 +62,7 @@ struct FzTile {
   int k;
   int tm;
   int tn;
-  int bn = kTcN;
 };
-
-// Which 32-column block of B a converter item stages: warp w of a group, item
-// j. For bn = 128 each warp takes one block (the even items); otherwise warp
-// w takes blocks 2w and 2w + 1 and blocks beyond bn / 32 are skipped.
-__device__ __forceinline__ int fz_bblk(int bn, int w, int j) { return bn == 128 ? w : 2 * w + (j & 1); }
-__device__ __forceinline__ bool fz_bitem(int bn, int w, int j) {
-  return bn == 128 ? (j & 1) == 0 : 2 * w + (j & 1) < bn / 32;
-}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -177,8 +166,7 @@ __device__ __forceinline__ void ld_cg_v8(const float* p, float (&v)[8]) {
 // Thread (w, lane) of a group (w = warp index in the group, 0..3) stages k-step kb:
 //   A item j (j = 0..3): row 8 w + (lane >> 2) + 32 j, 8 values from k = 32 kb + 8 (lane & 3);
 //   B item j (j = 0..7): k = 32 kb + 8 (j >> 1) + (lane >> 2), 8 values from
-//                        column 32 fz_bblk(bn, w, j) + 8 (lane & 3) of the
-//                        tile (items fz_bitem rejects are skipped).
+//                        column 32 (2 w + (j & 1)) + 8 (lane & 3).
 // Every load instruction of a warp reads 8 rows x 128 contiguous bytes and
 // every store fills one 512-byte swizzle atom (no bank conflicts).
 // Out-of-range elements are 0 (ragged m, n, k).
@@ -202,7 +190,7 @@ __device__ __forceinline__ void fz_load_a(const FzTile& t, int kb, int w, int la
 __device__ __forceinline__ void fz_load_b(const FzTile& t, int kb, int w, int lane, int j, int bvec,
                                           float (&v)[8]) {
   const int kk = kb * kTcBK + 8 * (j >> 1) + (lane >> 2);
-  const int64_t c = (int64_t)t.tn * t.bn + 32 * fz_bblk(t.bn, w, j) + 8 * (lane & 3);
+  const int64_t c = (int64_t)t.tn * kTcN + 32 * (2 * w + (j & 1)) + 8 * (lane & 3);
   const float* src = t.B + (int64_t)kk * t.n + c;
   if (kk < t.k && bvec == 2 && c + 8 <= t.n) {
     ld_cg_v8(src, v);
@@ -242,16 +230,14 @@ __device__ __forceinline__ bool fz_convert_loop(const FzTile& t, uint32_t base, 
   // First k-step of this tile with the group's parity.
   const int kb0 = (int)((it + (uint32_t)par) & 1u);
   if (kb0 >= nkb) return true;
-  const int bn = t.bn;
   const float* pa = t.A + (int64_t)(t.tm * kTcM + 8 * w + (lane >> 2)) * t.k + 8 * (lane & 3);
-  const float* pb = t.B + (int64_t)(lane >> 2) * t.n + (int64_t)t.tn * bn + 32 * fz_bblk(bn, w, 0) + 8 * (lane & 3);
+  const float* pb = t.B + (int64_t)(lane >> 2) * t.n + (int64_t)t.tn * kTcN + 64 * w + 8 * (lane & 3);
   const int64_t a_row32 = 32 * (int64_t)t.k, b_row8 = 8 * t.n, b_step = (int64_t)kTcBK * t.n;
   auto load_a = [&](int kb, int j, float (&v)[8]) {
     if (kFast) ld_cg_v8(pa + kb * kTcBK + j * a_row32, v);
     else fz_load_a(t, kb, w, lane, j, avec, v);
   };
   auto load_b = [&](int kb, int j, float (&v)[8]) {
-    if (!fz_bitem(bn, w, j)) return;
     if (kFast) ld_cg_v8(pb + kb * b_step + (j >> 1) * b_row8 + 32 * (j & 1), v);
     else fz_load_b(t, kb, w, lane, j, bvec, v);
   };
@@ -289,8 +275,7 @@ __device__ __forceinline__ bool fz_convert_loop(const FzTile& t, uint32_t base, 
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      if (!fz_bitem(bn, w, j)) continue;
-      const uint32_t off = (uint32_t)(j >> 1) * kFzBAtomK + (uint32_t)fz_bblk(bn, w, j) * kFzBAtomN + b_off;
+      const uint32_t off = (uint32_t)(j >> 1) * kFzBAtomK + (uint32_t)(2 * w + (j & 1)) * kFzBAtomN + b_off;
       uint4 hi, lo;
       split8_x2(vb[j], hi, lo);
       st_shared_v4(st + kTcBOff + off, hi);
@@ -324,7 +309,7 @@ __device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzS
                    : ((t.n & 3) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 15) == 0) ? 1
                                                                                       : 0;
   const bool fast = avec == 2 && bvec == 2 && (t.k % kTcBK) == 0 && (t.tm + 1) * kTcM <= t.m &&
-                    (int64_t)(t.tn + 1) * t.bn <= t.n;
+                    (int64_t)(t.tn + 1) * kTcN <= t.n;
   const uint32_t base = smem_u32(stages);
   return fast ? fz_convert_loop<true, kLate>(t, base, fs, it, avec, bvec, timeout_ns, cta_abort, fail_where,
                                              wait_acc)
@@ -347,8 +332,8 @@ __device__ __forceinline__ void fz_prefetch_tile(const FzTile& t) {
   const int lane = threadIdx.x & 31;
   const int r0 = t.tm * kTcM;
   const int rows = min(kTcM, t.m - r0);
-  const int64_t c0 = (int64_t)t.tn * t.bn;
-  const int64_t cols = min((int64_t)t.bn, t.n - c0);
+  const int64_t c0 = (int64_t)t.tn * kTcN;
+  const int64_t cols = min((int64_t)kTcN, t.n - c0);
   if (rows <= 0 || cols <= 0 || (t.k & 3) || (t.n & 3)) return;
   if ((reinterpret_cast<uintptr_t>(t.A) | reinterpret_cast<uintptr_t>(t.B)) & 15) return;
   if (lane == 0) prefetch_l2(t.A + (int64_t)r0 * t.k, (uint32_t)(rows * t.k * 4));
@@ -363,8 +348,8 @@ __device__ __forceinline__ void st_v8(float* p, const uint32_t* r) {
 }
 
 // Converter warps: drain accumulator (tile_no & 1) of tile t into C. Warp w
-// reads TMEM lanes 32 (w & 3) .. +31 (rows of the tile) and the (w >> 2)-th
-// half of the tile's bn columns, 32 columns at a time; TMEM hands each thread one
+// reads TMEM lanes 32 (w & 3) .. +31 (rows of the tile) and columns
+// 128 (w >> 2) .. +127, 32 columns at a time; TMEM hands each thread one
 // row, which it stores as whole 32-byte sectors (16-byte or single stores
 // when n does not allow). No shared memory: the operand loads keep all of L1
 // for their requests in flight. Then frees the accumulator.
@@ -384,14 +369,13 @@ __device__ __forceinline__ bool fz_epilogue(const FzTile& t, FzShared* fs, uint3
   const int row = t.tm * kTcM + q * 32 + lane;
   const uintptr_t ca = reinterpret_cast<uintptr_t>(t.C);
   const int vec = ((t.n & 7) == 0 && (ca & 31) == 0) ? 2 : ((t.n & 3) == 0 && (ca & 15) == 0) ? 1 : 0;
-  const int half = t.bn / 64;  // 32-column chunks per warp
 #pragma unroll 1
-  for (int ch = 0; ch < half; ++ch) {
-    const int chunk = cq * half + ch;
+  for (int ch = 0; ch < 4; ++ch) {
+    const int chunk = cq * 4 + ch;
     uint32_t r[32];
     tmem_ld_32x32b_x32(fs->tmem_base + b * kTcN + ((uint32_t)(q * 32) << 16) + (uint32_t)(chunk * 32), r);
     tmem_ld_wait();
-    const int64_t c0 = (int64_t)t.tn * t.bn + chunk * 32;
+    const int64_t c0 = (int64_t)t.tn * kTcN + chunk * 32;
     if (row < t.m && c0 < t.n) {
       float* dst = t.C + (int64_t)row * t.n + c0;
       if (vec == 2 && c0 + 32 <= t.n) {
@@ -431,7 +415,6 @@ __device__ __forceinline__ bool fz_mma(const FzTile& t, uint8_t* stages, FzShare
   tc_fence_after();
   const uint32_t tmem = fs->tmem_base + b * kTcN;
   const int nkb = (t.k + kTcBK - 1) / kTcBK;
-  const uint32_t idesc = idesc_bf16_f32(kTcM, t.bn) | (1u << 16);  // B MN-major
   for (int kb = 0; kb < nkb; ++kb) {
     const uint32_t q = it + (uint32_t)kb, s = q % kTcStages, ph = (q / kTcStages) & 1u;
     const uint64_t t0 = wait_acc ? globaltimer() : 0;
@@ -449,9 +432,9 @@ __device__ __forceinline__ bool fz_mma(const FzTile& t, uint8_t* stages, FzShare
     for (int kk = 0; kk < kTcBK / 16; ++kk) {
       const uint64_t adv_a = (uint64_t)(kk * 32) >> 4;             // 16 bf16 = 32 bytes along a K-major row
       const uint64_t adv_b = (uint64_t)(kk * 2 * kFzBAtomK) >> 4;  // two 8-row k groups of B
-      umma_bf16(tmem, dAl + adv_a, dBh + adv_b, idesc, (kb | kk) ? 1u : 0u);
-      umma_bf16(tmem, dAh + adv_a, dBl + adv_b, idesc, 1u);
-      umma_bf16(tmem, dAh + adv_a, dBh + adv_b, idesc, 1u);
+      umma_bf16(tmem, dAl + adv_a, dBh + adv_b, kFzIdesc, (kb | kk) ? 1u : 0u);
+      umma_bf16(tmem, dAh + adv_a, dBl + adv_b, kFzIdesc, 1u);
+      umma_bf16(tmem, dAh + adv_a, dBh + adv_b, kFzIdesc, 1u);
     }
     umma_commit(&fs->empty[s]);
   }

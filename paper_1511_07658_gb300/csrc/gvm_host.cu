@@ -498,9 +498,6 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   if (cfg.vadd_tile < 0) return GVM_EINVAL;
   if (cfg.direct_output < 0 || cfg.direct_output > 1 || cfg.l2_prefetch < 0 || cfg.l2_prefetch > 1)
     return GVM_EINVAL;
-  if (cfg.sgemm_tile_n != 0 && !fz_valid_bn(cfg.sgemm_tile_n)) return GVM_EINVAL;
-  for (float c : cfg.sgemm_tile_cost)
-    if (!(c >= 0.f && c < 1e30f)) return GVM_EINVAL;
   if (cfg.vadd_tile > 0) cfg.vadd_tile = std::max<int64_t>(1024, cfg.vadd_tile / 1024 * 1024);
   if (cfg.ingest_quantum <= 0) cfg.ingest_quantum = 4;
   if (cfg.copy_streams)
@@ -722,25 +719,6 @@ uint64_t stage_room(const gvm_rank* r, uint64_t bytes) {
   return waste + bytes;
 }
 
-// Tile width of a split3 task with n columns (fused form): the configured
-// width, or the one the autotuner's cost table makes cheapest for n.
-int sgemm_tile_width(const gvm_config& cfg, int64_t n) {
-  if (cfg.sgemm_tile_n) return cfg.sgemm_tile_n;
-  static const int kW[3] = {128, 192, 256};
-  int best = kTcN;
-  double best_t = 0.0;
-  for (int i = 2; i >= 0; --i) {  // widest first: it wins ties
-    const float c = cfg.sgemm_tile_cost[i];
-    if (c <= 0.f) continue;
-    const double t = (double)((n + kW[i] - 1) / kW[i]) * c;
-    if (best_t == 0.0 || t < best_t) {
-      best_t = t;
-      best = kW[i];
-    }
-  }
-  return best;
-}
-
 void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t da, uint64_t db, uint64_t dc,
                TaskBody* body) {
   const gvm_task* t = p.t;
@@ -777,10 +755,8 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
     const int tm = ctx->path == kPathSplit3 ? kTcM : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
     const int tn = ctx->path == kPathSplit3 ? kTcN : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
     if (ctx->path != kPathFma) body->flags |= kFlagSplit3;
-    const int bn = ctx->path == kPathSplit3 ? sgemm_tile_width(ctx->cfg, t->n) : tn;
-    body->tile_n = (uint32_t)bn;
     body->tiles_m = (uint32_t)((t->m + tm - 1) / tm);
-    body->tiles_n = (uint32_t)((t->n + bn - 1) / bn);
+    body->tiles_n = (uint32_t)((t->n + tn - 1) / tn);
     body->ntiles = body->tiles_m * body->tiles_n;
   }
   body->nsplit = 0;

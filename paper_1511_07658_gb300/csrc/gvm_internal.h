@@ -13,8 +13,6 @@ constexpr int kFmaTile = 128;         // FMA SGEMM output tile (square)
 constexpr int kFmaBK = 16;            // FMA SGEMM k-step
 constexpr int kTcM = 128;             // tcgen05 tile rows (one TMEM lane per row)
 constexpr int kTcN = 256;             // tcgen05 tile columns (fp32 TMEM columns)
-// Tile widths a fused split3 task may use (multiples of 64 up to kTcN).
-constexpr bool fz_valid_bn(int bn) { return bn == 128 || bn == 192 || bn == 256; }
 constexpr int kTcBK = 32;             // bf16 k per pipeline stage (64-byte rows)
 constexpr int kTcStages = 4;          // TMA -> MMA pipeline depth
 constexpr int kSplitRows = 128;       // rows of A (or columns of B) per split tile
@@ -76,9 +74,7 @@ struct alignas(128) TaskBody {
   uint64_t a, b, c;  // device addresses of the operands
   uint64_t scratch;  // device address of the split3 planes (A planes, then B^T planes)
   uint64_t scratch_b;// device address of the B^T planes
-  uint32_t tile_n;   // split3 (fused form): columns of C per tile (128, 192 or 256)
-  uint32_t pad0;
-  uint64_t pad[2];
+  uint64_t pad[3];
 };
 static_assert(sizeof(TaskBody) == 384, "TaskBody layout");
 

@@ -626,7 +626,7 @@ struct FzPend {
   uint64_t c;
   int64_t n;
   int32_t m;
-  uint32_t tile, tiles_n, task, ntiles, tag, flags, seq, bn;
+  uint32_t tile, tiles_n, task, ntiles, tag, flags, seq;
 };
 
 struct FzItem {
@@ -639,7 +639,7 @@ struct FzItem {
   uint32_t tiles_n;
   int32_t m;
   int32_t k;
-  uint32_t bn;  // GEMM tile width (fused form)
+  uint32_t pad;
   int64_t n;
   int64_t vadd_tile;
   uint64_t a, b, c;
@@ -754,7 +754,6 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
           it.k = __ldcg(&b->k);
           it.n = __ldcg(&b->n);
           it.vadd_tile = __ldcg(&b->vadd_tile);
-          it.bn = __ldcg(&b->tile_n);
           it.a = __ldcg(&b->a);
           it.b = __ldcg(&b->b);
           it.c = __ldcg(&b->c);
@@ -777,7 +776,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
       const FzItem& item = sh.items[slot];
       const uint32_t kind = item.kind;
       FzTile t{reinterpret_cast<const float*>(item.a), reinterpret_cast<const float*>(item.b),
-               reinterpret_cast<float*>(item.c), item.n, item.m, item.k, 0, 0, (int)item.bn};
+               reinterpret_cast<float*>(item.c), item.n, item.m, item.k, 0, 0};
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
       if (kind == kItemExit) break;
@@ -817,7 +816,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
     auto tile_of = [](const FzItem& item) {
       return FzTile{reinterpret_cast<const float*>(item.a), reinterpret_cast<const float*>(item.b),
                     reinterpret_cast<float*>(item.c), item.n, item.m, item.k,
-                    (int)(item.tile / item.tiles_n), (int)(item.tile % item.tiles_n), (int)item.bn};
+                    (int)(item.tile / item.tiles_n), (int)(item.tile % item.tiles_n)};
     };
     auto count_done = [&]() {
       if (!has_done) return;
@@ -831,7 +830,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
       const uint32_t no = tile_no - 1;
       const FzPend& d = sh.pend[warp][no % 3u];
       const FzTile pt{nullptr, nullptr, reinterpret_cast<float*>(d.c), d.n, d.m, 0, (int)(d.tile / d.tiles_n),
-                      (int)(d.tile % d.tiles_n), (int)d.bn};
+                      (int)(d.tile % d.tiles_n)};
       bool drained;
       if constexpr (kWide)
         drained = wd_epilogue(pt, &sh.fz, no, p.wait_timeout_ns, &sh.abort, &sh.fail_where);
@@ -879,7 +878,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
         if (lane == 0) {
           // The item's sequence number names its finish counter.
           sh.pend[warp][tile_no % 3u] = FzPend{item.c, item.n, item.m, item.tile, item.tiles_n,
-                                               item.task, item.ntiles, item.tag, item.flags, seq, item.bn};
+                                               item.task, item.ntiles, item.tag, item.flags, seq};
           mbar_arrive(&sh.item_empty[slot]);
         }
         __syncwarp();

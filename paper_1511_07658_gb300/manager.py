@@ -260,7 +260,6 @@ class Manager:
         copy_run_bytes: int | None = None,
         vadd_tile: int | None = None,
         direct_output: bool | None = None,
-        sgemm_tile_n: int | None = None,
         l2_prefetch: bool | None = None,
         device: int | None = None,
     ):
@@ -307,12 +306,6 @@ class Manager:
         cfg.vadd_tile = int(tuned.get("vadd_tile", 0) if vadd_tile is None else vadd_tile)
         cfg.direct_output = int(bool(tuned.get("direct_output", 0) if direct_output is None else direct_output))
         cfg.l2_prefetch = int(bool(tuned.get("l2_prefetch", 0) if l2_prefetch is None else l2_prefetch))
-        # split3 tile width: fixed, or per task from the autotuner's cost table
-        cfg.sgemm_tile_n = int(sgemm_tile_n or 0)
-        cost = tuned.get("sgemm_tile_cost") if sgemm_tile_n is None else None
-        if cost:
-            for i, w in enumerate((128, 192, 256)):
-                cfg.sgemm_tile_cost[i] = float(cost.get(str(w), 0.0))
         self.cfg = cfg
         h = c_void_p()
         with torch.cuda.device(self.device):

@@ -650,3 +650,61 @@ def test_stress_mix_ragged_sizes(gvm, mode, path):
     # scaled to test size: 8 ranks x 6 tasks, every result against the oracle.
     w = synth.stress_mix(ranks=8, per_rank=6, vadd_median=4096, side_median=96)
     run_workload(gvm, w, mode=mode, path=path, depth=8, slice_mb=32)
+
+
+def test_continuous_solo_equals_mix_bitwise(gvm):
+    """Serving (continuous mode): tasks of four ranks arrive open loop, 50 us
+    apart per rank, while earlier ones are still on the GPU (the resident
+    scheduler admits them as ring slots and staging space free up). Every
+    result must be bitwise the one the same task gives when it runs alone
+    through a manager of the same configuration, and the oracle's."""
+    R, per = 4, 8
+    w = synth.stress_mix(ranks=R, per_rank=per, vadd_median=1 << 18, side_median=320, rate_per_rank_hz=20000.0)
+    cfg = dict(ring_depth=4, mode="continuous", sgemm_path="split3", slice_bytes=320 << 20)
+
+    def task_of(spec, keep):
+        t = gvm.GvmTask()
+        if spec.kind == synth.TASK_VADD:
+            a, b = synth.vadd_inputs(spec.seed, spec.n)
+            ins = (pinned(a), pinned(b))
+            out = torch.full((spec.n,), float("nan")).pin_memory()
+            t.type, t.n = gvm.GVM_TASK_VADD, spec.n
+        else:
+            A, B = synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
+            ins = (pinned(A), pinned(B))
+            out = torch.full((spec.m, spec.n), float("nan")).pin_memory()
+            t.type, t.m, t.n, t.k = gvm.GVM_TASK_SGEMM, spec.m, spec.n, spec.k
+        t.flags = 0
+        t.a, t.b, t.c = ins[0].data_ptr(), ins[1].data_ptr(), out.data_ptr()
+        keep.append(ins)
+        return t, out
+
+    keep, mix_out = [], {}
+    with gvm.Manager(R, **cfg) as mgr:
+        ranks = [mgr.attach(r) for r in range(R)]
+        by_rank = w.by_rank()
+        arrays, arrivals = [], []
+        for r in range(R):
+            arr = (gvm.GvmTask * per)()
+            for i, spec in enumerate(by_rank[r]):
+                arr[i], mix_out[(r, i)] = task_of(spec, keep)
+            arrays.append(arr)
+            arrivals.append([int(s.arrival_s * 1e9) for s in by_rank[r]])
+        span, lat = mgr.open_loop_run(ranks, arrays, arrivals, max_inflight=4)
+        assert mgr.stats()["device_status"] == 0
+        # The mix overlapped: some task completed after a later arrival of another rank.
+        done_at = [arrivals[r][i] / 1e9 + lat[r][i] for r in range(R) for i in range(per)]
+        assert max(done_at) > min(a for arr in arrivals for a in arr[1:]) / 1e9
+    with gvm.Manager(1, **cfg) as solo:
+        rk = solo.attach(0)
+        for r in range(R):
+            for i, spec in enumerate(w.by_rank()[r]):
+                t, out = task_of(spec, keep)
+                rk.sync(rk.submit(t))
+                got = mix_out[(r, i)].numpy()
+                assert np.array_equal(bits(got), bits(out.numpy())), spec
+        assert solo.stats()["device_status"] == 0
+    for spec in w.tasks:
+        inputs = (synth.vadd_inputs(spec.seed, spec.n) if spec.kind == synth.TASK_VADD
+                  else synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k))
+        check_result(spec, inputs, mix_out[(spec.rank, spec.index)])
