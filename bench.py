@@ -63,7 +63,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gvm", "reference"], default="gvm")
-    p.add_argument("--workload", choices=["sgemm512", "vadd_tiny", "serving", "grouped", "stress"], default="sgemm512")
+    p.add_argument("--workload", choices=["sgemm512", "vadd_tiny", "vadd_hbm", "serving", "grouped", "stress"],
+                   default="sgemm512")
     p.add_argument("--serving-tasks", type=int, default=0, help="serving workload: total tasks (default 4096)")
     p.add_argument("--repeats", type=int, default=3, help="serving and stress: runs per load point")
     p.add_argument("--duration", type=float, default=10.0,
@@ -103,6 +104,10 @@ def workload(name, ranks=0, per_rank=0):
         R, P = ranks or 16, per_rank or 64
         w = synth.sgemm_square(ranks=R, per_rank=P, side=512)
         desc = f"SGEMM M=N=K=512, {R} ranks x {P} tasks, standard-normal operands"
+    elif name == "vadd_hbm":
+        R, P = ranks or 16, per_rank or 4
+        w = synth.vadd_tiny(ranks=R, per_rank=P, n=1 << 22)
+        desc = f"vector add n=2^22, {R} ranks x {P} tasks, uniform [-1,1) operands"
     else:
         R, P = ranks or 4, per_rank or 8
         w = synth.vadd_tiny(ranks=R, per_rank=P, n=65536)
@@ -792,8 +797,9 @@ def gpu_arm(args, w, desc, rank, world):
         "direct_output": bool(direct_output_used),
         "l2_prefetch": bool(mgr.cfg.l2_prefetch),
         "operands": "resident in HBM for value; pinned host buffers for e2e",
-        "l2": "inputs larger than L2 (2 GiB of operands per step)" if args.workload == "sgemm512"
-        else "inputs smaller than L2; latency-bound",
+        "l2": {"sgemm512": "inputs larger than L2 (2 GiB of operands per step)",
+               "vadd_hbm": "inputs larger than L2 (2 GiB of operands per step)"}.get(
+                   args.workload, "inputs smaller than L2; latency-bound"),
         "parallelism": f"replicas x{world}" if world > 1 else f"1 GPU, {R} SPMD ranks as host threads",
         "rank_threads": "native (gvm_spmd_run)" if args.harness == "native" else "Python threads",
     }
@@ -1882,7 +1888,7 @@ def main():
             # HBM roofline of the elementwise task kernel on the product path.
             wv = synth.vadd_tiny(ranks=16, per_rank=4, n=1 << 22)
             out["vadd_hbm"] = resident_leg(args, wv, gen_inputs(wv), "split3", max(5, args.steps), args.warmup,
-                                           "vadd16x4_2p22")
+                                           "vadd_hbm")
             out["vadd_hbm"]["workload"] = "vector add n=2^22, 16 ranks x 4 tasks (3.2 GB of HBM traffic a step)"
         if extras and not args.skip_plain:
             out["plain_per_rank"] = plain_forms(w, out)

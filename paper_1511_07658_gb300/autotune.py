@@ -106,7 +106,7 @@ def time_sgemm(m: int, n: int, k: int, ranks: int = 16, per_rank: int = 16, step
     """Median step time (s) of resident SGEMMs, every task m x n x k."""
     la, lb, lc = 4 * m * k, 4 * k * n, 4 * m * n
     per_task = _al(la) + _al(lb) + _al(lc)
-    mgr = Manager(ranks, ring_depth=per_rank, mode="barrier", sgemm_path=path,
+    mgr = Manager(ranks, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode="barrier", sgemm_path=path,
                   slice_bytes=per_task * per_rank + (4 << 20), resident_bytes=per_task * per_rank,
                   l2_prefetch=prefetch)
     try:

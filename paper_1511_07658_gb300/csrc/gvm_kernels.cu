@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
   if (warp < kFzConvWarps) {
     FzTile prev{};
     bool pending = false, ok = true;
+    uint32_t land_n = 0, land_iss = 0;
     auto drain = [&]() -> bool {
       if (!pending) return true;
       pending = false;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     };
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
-      ok = wd_convert(t, big, &ws, it, timeout_ns, &abort_flag, &fail_where, nullptr, drain);
+      ok = wd_convert(t, big, &ws, it, timeout_ns, &abort_flag, &fail_where, nullptr, drain, land_n, land_iss);
       if (ok) ok = drain();  // this group had no k-step of the tile
       prev = t;
       pending = true;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
       ++tile_no;
     }
     if (ok) drain();
+    wd_land_quiesce(&ws, land_n, land_iss, timeout_ns);
   } else if (warp == kFzMmaWarp) {
     if (lane == 0) {
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -392,7 +394,7 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
     return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
   }
   if (path == GVM_SGEMM_SPLIT3_WIDE) {
-    const size_t smem = (size_t)kWdStages * kWdStageBytes + 1024;
+    const size_t smem = (size_t)kWdSmemBytes + 1024;
     if (allow_smem(wd_sgemm_kernel, smem) != GVM_OK) return GVM_EDEVICE;
     const int sms = sm_count();
     if (sms <= 0) return GVM_ENODEV;

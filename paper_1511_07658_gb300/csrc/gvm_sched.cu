@@ -811,6 +811,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
     uint32_t it_k = 0, tile_no = 0;
     bool has_drain = false, has_done = false;  // tile tile_no-1 to drain; tile done_no to count
     uint32_t done_no = 0;
+    uint32_t land_n = 0, land_iss = 0;  // wide form: A landings this warp's group consumed, issued
     // GEMM tile number i of this CTA is kept (by lane 0) in pend[warp][i % 3]
     // until it is counted, out of the registers the staging loop needs.
     auto tile_of = [](const FzItem& item) {
@@ -898,7 +899,8 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
           // One accumulator: drain tile T-1 right after this group's first
           // k-step of T (T's MMAs wait for it), then count T-1.
           ok = wd_convert(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
-                          tid == 0 ? &sh.prof[kProfStageWait] : nullptr, [&]() -> bool { return drain(); });
+                          tid == 0 ? &sh.prof[kProfStageWait] : nullptr, [&]() -> bool { return drain(); },
+                          land_n, land_iss);
           if (ok) ok = drain();  // the group had no k-step of T
           if (ok) count_done();
         } else {
@@ -936,6 +938,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
     }
     if (ok && !sh.abort) ok = flush();
     if (!ok && lane == 0) report_error(p, kStatusTimeout, sh.fail_where, 0);
+    if constexpr (kWide) wd_land_quiesce(&sh.fz, land_n, land_iss, p.wait_timeout_ns);
   }
   if constexpr (kWide)
     wd_teardown(&sh.fz);
@@ -954,7 +957,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) sched_wide_kernel(const SchedPa
 
 static size_t dyn_smem_bytes(int path) {
   if (path == kPathSplit3) return (size_t)kTcStages * kTcStageBytes + 1024;
-  if (path == kPathSplit3Wide) return (size_t)kWdStages * kWdStageBytes + 1024;
+  if (path == kPathSplit3Wide) return (size_t)kWdSmemBytes + 1024;
   return sizeof(FmaSmem) + 1024;
 }
 

@@ -17,15 +17,20 @@
 // k-step of tile T, and the MMAs of tile T start once it is drained.
 //
 // CTA roles as in the fused form (10 warps: 8 converters in two groups, MMA,
-// control). A converter keeps 128 floats of loads in flight (8 items of A, 8
-// of B). With 10 warps two SM sub-partitions hold three warps each, which
-// caps a thread at 168 registers, so the compiler keeps part of that in
-// local memory.
+// control). On interior tiles the A operand arrives by bulk copy: each group
+// owns a landing buffer for its k-steps' binary32 A rows (256 rows x 128
+// bytes), filled by cp.async.bulk (one 128-byte row segment per copy, issued
+// by the group's first warp) while the group converts; the converters read A
+// from it and keep only B's 64 floats of loads in registers. With all of A
+// and B in registers (ragged tiles) a converter holds 128 floats of loads;
+// with 10 warps a thread has at most 168 registers, so part of that spills.
 //
-// Stage layout (64 KB, three stages): A hi, A lo [256 rows][32 k] K-major with
-// the 64-byte swizzle on 8-row atoms (rows 128..255 start 8 KB in, where the
-// second MMA half's descriptor points); B hi, B lo [32 k][256 n] MN-major, as
-// in the fused form.
+// Stage layout (64 KB, two stages: group g fills stage g): A hi, A lo [256
+// rows][32 k] K-major with the 64-byte swizzle on 8-row atoms (rows 128..255
+// start 8 KB in, where the second MMA half's descriptor points); B hi, B lo
+// [32 k][256 n] MN-major, as in the fused form. Then the two landing
+// buffers: row r at 144 r (the 16-byte pad spreads a warp's reads of 8 rows
+// over all banks).
 #pragma once
 
 #include "gvm_fused.cuh"
@@ -34,7 +39,7 @@ namespace gvm {
 
 constexpr int kWdM = 256;
 constexpr int kWdN = 256;
-constexpr int kWdStages = 3;
+constexpr int kWdStages = 2;
 constexpr uint32_t kWdAOff = 0;                       // A hi [256][32] bf16
 constexpr uint32_t kWdAlOff = kWdM * kTcBK * 2;       // A lo
 constexpr uint32_t kWdBOff = 2 * kWdM * kTcBK * 2;    // B hi [32][256] bf16, MN-major
@@ -43,11 +48,18 @@ constexpr uint32_t kWdStageBytes = kWdBlOff + kWdN * kTcBK * 2;
 static_assert(kWdStageBytes == 65536, "wide stage layout");
 constexpr uint32_t kWdHalfA = 128 * kTcBK * 2;  // bytes of 128 rows of an A plane
 constexpr uint32_t kWdTmemCols = 512;
+constexpr uint32_t kWdLandPitch = kTcBK * 4 + 16;             // bytes per landed A row
+constexpr uint32_t kWdLandBytes = kWdM * kWdLandPitch;         // one group's landing buffer
+constexpr uint32_t kWdLandTx = kWdM * kTcBK * 4;               // bytes a landing receives
+constexpr uint32_t kWdSmemBytes = kWdStages * kWdStageBytes + 2 * kWdLandBytes;  // dynamic, before alignment
+static_assert(kWdSmemBytes + 1024 <= 227 * 1024, "wide form shared memory");
 struct WdShared {
   uint64_t full[kWdStages];   // converters -> MMA: one arrival per warp of a group
   uint64_t empty[kWdStages];  // MMA -> converters: tcgen05.commit
   uint64_t acc_full;          // MMA -> epilogue: the accumulator holds a finished tile
   uint64_t acc_empty;         // epilogue -> MMA: one arrival per converter warp
+  uint64_t land_full[2];      // bulk copies -> group g: its landing holds a k-step of A (expect_tx)
+  uint64_t land_empty[2];     // group g's 4 warps -> its first warp: the landing has been read
   uint32_t tmem_base;
   uint32_t pad;
 };
@@ -60,6 +72,10 @@ __device__ __forceinline__ void wd_init(WdShared* ws) {
     }
     mbar_init(&ws->acc_full, 1);
     mbar_init(&ws->acc_empty, kFzConvWarps);
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(&ws->land_full[g], 1);
+      mbar_init(&ws->land_empty[g], kFzGroupWarps);
+    }
     mbar_fence_init();
   }
   if ((threadIdx.x >> 5) == kFzMmaWarp) tmem_alloc(&ws->tmem_base, kWdTmemCols);
@@ -73,6 +89,19 @@ __device__ __forceinline__ void wd_teardown(WdShared* ws) {
   __syncthreads();
   tc_fence_after();
   if ((threadIdx.x >> 5) == kFzMmaWarp) tmem_dealloc(ws->tmem_base, kWdTmemCols);
+}
+
+// Bulk copy of `bytes` (a multiple of 16) from global memory into this CTA's
+// shared memory, counted on `bar` (complete_tx); both addresses 16-byte aligned.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
 }
 
 // Thread (w, lane) of a group stages k-step kb of a wide tile:
@@ -120,46 +149,75 @@ __device__ __forceinline__ void wd_load_b(const FzTile& t, int kb, int w, int la
 // warp's group, loads one group k-step ahead and issued after each stage's
 // proxy fence (as the scheduler's fused form). after_first() runs once,
 // after the group's first k-step of the tile (the previous tile's drain).
-// Returns false when a wait ran out (*cta_abort set).
+// kFast (interior tile, k a multiple of kTcBK, 32-byte aligned rows): A
+// arrives in the group's landing buffer by bulk copy; land_n counts the
+// landings this group has consumed (the same in all its threads; it only
+// grows on kFast tiles). Returns false when a wait ran out (*cta_abort set).
 template <bool kFast, class AfterFirst>
 __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, WdShared* ws, uint32_t it,
                                                 int avec, int bvec, uint64_t timeout_ns,
                                                 volatile uint32_t* cta_abort, uint32_t* fail_where,
-                                                uint64_t* wait_acc, AfterFirst& after_first) {
+                                                uint64_t* wait_acc, AfterFirst& after_first, uint32_t& land_n,
+                                                uint32_t& land_iss) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int par = warp / kFzGroupWarps, w = warp % kFzGroupWarps;
   const int nkb = (t.k + kTcBK - 1) / kTcBK;
   const int kb0 = (int)((it + (uint32_t)par) & 1u);
   if (kb0 >= nkb) return true;
-  const float* pa = t.A + (int64_t)(t.tm * kWdM + 8 * w + (lane >> 2)) * t.k + 8 * (lane & 3);
   const float* pb = t.B + (int64_t)(lane >> 2) * t.n + (int64_t)t.tn * kWdN + 64 * w + 8 * (lane & 3);
-  const int64_t a_row32 = 32 * (int64_t)t.k, b_row8 = 8 * t.n, b_step = (int64_t)kTcBK * t.n;
-  auto load_a = [&](int kb, int j, float (&v)[8]) {
-    if (kFast) ld_cg_v8(pa + kb * kTcBK + j * a_row32, v);
-    else wd_load_a(t, kb, w, lane, j, avec, v);
+  const int64_t b_row8 = 8 * t.n, b_step = (int64_t)kTcBK * t.n;
+  const uint32_t land = base + kWdStages * kWdStageBytes + (uint32_t)par * kWdLandBytes;
+  auto fail = [&](uint32_t where) {
+    if (lane == 0) {
+      *fail_where = where;
+      *cta_abort = 1;
+    }
+    return false;
   };
+  // The group's first warp refills the landing with k-step kb's A rows once
+  // all four warps have read the previous landing.
+  auto land_a = [&](int kb) -> bool {
+    if (w != 0) return true;
+    if (land_n > 0 && !mbar_wait(&ws->land_empty[par], (land_n - 1) & 1u, timeout_ns, cta_abort))
+      return fail(kWhereEmptyBarrier);
+    if (lane == 0) mbar_expect_tx(&ws->land_full[par], kWdLandTx);
+    __syncwarp();
+    const float* src = t.A + (int64_t)(t.tm * kWdM) * t.k + kb * kTcBK;
+#pragma unroll
+    for (int i = 0; i < kWdM / 32; ++i) {
+      const int r = lane + 32 * i;
+      bulk_g2s(land + (uint32_t)r * kWdLandPitch, src + (int64_t)r * t.k, kTcBK * 4, &ws->land_full[par]);
+    }
+    ++land_iss;
+    return true;
+  };
+  auto load_a = [&](int kb, int j, float (&v)[8]) { wd_load_a(t, kb, w, lane, j, avec, v); };
   auto load_b = [&](int kb, int j, float (&v)[8]) {
     if (kFast) ld_cg_v8(pb + kb * b_step + (j >> 1) * b_row8 + 32 * (j & 1), v);
     else wd_load_b(t, kb, w, lane, j, bvec, v);
   };
-  float va[8][8], vb[8][8];
+  float va[kFast ? 1 : 8][8], vb[8][8];
+  if (kFast) {
+    if (!land_a(kb0)) return false;
+  } else {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) load_a(kb0, j, va[j]);
+    for (int j = 0; j < 8; ++j) load_a(kb0, j, va[kFast ? 0 : j]);
+  }
 #pragma unroll
   for (int j = 0; j < 8; ++j) load_b(kb0, j, vb[j]);
   const uint32_t a_off = (uint32_t)(8 * w) * 64u + swz64((uint32_t)(lane >> 2), (uint32_t)(lane & 3));
   const uint32_t b_off = swz64((uint32_t)(lane >> 2), (uint32_t)(lane & 3));
+  // A item j of this thread in the landing: row 8 w + (lane >> 2) + 32 j, bytes 32 (lane & 3) ..
+  const uint32_t a_land = land + (uint32_t)(8 * w + (lane >> 2)) * kWdLandPitch + 32u * (uint32_t)(lane & 3);
   bool first = true;
   for (int kb = kb0; kb < nkb; kb += 2) {
     const uint32_t q = it + (uint32_t)kb, s = q % kWdStages, ph = (q / kWdStages) & 1u;
     uint64_t t0 = 0;
     if (wait_acc != nullptr && warp == 0 && lane == 0) t0 = globaltimer();
-    if (!mbar_wait(&ws->empty[s], ph ^ 1u, timeout_ns, cta_abort)) {
-      if (lane == 0) {
-        *fail_where = kWhereEmptyBarrier;
-        *cta_abort = 1;
-      }
-      return false;
+    if (!mbar_wait(&ws->empty[s], ph ^ 1u, timeout_ns, cta_abort)) return fail(kWhereEmptyBarrier);
+    if (kFast) {
+      if (!mbar_wait(&ws->land_full[par], land_n & 1u, timeout_ns, cta_abort)) return fail(kWhereFullBarrier);
+      ++land_n;
     }
     if (t0) *wait_acc += globaltimer() - t0;
     const uint32_t st = base + s * kWdStageBytes;
@@ -170,9 +228,27 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
       // within its 8-row atom only, so every j shares a_off.
       const uint32_t off = a_off + (uint32_t)(32 * j) * 64u;
       uint4 hi, lo;
-      split8_x2(va[j], hi, lo);
+      if (kFast) {
+        // Odd rows of the 8 read their second 16 bytes first: the warp's
+        // 32 reads then fall on 8 different bank groups.
+        const uint32_t ra = a_land + (uint32_t)(32 * j) * kWdLandPitch;
+        const uint32_t sw = ((lane >> 2) & 1) ? 16u : 0u;
+        const uint4 x0 = ld_shared_v4(ra + sw), x1 = ld_shared_v4(ra + (sw ^ 16u));
+        const uint4 lo4 = sw ? x1 : x0, hi4 = sw ? x0 : x1;
+        float v[8] = {__uint_as_float(lo4.x), __uint_as_float(lo4.y), __uint_as_float(lo4.z),
+                      __uint_as_float(lo4.w), __uint_as_float(hi4.x), __uint_as_float(hi4.y),
+                      __uint_as_float(hi4.z), __uint_as_float(hi4.w)};
+        split8_x2(v, hi, lo);
+      } else {
+        split8_x2(va[kFast ? 0 : j], hi, lo);
+      }
       st_shared_v4(st + kWdAOff + off, hi);
       st_shared_v4(st + kWdAlOff + off, lo);
+    }
+    if (kFast) {
+      // This warp has read its rows of the landing.
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ws->land_empty[par]);
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -186,8 +262,12 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
     __syncwarp();
     if (lane == 0) mbar_arrive(&ws->full[s]);
     if (more) {
+      if (kFast) {
+        if (!land_a(kb + 2)) return false;
+      } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) load_a(kb + 2, j, va[j]);
+        for (int j = 0; j < 8; ++j) load_a(kb + 2, j, va[kFast ? 0 : j]);
+      }
 #pragma unroll
       for (int j = 0; j < 8; ++j) load_b(kb + 2, j, vb[j]);
     }
@@ -199,10 +279,23 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
   return true;
 }
 
+// Ragged tiles (every load checks its bounds, A in registers) in a function
+// of their own, so that their register needs do not weigh on the interior
+// tiles' loop.
+template <class AfterFirst>
+__device__ __noinline__ bool wd_convert_ragged(const FzTile& t, uint32_t base, WdShared* ws, uint32_t it, int avec,
+                                               int bvec, uint64_t timeout_ns, volatile uint32_t* cta_abort,
+                                               uint32_t* fail_where, uint64_t* wait_acc, AfterFirst& after_first,
+                                               uint32_t& land_n, uint32_t& land_iss) {
+  return wd_convert_loop<false>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
+                                after_first, land_n, land_iss);
+}
+
 template <class AfterFirst>
 __device__ __forceinline__ bool wd_convert(const FzTile& t, uint8_t* stages, WdShared* ws, uint32_t it,
                                            uint64_t timeout_ns, volatile uint32_t* cta_abort,
-                                           uint32_t* fail_where, uint64_t* wait_acc, AfterFirst after_first) {
+                                           uint32_t* fail_where, uint64_t* wait_acc, AfterFirst after_first,
+                                           uint32_t& land_n, uint32_t& land_iss) {
   const int avec = ((t.k & 7) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 31) == 0)   ? 2
                    : ((t.k & 3) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 15) == 0) ? 1
                                                                                       : 0;
@@ -213,9 +306,21 @@ __device__ __forceinline__ bool wd_convert(const FzTile& t, uint8_t* stages, WdS
                     (int64_t)(t.tn + 1) * kWdN <= t.n;
   const uint32_t base = smem_u32(stages);
   return fast ? wd_convert_loop<true>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
-                                      after_first)
-              : wd_convert_loop<false>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
-                                       after_first);
+                                      after_first, land_n, land_iss)
+              : wd_convert_ragged(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
+                                  after_first, land_n, land_iss);
+}
+
+// Converter warps, once they stop (normally every landing issued has been
+// consumed; after a failed wait one may still be in flight): wait, bounded
+// and whatever the abort flag says, for the group's last issued landing, so
+// that no bulk copy writes this CTA's shared memory after it exits.
+__device__ __forceinline__ void wd_land_quiesce(WdShared* ws, uint32_t land_n, uint32_t land_iss,
+                                                uint64_t timeout_ns) {
+  const int par = (threadIdx.x >> 5) / kFzGroupWarps;
+  if (land_iss <= land_n) return;
+  volatile uint32_t never = 0;
+  (void)mbar_wait(&ws->land_full[par], (land_iss - 1) & 1u, timeout_ns, &never);
 }
 
 // Converter warps: drain the accumulator of wide tile t (the tile_no-th of
