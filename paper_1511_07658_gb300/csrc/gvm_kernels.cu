@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(kFzThreads, 1)
 // accumulator is drained by the converters right after their first k-step of
 // the next tile (one accumulator fills TMEM).
 __global__ void __launch_bounds__(kFzThreads, 1)
-    wd_sgemm_kernel(const float* A, const float* B, float* C, int m, int n, int k, uint64_t timeout_ns) {
+    wd_sgemm_kernel(const __grid_constant__ CUtensorMap tmA, int a_tma, const float* A, const float* B, float* C,
+                    int m, int n, int k, uint64_t timeout_ns) {
   __shared__ WdShared ws;
   __shared__ uint32_t abort_flag, fail_where;
   extern __shared__ uint8_t dyn_smem[];
@@ -151,7 +152,8 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     };
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
-      ok = wd_convert(t, big, &ws, it, timeout_ns, &abort_flag, &fail_where, nullptr, drain, land_n, land_iss);
+      ok = wd_convert(t, big, &ws, it, timeout_ns, &abort_flag, &fail_where, nullptr, drain, land_n, land_iss,
+                      a_tma ? &tmA : nullptr);
       if (ok) ok = drain();  // this group had no k-step of the tile
       prev = t;
       pending = true;
@@ -312,6 +314,22 @@ CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUten
   }
 }
 
+CUresult encode_wide_a_map(const float* A, int32_t m, int32_t k, CUtensorMap* tm) {
+  // Only where the wide form's interior tiles land A (k a multiple of the
+  // k-step, rows 32-byte aligned); the map is then a box of 256 rows x 32
+  // binary32 values, written densely (128-byte rows) into shared memory.
+  if ((k % kTcBK) != 0 || (reinterpret_cast<uintptr_t>(A) & 31) != 0 || m < kWdM) return CUDA_ERROR_INVALID_VALUE;
+  const DriverApi* api = driver_api();
+  if (!api) return CUDA_ERROR_NOT_INITIALIZED;
+  const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)m};
+  const cuuint64_t strides[1] = {(cuuint64_t)k * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kWdM};
+  const cuuint32_t estr[2] = {1, 1};
+  return api->encode_tiled(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
 constexpr uint64_t kStandaloneTimeoutNs = 10ull * 1000 * 1000 * 1000;
 
 static int sm_count() {
@@ -400,7 +418,10 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
     if (sms <= 0) return GVM_ENODEV;
     const int64_t ntiles = (int64_t)((m + kWdM - 1) / kWdM) * ((n + kWdN - 1) / kWdN);
     const int grid = (int)(ntiles < sms ? ntiles : sms);
-    wd_sgemm_kernel<<<grid, kFzThreads, smem, s>>>(A, B, C, m, n, k, kStandaloneTimeoutNs);
+    CUtensorMap tmA;
+    const int a_tma = encode_wide_a_map(A, m, k, &tmA) == CUDA_SUCCESS ? 1 : 0;
+    if (!a_tma) memset(&tmA, 0, sizeof(tmA));
+    wd_sgemm_kernel<<<grid, kFzThreads, smem, s>>>(tmA, a_tma, A, B, C, m, n, k, kStandaloneTimeoutNs);
     return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
   }
   if (path == GVM_SGEMM_SPLIT3_PAIR) {

@@ -17,11 +17,12 @@
 // k-step of tile T, and the MMAs of tile T start once it is drained.
 //
 // CTA roles as in the fused form (10 warps: 8 converters in two groups, MMA,
-// control). On interior tiles the A operand arrives by bulk copy: each group
-// owns a landing buffer for its k-steps' binary32 A rows (256 rows x 128
-// bytes), filled by cp.async.bulk (one 128-byte row segment per copy, issued
-// by the group's first warp) while the group converts; the converters read A
-// from it and keep only B's 64 floats of loads in registers. With all of A
+// control). On interior tiles the A operand arrives by TMA: each group owns a
+// landing buffer for its k-steps' binary32 A rows (256 rows x 128 bytes),
+// filled by one cp.async.bulk.tensor box of the task's A tensor map (or,
+// without a map, by 256 row copies of cp.async.bulk) issued by the group's
+// first warp while the group converts; the converters read A from it and
+// keep only B's 64 floats of loads in registers. With all of A
 // and B in registers (ragged tiles) a converter holds 128 floats of loads;
 // with 10 warps a thread has at most 168 registers, so part of that spills.
 //
@@ -29,8 +30,8 @@
 // rows][32 k] K-major with the 64-byte swizzle on 8-row atoms (rows 128..255
 // start 8 KB in, where the second MMA half's descriptor points); B hi, B lo
 // [32 k][256 n] MN-major, as in the fused form. Then the two landing
-// buffers: row r at 144 r (the 16-byte pad spreads a warp's reads of 8 rows
-// over all banks).
+// buffers: row r at 128 r (a warp reads 8 rows; odd rows take their second
+// 16 bytes first, which spreads the reads over all banks).
 #pragma once
 
 #include "gvm_fused.cuh"
@@ -48,7 +49,7 @@ constexpr uint32_t kWdStageBytes = kWdBlOff + kWdN * kTcBK * 2;
 static_assert(kWdStageBytes == 65536, "wide stage layout");
 constexpr uint32_t kWdHalfA = 128 * kTcBK * 2;  // bytes of 128 rows of an A plane
 constexpr uint32_t kWdTmemCols = 512;
-constexpr uint32_t kWdLandPitch = kTcBK * 4 + 16;             // bytes per landed A row
+constexpr uint32_t kWdLandPitch = kTcBK * 4;                  // bytes per landed A row (dense, as TMA writes)
 constexpr uint32_t kWdLandBytes = kWdM * kWdLandPitch;         // one group's landing buffer
 constexpr uint32_t kWdLandTx = kWdM * kTcBK * 4;               // bytes a landing receives
 constexpr uint32_t kWdSmemBytes = kWdStages * kWdStageBytes + 2 * kWdLandBytes;  // dynamic, before alignment
@@ -158,7 +159,7 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
                                                 int avec, int bvec, uint64_t timeout_ns,
                                                 volatile uint32_t* cta_abort, uint32_t* fail_where,
                                                 uint64_t* wait_acc, AfterFirst& after_first, uint32_t& land_n,
-                                                uint32_t& land_iss) {
+                                                uint32_t& land_iss, const CUtensorMap* tmA) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int par = warp / kFzGroupWarps, w = warp % kFzGroupWarps;
   const int nkb = (t.k + kTcBK - 1) / kTcBK;
@@ -182,11 +183,15 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
       return fail(kWhereEmptyBarrier);
     if (lane == 0) mbar_expect_tx(&ws->land_full[par], kWdLandTx);
     __syncwarp();
-    const float* src = t.A + (int64_t)(t.tm * kWdM) * t.k + kb * kTcBK;
+    if (tmA != nullptr) {
+      if (lane == 0) tma_load_2d(land, tmA, kb * kTcBK, t.tm * kWdM, &ws->land_full[par]);
+    } else {
+      const float* src = t.A + (int64_t)(t.tm * kWdM) * t.k + kb * kTcBK;
 #pragma unroll
-    for (int i = 0; i < kWdM / 32; ++i) {
-      const int r = lane + 32 * i;
-      bulk_g2s(land + (uint32_t)r * kWdLandPitch, src + (int64_t)r * t.k, kTcBK * 4, &ws->land_full[par]);
+      for (int i = 0; i < kWdM / 32; ++i) {
+        const int r = lane + 32 * i;
+        bulk_g2s(land + (uint32_t)r * kWdLandPitch, src + (int64_t)r * t.k, kTcBK * 4, &ws->land_full[par]);
+      }
     }
     ++land_iss;
     return true;
@@ -288,14 +293,14 @@ __device__ __noinline__ bool wd_convert_ragged(const FzTile& t, uint32_t base, W
                                                uint32_t* fail_where, uint64_t* wait_acc, AfterFirst& after_first,
                                                uint32_t& land_n, uint32_t& land_iss) {
   return wd_convert_loop<false>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
-                                after_first, land_n, land_iss);
+                                after_first, land_n, land_iss, nullptr);
 }
 
 template <class AfterFirst>
 __device__ __forceinline__ bool wd_convert(const FzTile& t, uint8_t* stages, WdShared* ws, uint32_t it,
                                            uint64_t timeout_ns, volatile uint32_t* cta_abort,
                                            uint32_t* fail_where, uint64_t* wait_acc, AfterFirst after_first,
-                                           uint32_t& land_n, uint32_t& land_iss) {
+                                           uint32_t& land_n, uint32_t& land_iss, const CUtensorMap* tmA = nullptr) {
   const int avec = ((t.k & 7) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 31) == 0)   ? 2
                    : ((t.k & 3) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 15) == 0) ? 1
                                                                                       : 0;
@@ -306,7 +311,7 @@ __device__ __forceinline__ bool wd_convert(const FzTile& t, uint8_t* stages, WdS
                     (int64_t)(t.tn + 1) * kWdN <= t.n;
   const uint32_t base = smem_u32(stages);
   return fast ? wd_convert_loop<true>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
-                                      after_first, land_n, land_iss)
+                                      after_first, land_n, land_iss, tmA)
               : wd_convert_ragged(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
                                   after_first, land_n, land_iss);
 }
