@@ -755,6 +755,10 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
     const int tm = ctx->path == kPathSplit3 ? kTcM : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
     const int tn = ctx->path == kPathSplit3 ? kTcN : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
     if (ctx->path != kPathFma) body->flags |= kFlagSplit3;
+    // Wide tiles land A by TMA: the task's own map of A at its device address.
+    if (ctx->path == kPathSplit3Wide &&
+        encode_wide_a_map(reinterpret_cast<const float*>(da), t->m, t->k, &body->tmA) == CUDA_SUCCESS)
+      body->flags |= kFlagTmA;
     body->tiles_m = (uint32_t)((t->m + tm - 1) / tm);
     body->tiles_n = (uint32_t)((t->n + tn - 1) / tn);
     body->ntiles = body->tiles_m * body->tiles_n;

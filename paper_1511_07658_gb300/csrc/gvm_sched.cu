@@ -185,6 +185,13 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
         uint4* dst = reinterpret_cast<uint4*>(&dt->body) + kFieldsAt;
 #pragma unroll
         for (int j = 0; j < 8; ++j) st_cg_v4(dst + j, v[j]);
+        if (flags & kFlagTmA) {  // the A tensor map (the descriptor's first 128 bytes)
+          static_assert(offsetof(TaskBody, tmA) == 0 && sizeof(CUtensorMap) == 128, "TaskBody tmA");
+          const uint4* m_src = reinterpret_cast<const uint4*>(&p.host_desc[idx]);
+          uint4* m_dst = reinterpret_cast<uint4*>(&dt->body);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) st_cg_v4(m_dst + j, ld_volatile_v4(m_src + j));
+        }
         const uint32_t tag = v[1].x;
         const uint32_t ntiles = v[1].y;
         const uint32_t nsplit = v[1].z;
@@ -643,6 +650,7 @@ struct FzItem {
   int64_t n;
   int64_t vadd_tile;
   uint64_t a, b, c;
+  uint64_t tma;  // wide split3: device address of the task's A tensor map, or 0
 };
 
 // Shared state of a tensor-core scheduler CTA; Pipe is the tile form's
@@ -754,6 +762,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
           it.k = __ldcg(&b->k);
           it.n = __ldcg(&b->n);
           it.vadd_tile = __ldcg(&b->vadd_tile);
+          it.tma = (it.flags & kFlagTmA) ? reinterpret_cast<uint64_t>(&b->tmA) : 0ull;
           it.a = __ldcg(&b->a);
           it.b = __ldcg(&b->b);
           it.c = __ldcg(&b->c);
@@ -875,6 +884,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
       const uint64_t t0 = tid == 0 ? globaltimer() : 0;
       if (kind == kTaskSgemm) {
         const FzTile t = tile_of(item);
+        const CUtensorMap* tma = kWide ? reinterpret_cast<const CUtensorMap*>(item.tma) : nullptr;
         __syncwarp();
         if (lane == 0) {
           // The item's sequence number names its finish counter.
@@ -898,9 +908,12 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
         if constexpr (kWide) {
           // One accumulator: drain tile T-1 right after this group's first
           // k-step of T (T's MMAs wait for it), then count T-1.
+          // The map was written by the ingest's generic stores: order them
+          // before the tensor copies that read it.
+          if (tma != nullptr && (warp % kFzGroupWarps) == 0) fence_tensormap_acquire(tma);
           ok = wd_convert(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
                           tid == 0 ? &sh.prof[kProfStageWait] : nullptr, [&]() -> bool { return drain(); },
-                          land_n, land_iss);
+                          land_n, land_iss, tma);
           if (ok) ok = drain();  // the group had no k-step of T
           if (ok) count_done();
         } else {
