@@ -87,6 +87,8 @@ def parse():
     p.add_argument("--paper-modes", action="store_true",
                    help="also run the workload in the paper's host-issued PS-1 / PS-2 modes")
     p.add_argument("--quantum", type=int, default=8)
+    p.add_argument("--copy-run-mb", type=int, default=None,
+                   help="merge adjacent host-mode copies up to this many MiB (default: the tuned choice)")
     p.add_argument("--l2-prefetch", type=int, choices=[0, 1], default=None,
                    help="split3: prefetch the next queued tile's operands into L2 (default: the tuned choice)")
     p.add_argument("--harness", choices=["native", "python"], default="native",
@@ -493,6 +495,7 @@ def gpu_arm(args, w, desc, rank, world):
         slice_bytes=slice_bytes, resident_bytes=resident, ingest_quantum=args.quantum,
         direct_output=None if args.direct_output is None else bool(args.direct_output),
         l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
+        copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
     )
     direct_output_used = mgr.cfg.direct_output
     ranks = [mgr.attach(r) for r in range(R)]
@@ -678,6 +681,8 @@ def gpu_arm(args, w, desc, rank, world):
             R, ring_depth=max(2, 1 << (2 * per_rank - 1).bit_length()), mode=args.mode, sgemm_path=args.path,
             slice_bytes=2 * host_stage + (64 << 20), ingest_quantum=args.quantum,
             direct_output=None if args.direct_output is None else bool(args.direct_output),
+            l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
+            copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
         )
         ranks2 = [mgr2.attach(r) for r in range(R)]
         mgr2.spmd_run_overlapped(ranks2, host_arrays, host_arrays_odd, max(1, args.warmup))
@@ -796,6 +801,7 @@ def gpu_arm(args, w, desc, rank, world):
         "mode": args.mode,
         "direct_output": bool(direct_output_used),
         "l2_prefetch": bool(mgr.cfg.l2_prefetch),
+        "copy_run_bytes": int(mgr.cfg.copy_run_bytes),
         "operands": "resident in HBM for value; pinned host buffers for e2e",
         "l2": {"sgemm512": "inputs larger than L2 (2 GiB of operands per step)",
                "vadd_hbm": "inputs larger than L2 (2 GiB of operands per step)"}.get(
