@@ -315,10 +315,10 @@ CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUten
 }
 
 CUresult encode_wide_a_map(const float* A, int32_t m, int32_t k, CUtensorMap* tm) {
-  // Only where the wide form's interior tiles land A (k a multiple of the
-  // k-step, rows 32-byte aligned); the map is then a box of 256 rows x 32
-  // binary32 values, written densely (128-byte rows) into shared memory.
-  if ((k % kTcBK) != 0 || (reinterpret_cast<uintptr_t>(A) & 31) != 0 || m < kWdM) return CUDA_ERROR_INVALID_VALUE;
+  // A box of 256 rows x 32 binary32 values, written densely (128-byte rows)
+  // into shared memory; rows beyond m and columns beyond k read as zero. The
+  // row pitch must be a multiple of 16 bytes and A 16-byte aligned.
+  if ((k % 4) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return CUDA_ERROR_INVALID_VALUE;
   const DriverApi* api = driver_api();
   if (!api) return CUDA_ERROR_NOT_INITIALIZED;
   const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)m};

@@ -35,9 +35,9 @@ uint64_t current_ctx_id();
 CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUtensorMap* tmA, CUtensorMap* tmB);
 
 // Tensor map of a row-major binary32 A (m x k) in boxes of 256 rows x 32
-// values, for the wide split3 form's landing buffers; an error where that
-// form does not land A (k not a multiple of 32, A not 32-byte aligned, m <
-// 256).
+// values (out-of-range elements read as zero), for the wide split3 form's
+// landing buffers; an error where TMA cannot address A (k not a multiple of
+// 4, A not 16-byte aligned).
 CUresult encode_wide_a_map(const float* A, int32_t m, int32_t k, CUtensorMap* tm);
 
 // Scheduler kernel: occupancy-derived grid for `path`, dynamic smem bytes,

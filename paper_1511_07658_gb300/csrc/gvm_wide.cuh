@@ -58,7 +58,7 @@ struct WdShared {
   uint64_t full[kWdStages];   // converters -> MMA: one arrival per warp of a group
   uint64_t empty[kWdStages];  // MMA -> converters: tcgen05.commit
   uint64_t acc_full;          // MMA -> epilogue: the accumulator holds a finished tile
-  uint64_t acc_empty;         // epilogue -> MMA: one arrival per converter warp
+  uint64_t acc_empty[2];      // epilogue -> MMA: half h (rows 128 h ..) drained, one arrival per converter warp
   uint64_t land_full[2];      // bulk copies -> group g: its landing holds a k-step of A (expect_tx)
   uint64_t land_empty[2];     // group g's 4 warps -> its first warp: the landing has been read
   uint32_t tmem_base;
@@ -72,7 +72,8 @@ __device__ __forceinline__ void wd_init(WdShared* ws) {
       mbar_init(&ws->empty[s], 1);
     }
     mbar_init(&ws->acc_full, 1);
-    mbar_init(&ws->acc_empty, kFzConvWarps);
+    mbar_init(&ws->acc_empty[0], kFzConvWarps);
+    mbar_init(&ws->acc_empty[1], kFzConvWarps);
     for (int g = 0; g < 2; ++g) {
       mbar_init(&ws->land_full[g], 1);
       mbar_init(&ws->land_empty[g], kFzGroupWarps);
@@ -150,11 +151,13 @@ __device__ __forceinline__ void wd_load_b(const FzTile& t, int kb, int w, int la
 // warp's group, loads one group k-step ahead and issued after each stage's
 // proxy fence (as the scheduler's fused form). after_first() runs once,
 // after the group's first k-step of the tile (the previous tile's drain).
-// kFast (interior tile, k a multiple of kTcBK, 32-byte aligned rows): A
-// arrives in the group's landing buffer by bulk copy; land_n counts the
-// landings this group has consumed (the same in all its threads; it only
-// grows on kFast tiles). Returns false when a wait ran out (*cta_abort set).
-template <bool kFast, class AfterFirst>
+// kATma: A arrives in the group's landing buffer (a TMA box of the task's A
+// map, rows and k beyond A zero-filled; without a map, row copies, interior
+// tiles only); land_n / land_iss count the landings this group has consumed
+// and issued (the same in all its threads). kBFast (B columns inside B, k a
+// multiple of kTcBK, 32-byte aligned rows): B by unchecked 32-byte loads.
+// Returns false when a wait ran out (*cta_abort set).
+template <bool kATma, bool kBFast, class AfterFirst>
 __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, WdShared* ws, uint32_t it,
                                                 int avec, int bvec, uint64_t timeout_ns,
                                                 volatile uint32_t* cta_abort, uint32_t* fail_where,
@@ -198,15 +201,15 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
   };
   auto load_a = [&](int kb, int j, float (&v)[8]) { wd_load_a(t, kb, w, lane, j, avec, v); };
   auto load_b = [&](int kb, int j, float (&v)[8]) {
-    if (kFast) ld_cg_v8(pb + kb * b_step + (j >> 1) * b_row8 + 32 * (j & 1), v);
+    if (kBFast) ld_cg_v8(pb + kb * b_step + (j >> 1) * b_row8 + 32 * (j & 1), v);
     else wd_load_b(t, kb, w, lane, j, bvec, v);
   };
-  float va[kFast ? 1 : 8][8], vb[8][8];
-  if (kFast) {
+  float va[kATma ? 1 : 8][8], vb[8][8];
+  if (kATma) {
     if (!land_a(kb0)) return false;
   } else {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) load_a(kb0, j, va[kFast ? 0 : j]);
+    for (int j = 0; j < 8; ++j) load_a(kb0, j, va[kATma ? 0 : j]);
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) load_b(kb0, j, vb[j]);
@@ -220,7 +223,7 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
     uint64_t t0 = 0;
     if (wait_acc != nullptr && warp == 0 && lane == 0) t0 = globaltimer();
     if (!mbar_wait(&ws->empty[s], ph ^ 1u, timeout_ns, cta_abort)) return fail(kWhereEmptyBarrier);
-    if (kFast) {
+    if (kATma) {
       if (!mbar_wait(&ws->land_full[par], land_n & 1u, timeout_ns, cta_abort)) return fail(kWhereFullBarrier);
       ++land_n;
     }
@@ -233,7 +236,7 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
       // within its 8-row atom only, so every j shares a_off.
       const uint32_t off = a_off + (uint32_t)(32 * j) * 64u;
       uint4 hi, lo;
-      if (kFast) {
+      if (kATma) {
         // Odd rows of the 8 read their second 16 bytes first: the warp's
         // 32 reads then fall on 8 different bank groups.
         const uint32_t ra = a_land + (uint32_t)(32 * j) * kWdLandPitch;
@@ -245,12 +248,12 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
                       __uint_as_float(hi4.z), __uint_as_float(hi4.w)};
         split8_x2(v, hi, lo);
       } else {
-        split8_x2(va[kFast ? 0 : j], hi, lo);
+        split8_x2(va[kATma ? 0 : j], hi, lo);
       }
       st_shared_v4(st + kWdAOff + off, hi);
       st_shared_v4(st + kWdAlOff + off, lo);
     }
-    if (kFast) {
+    if (kATma) {
       // This warp has read its rows of the landing.
       __syncwarp();
       if (lane == 0) mbar_arrive(&ws->land_empty[par]);
@@ -267,11 +270,11 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
     __syncwarp();
     if (lane == 0) mbar_arrive(&ws->full[s]);
     if (more) {
-      if (kFast) {
+      if (kATma) {
         if (!land_a(kb + 2)) return false;
       } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) load_a(kb + 2, j, va[kFast ? 0 : j]);
+        for (int j = 0; j < 8; ++j) load_a(kb + 2, j, va[kATma ? 0 : j]);
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) load_b(kb + 2, j, vb[j]);
@@ -284,16 +287,15 @@ __device__ __forceinline__ bool wd_convert_loop(const FzTile& t, uint32_t base, 
   return true;
 }
 
-// Ragged tiles (every load checks its bounds, A in registers) in a function
-// of their own, so that their register needs do not weigh on the interior
-// tiles' loop.
-template <class AfterFirst>
+// The variants other than the interior one in functions of their own, so
+// that their register needs do not weigh on the interior tiles' loop.
+template <bool kATma, class AfterFirst>
 __device__ __noinline__ bool wd_convert_ragged(const FzTile& t, uint32_t base, WdShared* ws, uint32_t it, int avec,
                                                int bvec, uint64_t timeout_ns, volatile uint32_t* cta_abort,
                                                uint32_t* fail_where, uint64_t* wait_acc, AfterFirst& after_first,
-                                               uint32_t& land_n, uint32_t& land_iss) {
-  return wd_convert_loop<false>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
-                                after_first, land_n, land_iss, nullptr);
+                                               uint32_t& land_n, uint32_t& land_iss, const CUtensorMap* tmA) {
+  return wd_convert_loop<kATma, false>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
+                                       after_first, land_n, land_iss, tmA);
 }
 
 template <class AfterFirst>
@@ -307,13 +309,17 @@ __device__ __forceinline__ bool wd_convert(const FzTile& t, uint8_t* stages, WdS
   const int bvec = ((t.n & 7) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 31) == 0)   ? 2
                    : ((t.n & 3) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 15) == 0) ? 1
                                                                                       : 0;
-  const bool fast = avec == 2 && bvec == 2 && (t.k % kTcBK) == 0 && (t.tm + 1) * kWdM <= t.m &&
-                    (int64_t)(t.tn + 1) * kWdN <= t.n;
+  const bool interior = avec == 2 && (t.tm + 1) * kWdM <= t.m;  // A rows by row copies without a map
+  const bool b_fast = bvec == 2 && (t.k % kTcBK) == 0 && (int64_t)(t.tn + 1) * kWdN <= t.n;
   const uint32_t base = smem_u32(stages);
-  return fast ? wd_convert_loop<true>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
-                                      after_first, land_n, land_iss, tmA)
-              : wd_convert_ragged(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
-                                  after_first, land_n, land_iss);
+  if (b_fast && (tmA != nullptr || (interior && (t.k % kTcBK) == 0)))
+    return wd_convert_loop<true, true>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
+                                       after_first, land_n, land_iss, tmA);
+  if (tmA != nullptr)
+    return wd_convert_ragged<true>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
+                                   after_first, land_n, land_iss, tmA);
+  return wd_convert_ragged<false>(t, base, ws, it, avec, bvec, timeout_ns, cta_abort, fail_where, wait_acc,
+                                  after_first, land_n, land_iss, nullptr);
 }
 
 // Converter warps, once they stop (normally every landing issued has been
@@ -375,10 +381,12 @@ __device__ __forceinline__ bool wd_epilogue(const FzTile& t, WdShared* ws, uint3
         }
       }
     }
+    // Half h is drained: the next tile's MMAs into it may start while the
+    // other half drains.
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ws->acc_empty[h]);
   }
-  tc_fence_before();
-  __syncwarp();
-  if (lane == 0) mbar_arrive(&ws->acc_empty);
   return true;
 }
 
@@ -387,7 +395,9 @@ __device__ __forceinline__ bool wd_epilogue(const FzTile& t, WdShared* ws, uint3
 __device__ __forceinline__ bool wd_mma(const FzTile& t, uint8_t* stages, WdShared* ws, uint32_t it,
                                        uint32_t tile_no, uint64_t timeout_ns, volatile uint32_t* cta_abort,
                                        uint32_t* fail_where, uint64_t* wait_acc) {
-  if (!mbar_wait(&ws->acc_empty, (tile_no & 1u) ^ 1u, timeout_ns, cta_abort)) {
+  // Half 0 of the accumulator must be drained before the first MMA; half 1
+  // is waited for inside the first k-step, before its first MMA.
+  if (!mbar_wait(&ws->acc_empty[0], (tile_no & 1u) ^ 1u, timeout_ns, cta_abort)) {
     *fail_where = kWhereAccumBarrier;
     *cta_abort = 1;
     return false;
@@ -408,6 +418,14 @@ __device__ __forceinline__ bool wd_mma(const FzTile& t, uint8_t* stages, WdShare
     const uint64_t dBh = sdesc_mn64b(sb + kWdBOff), dBl = sdesc_mn64b(sb + kWdBlOff);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+      if (h == 1 && kb == 0) {
+        if (!mbar_wait(&ws->acc_empty[1], (tile_no & 1u) ^ 1u, timeout_ns, cta_abort)) {
+          *fail_where = kWhereAccumBarrier;
+          *cta_abort = 1;
+          return false;
+        }
+        tc_fence_after();
+      }
       const uint32_t tmem = ws->tmem_base + (uint32_t)(h * kWdN);
       const uint64_t dAh = sdesc_k64b(sb + kWdAOff + h * kWdHalfA), dAl = sdesc_k64b(sb + kWdAlOff + h * kWdHalfA);
 #pragma unroll
