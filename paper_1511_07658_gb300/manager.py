@@ -411,6 +411,10 @@ class Manager:
             if rc != _abi.GVM_ESTATE:  # an IPC server still serves it: nothing was freed
                 self.handle = None
             check(rc, "gvm_shutdown")
+            # The device memory goes back to PyTorch's allocator now, not when
+            # the last reference to this object goes away.
+            self.arena = None
+            self.ctrl = None
 
     def __enter__(self):
         return self
