@@ -69,7 +69,8 @@ def parse():
     p.add_argument("--repeats", type=int, default=3, help="serving and stress: runs per load point")
     p.add_argument("--duration", type=float, default=10.0,
                    help="stress: seconds of arrivals per load point (the configuration's is 60)")
-    p.add_argument("--path", choices=["split3", "split3_wide", "fma"], default="split3")
+    p.add_argument("--path", choices=["split3", "split3_wide", "fma"], default=None,
+                   help="SGEMM arithmetic and tile form (default: the autotuner's split3 form)")
     p.add_argument("--mode", choices=["barrier", "continuous"], default="barrier")
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
@@ -1844,6 +1845,10 @@ def grouped_arm(args):
 
 def main():
     args = parse()
+    if args.path is None:  # the split3 tile form the autotuner chose on this GPU (fused if none)
+        from paper_1511_07658_gb300.manager import tuning
+
+        args.path = tuning().get("sgemm_form", "split3")
     if args.ipc_client:
         ipc_client_main(args)
         return
@@ -1893,7 +1898,7 @@ def main():
             # Vector adds through the scheduler at a size far beyond L2: the
             # HBM roofline of the elementwise task kernel on the product path.
             wv = synth.vadd_tiny(ranks=16, per_rank=4, n=1 << 22)
-            out["vadd_hbm"] = resident_leg(args, wv, gen_inputs(wv), "split3", max(5, args.steps), args.warmup,
+            out["vadd_hbm"] = resident_leg(args, wv, gen_inputs(wv), args.path, max(5, args.steps), args.warmup,
                                            "vadd_hbm")
             out["vadd_hbm"]["workload"] = "vector add n=2^22, 16 ranks x 4 tasks (3.2 GB of HBM traffic a step)"
         if extras and not args.skip_plain:
