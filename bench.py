@@ -78,7 +78,7 @@ def parse():
     p.add_argument("--skip-extra", action="store_true",
                    help="skip the FMA, vector-add and plain-form legs of the default workload")
     p.add_argument("--model", action="store_true", help="also check timings against Eqs. 1, 2 and 7")
-    p.add_argument("--e2e-overlap", type=int, choices=[1, 2], default=1,
+    p.add_argument("--e2e-overlap", type=int, choices=[1, 2], default=2,
                    help="end-to-end leg: steps in flight per rank (2: gvm_spmd_run_overlapped, own manager)")
     p.add_argument("--direct-output", type=int, choices=[0, 1], default=None,
                    help="host-mode results written by the scheduler into the host buffers (default: tuning)")
@@ -1170,6 +1170,11 @@ def plain_forms(w, out):
            "t_init": init}
     recs, _ = plain_per_rank(w, inputs, [("split3", "copy")], init="timed")
     res["split3"]["copy_with_init"] = recs[0]
+    # T_init of one process alone (this process keeps the GPU initialised)
+    w1 = synth.Workload("plain_solo", 1, [synth.TaskSpec(0, 0, synth.TASK_SGEMM, n=512, m=512, k=512,
+                                                         seed=synth.task_seed(0, 0))])
+    _, solo = plain_per_rank(w1, [inputs[0]], [("split3", "resident")], init="before")
+    res["t_init_one_process"] = {k: solo[k] for k in ("mean_s", "context_mean_s", "alloc_mean_s", "page_lock_mean_s")}
     ratios = {"shared_over_plain_resident": out["value"] / res["split3"]["resident"]["value"]}
     if out.get("e2e"):
         ratios["shared_e2e_over_plain_copy"] = out["e2e"]["value"] / res["split3"]["copy"]["value"]
@@ -1845,10 +1850,12 @@ def grouped_arm(args):
 
 def main():
     args = parse()
-    if args.path is None:  # the split3 tile form the autotuner chose on this GPU (fused if none)
+    if args.path is None:  # the split3 tile form the autotuner chose for this workload class (fused if none)
         from paper_1511_07658_gb300.manager import tuning
 
-        args.path = tuning().get("sgemm_form", "split3")
+        t = tuning()
+        args.path = (t.get("sgemm_form_by_class", {}).get("grouped") if args.workload == "grouped" else None) \
+            or t.get("sgemm_form", "split3")
     if args.ipc_client:
         ipc_client_main(args)
         return

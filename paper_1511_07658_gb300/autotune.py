@@ -12,12 +12,15 @@ and keeps the fastest:
 * ``vadd_tile`` (elements per vector-add tile; 0 = per task, n / CTAs): 16
   ranks x 8 resident vector adds of n = 2^22 (10 steps);
 * ``sgemm_form`` (the split3 SGEMM tile shape): fused 128 x 256 tiles
-  against wide 256 x 256 tiles of one CTA, on square 512^3 (16 x 64 tasks),
-  on 512 x 768 x 512 (16 x 16) and on 2048^3 (16 x 1), resident; the wide
-  form becomes the manager's default only if it wins every one. A tile
-  shape per task inside one launch would need both forms in one kernel,
-  whose converters then spill (measured); so the shape is chosen per
-  manager, and a task's result is the same alone and in any mix;
+  against wide 256 x 256 tiles of one CTA (A by TMA), per workload class:
+  square 512^3 (16 x 64 tasks, the headline shape), 512 x 768 x 512
+  (16 x 16), 2048^3 (16 x 1) and a grouped mix of shapes drawn from
+  {128, ..., 2048} (16 ranks x 16 tasks). ``sgemm_form_by_class`` keeps the
+  faster form of each class; ``sgemm_form``, the manager's default, is the
+  512^3 class's. A tile shape per task inside one launch would need both
+  forms in one kernel, whose converters then spill (measured); so the shape
+  is chosen per manager (per workload), and a task's result is the same
+  alone and in any mix (every form computes each element the same way);
 * ``l2_prefetch`` (split3: the next queued tile's operands prefetched into
   L2): on against off on the same three workloads, kept if it wins all.
 
@@ -133,18 +136,58 @@ def time_sgemm(m: int, n: int, k: int, ranks: int = 16, per_rank: int = 16, step
 
 
 SGEMM_SHAPES = ((512, 512, 512, 64), (512, 768, 512, 16), (2048, 2048, 2048, 1))  # m, n, k, tasks a rank
+GROUPED_CLASS = "grouped"
+
+
+def time_grouped(path: str, ranks: int = 16, per_rank: int = 16, steps: int = 4) -> float:
+    """Median step time (s) of resident SGEMMs with M, N, K drawn from
+    {128, ..., 2048} (the grouped recipe), operands drawn on the device."""
+    import synth
+
+    w = synth.grouped_mixed(ranks=ranks, per_rank=per_rank)
+    side = 2048
+    pool = 4 * side * side
+    need, offs = [2 * pool] * ranks, {}
+    for spec in w.tasks:
+        offs[(spec.rank, spec.index)] = need[spec.rank]
+        need[spec.rank] += _al(4 * spec.m * spec.n)
+    resident = max(need)
+    mgr = Manager(ranks, ring_depth=max(2, 1 << (per_rank - 1).bit_length()), mode="barrier", sgemm_path=path,
+                  slice_bytes=resident + (4 << 20), resident_bytes=resident)
+    try:
+        rk = [mgr.attach(r) for r in range(ranks)]
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(5)
+        arrays = []
+        for r in range(ranks):
+            rk[r].resident_view(0, (2 * side * side,)).copy_(torch.randn(2 * side * side, generator=gen, device="cuda"))
+            arr = (GvmTask * per_rank)()
+            for i, spec in enumerate(w.by_rank()[r]):
+                t = arr[i]
+                t.type, t.flags, t.m, t.n, t.k = GVM_TASK_SGEMM, GVM_TASK_RESIDENT, spec.m, spec.n, spec.k
+                t.a_off, t.b_off, t.c_off = 0, pool, offs[(r, i)]
+            arrays.append(arr)
+        mgr.spmd_run(rk, arrays, 1)
+        dev, _, _ = mgr.spmd_run(rk, arrays, steps)
+        return statistics.median(dev) / 1e3
+    finally:
+        mgr.shutdown()
 
 
 def _shape_key(m, n, k):
     return f"{m}x{n}x{k}"
 
 
+HEADLINE_CLASS = "512x512x512"
+
+
 def choose_sgemm(form_t: dict, pf_t: dict) -> dict:
-    """The wide form and the prefetch are kept only where they win every
+    """Per workload class the faster tile form; the manager's default is the
+    headline class's (512^3). The prefetch is kept only if it wins every
     workload timed (step times in seconds, keyed by shape)."""
-    wide = all(t["split3_wide"] < t["split3"] for t in form_t.values())
+    by_class = {c: min(t, key=t.get) for c, t in form_t.items()}
     pf = all(t["1"] < t["0"] for t in pf_t.values())
-    return {"sgemm_form": "split3_wide" if wide else "split3", "l2_prefetch": int(pf)}
+    return {"sgemm_form": by_class[HEADLINE_CLASS], "sgemm_form_by_class": by_class, "l2_prefetch": int(pf)}
 
 
 def run(path: str = _m.TUNING_FILE) -> dict:
@@ -156,6 +199,7 @@ def run(path: str = _m.TUNING_FILE) -> dict:
         key = _shape_key(m, n, k)
         form_t[key] = {f: time_sgemm(m, n, k, per_rank=per, path=f) for f in ("split3", "split3_wide")}
         pf_t[key] = {str(int(on)): time_sgemm(m, n, k, per_rank=per, prefetch=on) for on in (False, True)}
+    form_t[GROUPED_CLASS] = {f: time_grouped(f) for f in ("split3", "split3_wide")}
     choice = {
         "copy_run_bytes": int(min(copy_t, key=copy_t.get)),
         "vadd_tile": int(min(vadd_t, key=vadd_t.get)),
@@ -168,8 +212,8 @@ def run(path: str = _m.TUNING_FILE) -> dict:
         "workloads": {
             "copy_run_bytes": "end-to-end leg, 16 ranks x 16 SGEMM 512^3, operands in one pinned block per rank",
             "vadd_tile": "16 ranks x 8 resident vector adds, n = 2^22",
-            "sgemm_form": "resident SGEMM, 16 ranks x (64 of 512^3, 16 of 512 x 768 x 512, 1 of 2048^3): "
-                          "fused 128 x 256 tiles against wide 256 x 256 tiles",
+            "sgemm_form": "resident SGEMM, 16 ranks x (64 of 512^3, 16 of 512 x 768 x 512, 1 of 2048^3, "
+                          "16 of the grouped mix): fused 128 x 256 tiles against wide 256 x 256 tiles",
             "l2_prefetch": "the same SGEMM workloads, fused tiles, next-tile L2 prefetch off (0) and on (1)",
         },
     }
