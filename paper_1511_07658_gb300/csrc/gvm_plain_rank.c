@@ -24,9 +24,9 @@
  * Protocol on stdin/stdout: the process reads its inputs, initialises
  * (INIT = before), prints "ready CTX ALLOC PIN" (ns spent creating the
  * context, allocating device memory and page-locking host memory), then per
- * phase waits for one byte on stdin, runs, and prints "T0 T1 T_INIT RC"
- * (CLOCK_MONOTONIC ns at the start and end of the timed region, the ns of
- * initialisation inside it, status 0 = ok).
+ * phase waits for one byte on stdin, runs, writes OUTFILE.i and then prints
+ * "T0 T1 T_INIT RC" (CLOCK_MONOTONIC ns at the start and end of the timed
+ * region, the ns of initialisation inside it, status 0 = ok).
  */
 #define _GNU_SOURCE
 #include <cuda_runtime.h>
@@ -185,14 +185,15 @@ int main(int argc, char** argv) {
     }
     if (!rc) rc = run_tasks(&r, paths[i], modes[i]);
     const uint64_t t1 = now_ns();
-    printf("%llu %llu %llu %d\n", (unsigned long long)t0, (unsigned long long)t1, (unsigned long long)t_init, rc);
-    fflush(stdout);
+    // The result file is complete before the line that reports the phase.
     snprintf(name, sizeof(name), "%s.%d", argv[6], i);
     FILE* o = fopen(name, "wb");
     if (!o) return 6;
     const size_t last = (size_t)(r.tasks - 1) * r.c_elems;
-    fwrite(r.host_out + last, sizeof(float), r.c_elems, o);
-    fclose(o);
+    if (fwrite(r.host_out + last, sizeof(float), r.c_elems, o) != r.c_elems) rc = rc ? rc : 30;
+    if (fclose(o) != 0) rc = rc ? rc : 31;
+    printf("%llu %llu %llu %d\n", (unsigned long long)t0, (unsigned long long)t1, (unsigned long long)t_init, rc);
+    fflush(stdout);
   }
   return rc ? 1 : 0;
 }
