@@ -223,8 +223,7 @@ template <bool kFast, bool kLate>
 __device__ __forceinline__ bool fz_convert_loop(const FzTile& t, uint32_t base, FzShared* fs, uint32_t it,
                                                 int avec, int bvec, uint64_t timeout_ns,
                                                 volatile uint32_t* cta_abort, uint32_t* fail_where,
-                                                uint64_t* wait_acc, float (&va)[4][8], float (&vb)[8][8],
-                                                bool preloaded) {
+                                                uint64_t* wait_acc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int par = warp / kFzGroupWarps, w = warp % kFzGroupWarps;
   const int nkb = (t.k + kTcBK - 1) / kTcBK;
@@ -242,12 +241,11 @@ __device__ __forceinline__ bool fz_convert_loop(const FzTile& t, uint32_t base, 
     if (kFast) ld_cg_v8(pb + kb * b_step + (j >> 1) * b_row8 + 32 * (j & 1), v);
     else fz_load_b(t, kb, w, lane, j, bvec, v);
   };
-  if (!preloaded) {
+  float va[4][8], vb[8][8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) load_a(kb0, j, va[j]);
+  for (int j = 0; j < 4; ++j) load_a(kb0, j, va[j]);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) load_b(kb0, j, vb[j]);
-  }
+  for (int j = 0; j < 8; ++j) load_b(kb0, j, vb[j]);
   const uint32_t a_off = (uint32_t)(8 * w) * 64u + swz64((uint32_t)(lane >> 2), (uint32_t)(lane & 3));
   const uint32_t b_off = swz64((uint32_t)(lane >> 2), (uint32_t)(lane & 3));
   for (int kb = kb0; kb < nkb; kb += 2) {
@@ -299,35 +297,10 @@ __device__ __forceinline__ bool fz_convert_loop(const FzTile& t, uint32_t base, 
   return true;
 }
 
-// Loads the first k-step of tile t that belongs to this warp's group (the
-// k-step fz_convert would load first) into va, vb, with bounds checks, so
-// that a caller can issue them early: before draining the previous tile's
-// accumulator, while the current tile's last MMAs run. Returns whether the
-// group has a k-step of t (if not, nothing is loaded).
-__device__ __forceinline__ bool fz_preload(const FzTile& t, uint32_t it, float (&va)[4][8], float (&vb)[8][8]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int par = warp / kFzGroupWarps, w = warp % kFzGroupWarps;
-  const int nkb = (t.k + kTcBK - 1) / kTcBK;
-  const int kb0 = (int)((it + (uint32_t)par) & 1u);
-  if (kb0 >= nkb) return false;
-  const int avec = ((t.k & 7) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 31) == 0)   ? 2
-                   : ((t.k & 3) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 15) == 0) ? 1
-                                                                                      : 0;
-  const int bvec = ((t.n & 7) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 31) == 0)   ? 2
-                   : ((t.n & 3) == 0 && (reinterpret_cast<uintptr_t>(t.B) & 15) == 0) ? 1
-                                                                                      : 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) fz_load_a(t, kb0, w, lane, j, avec, va[j]);
-#pragma unroll
-  for (int j = 0; j < 8; ++j) fz_load_b(t, kb0, w, lane, j, bvec, vb[j]);
-  return true;
-}
-
 template <bool kLate>
 __device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzShared* fs, uint32_t it,
                                            uint64_t timeout_ns, volatile uint32_t* cta_abort,
-                                           uint32_t* fail_where, uint64_t* wait_acc, float (&va)[4][8],
-                                           float (&vb)[8][8], bool preloaded = false) {
+                                           uint32_t* fail_where, uint64_t* wait_acc) {
   // Widest load every item of the tile allows: 2 = 32 bytes, 1 = 16 bytes, 0 = scalar.
   const int avec = ((t.k & 7) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 31) == 0)   ? 2
                    : ((t.k & 3) == 0 && (reinterpret_cast<uintptr_t>(t.A) & 15) == 0) ? 1
@@ -339,9 +312,9 @@ __device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzS
                     (int64_t)(t.tn + 1) * kTcN <= t.n;
   const uint32_t base = smem_u32(stages);
   return fast ? fz_convert_loop<true, kLate>(t, base, fs, it, avec, bvec, timeout_ns, cta_abort, fail_where,
-                                             wait_acc, va, vb, preloaded)
+                                             wait_acc)
               : fz_convert_loop<false, kLate>(t, base, fs, it, avec, bvec, timeout_ns, cta_abort, fail_where,
-                                              wait_acc, va, vb, preloaded);
+                                              wait_acc);
 }
 
 // Bulk prefetch of [p, p + bytes) into L2: a hint with no completion and no

@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     bool have_prev = false, ok = true;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
-      float va[4][8], vb[8][8];
-      ok = fz_convert<false>(t, big, &fs, it, timeout_ns, &abort_flag, &fail_where, nullptr, va, vb);
+      ok = fz_convert<false>(t, big, &fs, it, timeout_ns, &abort_flag, &fail_where, nullptr);
       if (ok && have_prev) ok = fz_epilogue(prev, &fs, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
       prev = t;
       have_prev = true;

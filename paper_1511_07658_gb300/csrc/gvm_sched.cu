@@ -821,11 +821,6 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
     bool has_drain = false, has_done = false;  // tile tile_no-1 to drain; tile done_no to count
     uint32_t done_no = 0;
     uint32_t land_n = 0, land_iss = 0;  // wide form: A landings this warp's group consumed, issued
-    // Fused form: the next GEMM tile's first k-step of this group, loaded
-    // before the previous tile's drain (pre_seq: the item it belongs to).
-    float pva[4][8], pvb[8][8];
-    bool pre = false;
-    uint32_t pre_seq = 0;
     // GEMM tile number i of this CTA is kept (by lane 0) in pend[warp][i % 3]
     // until it is counted, out of the registers the staging loop needs.
     auto tile_of = [](const FzItem& item) {
@@ -923,20 +918,8 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
           if (ok) count_done();
         } else {
           ok = fz_convert<true>(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
-                                tid == 0 ? &sh.prof[kProfStageWait] : nullptr, pva, pvb, pre && pre_seq == seq);
-          pre = false;
+                                tid == 0 ? &sh.prof[kProfStageWait] : nullptr);
           if (ok) {
-            // If the next item is a GEMM tile already queued, its first
-            // loads go out now, in flight while tile T-1 drains.
-            const uint32_t ns = (seq + 1) % kFzItems, nph = ((seq + 1) / kFzItems) & 1u;
-            uint32_t queued = 0;
-            if (lane == 0) queued = mbar_try_wait(&sh.item_full[ns], nph) ? 1u : 0u;
-            queued = __shfl_sync(0xffffffffu, queued, 0);
-            if (queued && sh.items[ns].kind == kTaskSgemm) {
-              const uint32_t it_next = it_k + (uint32_t)((t.k + kTcBK - 1) / kTcBK);
-              pre = fz_preload(tile_of(sh.items[ns]), it_next, pva, pvb);
-              pre_seq = seq + 1;
-            }
             count_done();
             ok = drain();
           }
