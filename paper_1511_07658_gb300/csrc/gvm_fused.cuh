@@ -317,29 +317,6 @@ __device__ __forceinline__ bool fz_convert(const FzTile& t, uint8_t* stages, FzS
                                               wait_acc);
 }
 
-// Bulk prefetch of [p, p + bytes) into L2: a hint with no completion and no
-// effect on results. p 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// One warp: ask L2 for the operands of GEMM tile t -- its rows of A (one
-// contiguous block) and, row by row of B, the tile's columns -- when every
-// piece starts on a 16-byte boundary and spans a multiple of 16 bytes (k and
-// n multiples of 4, 16-byte aligned bases); otherwise nothing. Every range
-// lies inside A or B.
-__device__ __forceinline__ void fz_prefetch_tile(const FzTile& t) {
-  const int lane = threadIdx.x & 31;
-  const int r0 = t.tm * kTcM;
-  const int rows = min(kTcM, t.m - r0);
-  const int64_t c0 = (int64_t)t.tn * kTcN;
-  const int64_t cols = min((int64_t)kTcN, t.n - c0);
-  if (rows <= 0 || cols <= 0 || (t.k & 3) || (t.n & 3)) return;
-  if ((reinterpret_cast<uintptr_t>(t.A) | reinterpret_cast<uintptr_t>(t.B)) & 15) return;
-  if (lane == 0) prefetch_l2(t.A + (int64_t)r0 * t.k, (uint32_t)(rows * t.k * 4));
-  for (int kk = lane; kk < t.k; kk += 32) prefetch_l2(t.B + (int64_t)kk * t.n + c0, (uint32_t)(cols * 4));
-}
-
 // 32-byte store of 8 floats; the address must be 32-byte aligned.
 __device__ __forceinline__ void st_v8(float* p, const uint32_t* r) {
   asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(r[0]), "r"(r[1]), "r"(r[2]),

@@ -653,6 +653,27 @@ struct FzItem {
   uint64_t tma;  // wide split3: device address of the task's A tensor map, or 0
 };
 
+// One thread: ask L2 for a GEMM item's task operands -- A's 128-row block
+// of the tile's row (from the tile in column 0 of its row) and all of B
+// (from tile (0, 0)) -- so that each task's operands are requested once, in
+// pieces of at most 1 MiB, when they are 16-byte aligned, span a multiple
+// of 16 bytes and B holds at most 4 MiB. A hint only.
+__device__ __forceinline__ void prefetch_task_operands(const FzItem& it) {
+  if (it.kind != kTaskSgemm || (it.k & 3) || ((it.a | it.b) & 15)) return;
+  const uint32_t tm = it.tile / it.tiles_n, tn = it.tile % it.tiles_n;
+  if (tn != 0) return;
+  auto pf = [](uint64_t addr, uint64_t bytes) {
+    for (uint64_t off = 0; off < bytes; off += (1u << 20)) {
+      const uint64_t len = bytes - off < (1u << 20) ? bytes - off : (1u << 20);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(addr + off), "r"((uint32_t)len) : "memory");
+    }
+  };
+  const int64_t rows = min((int64_t)kTcM, (int64_t)it.m - (int64_t)tm * kTcM);
+  if (rows > 0) pf(it.a + (uint64_t)tm * kTcM * (uint64_t)it.k * 4u, (uint64_t)rows * (uint64_t)it.k * 4u);
+  const uint64_t b_bytes = (uint64_t)it.k * (uint64_t)it.n * 4u;
+  if (tm == 0 && b_bytes <= (4u << 20) && (b_bytes & 15) == 0) pf(it.b, b_bytes);
+}
+
 // Shared state of a tensor-core scheduler CTA; Pipe is the tile form's
 // pipeline (FzShared: 128 x 256 tiles, WdShared: 256 x 256 tiles).
 template <class Pipe>
@@ -769,6 +790,9 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
         }
         sh.prof[kProfAcquire] += globaltimer() - t0;
         mbar_arrive(&sh.item_full[slot]);
+        // L2 prefetch, a few tiles ahead of the staging warps: the item two
+        // claims back (its slot is rewritten only two claims from now).
+        if (p.prefetch && seq >= 2) prefetch_task_operands(sh.items[(seq + 2) % kFzItems]);
       }
       __syncwarp();
       if (got == 0) break;
@@ -893,18 +917,6 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
           mbar_arrive(&sh.item_empty[slot]);
         }
         __syncwarp();
-        if constexpr (!kWide) {
-          if (p.prefetch && warp == 0) {
-            // The next queued tile's operands head for L2 while this tile
-            // stages (its slot is not reused before this warp releases it).
-            const uint32_t ns = (seq + 1) % kFzItems, nph = ((seq + 1) / kFzItems) & 1u;
-            uint32_t queued = 0;
-            if (lane == 0) queued = mbar_try_wait(&sh.item_full[ns], nph) ? 1u : 0u;
-            if (__shfl_sync(0xffffffffu, queued, 0) && sh.items[ns].kind == kTaskSgemm)
-              fz_prefetch_tile(tile_of(sh.items[ns]));
-            __syncwarp();
-          }
-        }
         if constexpr (kWide) {
           // One accumulator: drain tile T-1 right after this group's first
           // k-step of T (T's MMAs wait for it), then count T-1.
