@@ -17,6 +17,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sys/prctl.h>
 
 #include <atomic>
 #include <chrono>
@@ -69,12 +70,25 @@ bool debug_on() {
 
 // gvm_sync gives the device this long beyond its own wait limit to report.
 constexpr uint64_t kStreamQueryNs = 2000000;  // gvm_sync: driver status check period (2 ms)
+constexpr uint64_t kSyncSpinNs = 200000;      // gvm_sync: spin this long, then sleep between polls
+constexpr uint64_t kSyncSleepNs = 10000;      // gvm_sync: poll period once sleeping
 // Copies of one batch are merged when both sides are adjacent, by default up
 // to this many bytes per copy (gvm_config.copy_run_bytes): the link serves
 // 1 MiB copies at less than half its rate, while a few MiB per copy still
 // lets the scheduler start on the first tasks while later inputs arrive.
 constexpr uint64_t kDefaultCopyRun = 16ull << 20;
 constexpr uint64_t kHostGraceNs = 1000ull * 1000 * 1000;
+
+// Sleeps about ns nanoseconds: the calling thread's timer slack is set to
+// 1 us the first time (the default 50 us would stretch every short sleep).
+inline void short_sleep(uint64_t ns) {
+  thread_local bool slack_set = false;
+  if (!slack_set) {
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+    slack_set = true;
+  }
+  std::this_thread::sleep_for(std::chrono::nanoseconds(ns));
+}
 
 inline uint64_t now_ns() {
   return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -1029,6 +1043,7 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
   if (push_flushed(r) != GVM_OK) return GVM_EDEVICE;
   uint64_t last = r->synced;
   uint64_t t_prog = now_ns(), t_query = t_prog;
+  const uint64_t t_wait = t_prog;
   uint32_t spins = 0;
   while (true) {
     reap(r);
@@ -1052,7 +1067,14 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
     }
     if ((++spins & 63) == 0) {
       g.unlock();
-      std::this_thread::yield();
+      // Spin (yielding) for the first kSyncSpinNs, then poll every
+      // kSyncSleepNs: many ranks waiting on one GPU then leave the host's
+      // cores to the threads that have work (a rank preempted while it
+      // submits delays the whole request barrier by a scheduler slice).
+      if (now - t_wait > kSyncSpinNs)
+        short_sleep(kSyncSleepNs);
+      else
+        std::this_thread::yield();
       g.lock();
     }
   }

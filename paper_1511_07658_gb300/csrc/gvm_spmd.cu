@@ -4,6 +4,8 @@
 // step times contain the manager's work and not an interpreter's.
 #include <cuda_runtime.h>
 
+#include <sys/prctl.h>
+
 #include <atomic>
 #include <chrono>
 #include <thread>
@@ -26,8 +28,20 @@ class SpinBarrier {
       return;
     }
     uint32_t spins = 0;
+    const auto t0 = std::chrono::steady_clock::now();
     while (gen_.load(std::memory_order_acquire) == gen) {
-      if (++spins > 64) std::this_thread::yield();
+      if (++spins <= 64) continue;
+      // After 200 us, sleep between checks: waiting threads free the cores
+      // for the threads the barrier waits for.
+      if ((spins & 63) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200)) {
+        thread_local bool slack_set = false;  // 1 us timer slack for this thread's short sleeps
+        if (!slack_set) {
+          prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+          slack_set = true;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(10));
+      } else
+        std::this_thread::yield();
     }
   }
 
