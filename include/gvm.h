@@ -146,9 +146,15 @@ typedef struct gvm_config {
                                device mapping (page-locked memory the GPU can address;
                                a buffer without one uses the staged path), so outputs
                                take no staging and no copy */
-  int32_t l2_prefetch;      /* GVM_SGEMM_SPLIT3: 1 = when a CTA starts a GEMM tile, it
-                               asks L2 for the operands of the next tile it has queued
-                               (bulk prefetch; a hint, no result depends on it); 0 = off */
+  int32_t l2_prefetch;      /* split3: 1 = the claiming warp asks L2 for each task's operands
+                               (bulk prefetch, a few tiles ahead; a hint, no result depends
+                               on it); 0 = off */
+  int32_t copy_streams_max; /* copy_streams NULL: at most this many copy streams are created
+                               (0 = 31, which with the scheduler's stream fills the 32
+                               hardware queues of CUDA_DEVICE_MAX_CONNECTIONS=32); while
+                               2 x max_ranks exceeds it, ranks share input streams (r % n_in)
+                               and output streams (r % n_out), n_in + n_out <= the limit */
+  int32_t reserved0;        /* 0 */
 } gvm_config;
 
 typedef struct gvm_task {

@@ -57,6 +57,8 @@ class GvmConfig(ctypes.Structure):
         ("vadd_tile", c_int64),
         ("direct_output", c_int32),
         ("l2_prefetch", c_int32),
+        ("copy_streams_max", c_int32),
+        ("reserved0", c_int32),
     ]
 
 

@@ -510,7 +510,8 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   if (cfg.idle_poll_ns == 0) cfg.idle_poll_ns = 1000;
   if (cfg.copy_run_bytes == 0) cfg.copy_run_bytes = kDefaultCopyRun;
   if (cfg.vadd_tile < 0) return GVM_EINVAL;
-  if (cfg.direct_output < 0 || cfg.direct_output > 1 || cfg.l2_prefetch < 0 || cfg.l2_prefetch > 1)
+  if (cfg.direct_output < 0 || cfg.direct_output > 1 || cfg.l2_prefetch < 0 || cfg.l2_prefetch > 1 ||
+      cfg.copy_streams_max < 0 || cfg.reserved0 != 0)
     return GVM_EINVAL;
   if (cfg.vadd_tile > 0) cfg.vadd_tile = std::max<int64_t>(1024, cfg.vadd_tile / 1024 * 1024);
   if (cfg.ingest_quantum <= 0) cfg.ingest_quantum = 4;
@@ -598,6 +599,15 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   p.wait_timeout_ns = cfg.wait_timeout_ns;
   p.idle_poll_ns = cfg.idle_poll_ns;
 
+  // Copy streams the manager creates: one input and one output stream per
+  // rank while they fit the stream budget with the scheduler's stream,
+  // otherwise at most half of the budget each.
+  const uint32_t budget = cfg.copy_streams_max > 0 ? (uint32_t)cfg.copy_streams_max : 31u;
+  uint32_t n_in = R, n_out = R;
+  if (2 * R > budget) {
+    n_in = std::min<uint32_t>(R, std::max<uint32_t>(1u, (budget + 1) / 2));
+    n_out = std::min<uint32_t>(R, std::max<uint32_t>(1u, budget - n_in));
+  }
   ctx->ranks.resize(R);
   for (uint32_t r = 0; r < R; ++r) {
     auto rk = std::make_unique<gvm_rank>();
@@ -611,10 +621,20 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
       rk->in_stream = static_cast<cudaStream_t>(cfg.copy_streams[2 * r]);
       rk->out_stream = static_cast<cudaStream_t>(cfg.copy_streams[2 * r + 1]);
     } else {
-      e = cudaStreamCreateWithFlags(&rk->in_stream, cudaStreamNonBlocking);
-      if (e == cudaSuccess) ctx->owned_streams.push_back(rk->in_stream);
-      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&rk->out_stream, cudaStreamNonBlocking);
-      if (e == cudaSuccess) ctx->owned_streams.push_back(rk->out_stream);
+      // Ranks beyond the stream budget share streams round robin (rank r
+      // uses input stream r % n_in and output stream r % n_out).
+      if (r < n_in) {
+        e = cudaStreamCreateWithFlags(&rk->in_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) ctx->owned_streams.push_back(rk->in_stream);
+      } else {
+        rk->in_stream = ctx->ranks[r % n_in]->in_stream;
+      }
+      if (e == cudaSuccess && r < n_out) {
+        e = cudaStreamCreateWithFlags(&rk->out_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) ctx->owned_streams.push_back(rk->out_stream);
+      } else if (e == cudaSuccess) {
+        rk->out_stream = ctx->ranks[r % n_out]->out_stream;
+      }
       if (e != cudaSuccess) {
         cudaFreeHost(hb);
         return GVM_EDEVICE;

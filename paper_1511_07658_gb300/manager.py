@@ -261,6 +261,7 @@ class Manager:
         vadd_tile: int | None = None,
         direct_output: bool | None = None,
         l2_prefetch: bool | None = None,
+        copy_streams_max: int = 0,
         device: int | None = None,
     ):
         if not torch.cuda.is_available():
@@ -306,6 +307,7 @@ class Manager:
         cfg.vadd_tile = int(tuned.get("vadd_tile", 0) if vadd_tile is None else vadd_tile)
         cfg.direct_output = int(bool(tuned.get("direct_output", 0) if direct_output is None else direct_output))
         cfg.l2_prefetch = int(bool(tuned.get("l2_prefetch", 0) if l2_prefetch is None else l2_prefetch))
+        cfg.copy_streams_max = int(copy_streams_max)
         self.cfg = cfg
         h = c_void_p()
         with torch.cuda.device(self.device):
