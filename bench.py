@@ -1838,6 +1838,8 @@ def grouped_arm(args):
                      "peak_basis": basis,
                      "kernel": "gvm::" + {"split3": "sched_fused_kernel",
                                           "split3_wide": "sched_wide_kernel"}.get(args.path, "sched_fma_kernel"),
+                     "traffic": ncu_traffic({"split3": "sched_fused_kernel", "split3_wide": "sched_wide_kernel"}.get(
+                         args.path, "sched_fma_kernel") + "/grouped") if (R, P) == (64, 256) else None,
                      "launch_ms": kmean * 1e3},
         "sched_timeline_last_launch": {
             "cta_ms": {"acquire": ph[0] / 1e6, "stage_wait": ph[2] / 1e6, "gemm": ph[3] / 1e6,
