@@ -256,6 +256,21 @@ def whole_job_rate(units_per_rank_step: int, steps: int, world: int, slowest_s: 
     return units_per_rank_step * steps * world / slowest_s
 
 
+def host_memcpy_gbs(nbytes=256 << 20, reps=3):
+    """Host memory copy rate (read + write bytes per second) right after a
+    host-link-bound leg: context for its number, since other jobs on the
+    same host share the memory system the copies go through."""
+    a = np.ones(nbytes, dtype=np.uint8)
+    b = np.empty_like(a)
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        np.copyto(b, a)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return 2 * nbytes / best / 1e9
+
+
 def percentile(xs, q):
     if not xs:
         return None
@@ -710,6 +725,7 @@ def gpu_arm(args, w, desc, rank, world):
             "host_link_gbs": (h2d + d2h) * e_steps / h_s / 1e9,
             "ms_per_step": 1e3 * h_s / e_steps,
             "steps_in_flight": 2,
+            "host_memcpy_gbs": host_memcpy_gbs(),
         }
     elif not args.skip_e2e:
         if native:
@@ -739,6 +755,7 @@ def gpu_arm(args, w, desc, rank, world):
             "d2h_bytes_per_step": d2h,
             "host_link_gbs": (h2d + d2h) * e_steps / h_s / 1e9,
             "ms_per_step": 1e3 * h_s / e_steps,
+            "host_memcpy_gbs": host_memcpy_gbs(),
         }
 
     # ---- parity spot check of the last step (resident outputs), sampled rows
