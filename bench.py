@@ -69,7 +69,7 @@ def parse():
     p.add_argument("--repeats", type=int, default=3, help="serving and stress: runs per load point")
     p.add_argument("--duration", type=float, default=10.0,
                    help="stress: seconds of arrivals per load point (the configuration's is 60)")
-    p.add_argument("--path", choices=["split3", "split3_wide", "fma"], default=None,
+    p.add_argument("--path", choices=["split3", "split3_wide", "split3_tma", "fma"], default=None,
                    help="SGEMM arithmetic and tile form (default: the autotuner's split3 form)")
     p.add_argument("--mode", choices=["barrier", "continuous"], default="barrier")
     p.add_argument("--skip-e2e", action="store_true")
@@ -209,7 +209,7 @@ def peaks():
 
 # The sources the scheduler kernels are compiled from (host code does not
 # change their DRAM traffic per tile).
-KERNEL_SOURCES = ("gvm_sched.cu", "gvm_fused.cuh", "gvm_wide.cuh", "gvm_device.cuh", "gvm_internal.h")
+KERNEL_SOURCES = ("gvm_sched.cu", "gvm_fused.cuh", "gvm_wide.cuh", "gvm_tma.cuh", "gvm_device.cuh", "gvm_internal.h")
 
 
 def kernel_source_hash():
@@ -796,7 +796,7 @@ def gpu_arm(args, w, desc, rank, world):
     kmean = statistics.mean(t_kernel)
     if w.tasks[0].kind == synth.TASK_SGEMM:
         flops = sum(s.flops for s in w.tasks)
-        if args.path in ("split3", "split3_wide"):
+        if args.path in ("split3", "split3_wide", "split3_tma"):
             peak = pk["bf16_tflops"] / 3.0
             roof = {"bound": "tensor", "unit": "TFLOP/s",
                     "peak_basis": f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"}
@@ -810,7 +810,8 @@ def gpu_arm(args, w, desc, rank, world):
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "unit": "GB/s", "peak_basis": f"HBM copy {pk['hbm_gbs']} GB/s ({pk_kind})"}
         achieved = byts / kmean / 1e9
-    kname = {"split3": "sched_fused_kernel", "split3_wide": "sched_wide_kernel"}.get(args.path, "sched_fma_kernel")
+    kname = {"split3": "sched_fused_kernel", "split3_wide": "sched_wide_kernel",
+             "split3_tma": "sched_tma_kernel"}.get(args.path, "sched_fma_kernel")
     key = f"{kname}/{args.workload}"
     roof.update({"kernel": f"gvm::{kname}", "achieved": achieved, "peak": peak,
                  "frac": achieved / peak, "traffic": ncu_traffic(key), "launch_ms": kmean * 1e3})
@@ -948,7 +949,8 @@ def resident_leg(args, w, inputs, path, steps, warmup, label):
         roof = {"bound": "hbm", "unit": "GB/s", "peak_basis": f"HBM copy {pk['hbm_gbs']} GB/s ({pk_kind})",
                 "bytes_per_launch": byts}
         achieved = byts / kmean / 1e9
-    kname = {"fma": "sched_fma_kernel", "split3_wide": "sched_wide_kernel"}.get(path, "sched_fused_kernel")
+    kname = {"fma": "sched_fma_kernel", "split3_wide": "sched_wide_kernel",
+             "split3_tma": "sched_tma_kernel"}.get(path, "sched_fused_kernel")
     roof.update({"kernel": f"gvm::{kname}", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "traffic": ncu_traffic(f"{kname}/{label}"), "launch_ms": kmean * 1e3})
     return {
@@ -1854,8 +1856,10 @@ def grouped_arm(args):
         "roofline": {"bound": bound, "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                      "peak_basis": basis,
                      "kernel": "gvm::" + {"split3": "sched_fused_kernel",
-                                          "split3_wide": "sched_wide_kernel"}.get(args.path, "sched_fma_kernel"),
-                     "traffic": ncu_traffic({"split3": "sched_fused_kernel", "split3_wide": "sched_wide_kernel"}.get(
+                                          "split3_wide": "sched_wide_kernel",
+                                          "split3_tma": "sched_tma_kernel"}.get(args.path, "sched_fma_kernel"),
+                     "traffic": ncu_traffic({"split3": "sched_fused_kernel", "split3_wide": "sched_wide_kernel",
+                                             "split3_tma": "sched_tma_kernel"}.get(
                          args.path, "sched_fma_kernel") + "/grouped") if (R, P) == (64, 256) else None,
                      "launch_ms": kmean * 1e3},
         "sched_timeline_last_launch": {

@@ -81,6 +81,11 @@ extern "C" {
 #define GVM_SGEMM_SPLIT3_WIDE 4 /* split during staging on 256 x 256 tiles of one CTA (the
                               two 128-row halves share each B stage; one accumulator);
                               bit-identical to GVM_SGEMM_SPLIT3. Also a manager path */
+#define GVM_SGEMM_SPLIT3_TMA 5 /* manager path only: 128 x 256 tiles whose binary32 A and B
+                              arrive by TMA boxes (a tensor map of each per task, where A
+                              and B are 16-byte aligned with row pitches of 16-byte
+                              multiples; other tasks are loaded by the converting warps)
+                              and are split in place; bit-identical to GVM_SGEMM_SPLIT3 */
 
 /* ---- manager modes ------------------------------------------------------ */
 #define GVM_MODE_BARRIER 0    /* Section 5 request barrier: gvm_flush runs the scheduler
@@ -109,7 +114,8 @@ typedef struct gvm_config {
   int32_t ring_depth;     /* task descriptors per rank; power of two, 2 .. 4096 */
   int32_t mode;           /* GVM_MODE_BARRIER, GVM_MODE_CONTINUOUS, GVM_MODE_PS1 or
                              GVM_MODE_PS2 */
-  int32_t sgemm_path;     /* GVM_SGEMM_FMA, GVM_SGEMM_SPLIT3 or GVM_SGEMM_SPLIT3_WIDE */
+  int32_t sgemm_path;     /* GVM_SGEMM_FMA, GVM_SGEMM_SPLIT3, GVM_SGEMM_SPLIT3_WIDE or
+                             GVM_SGEMM_SPLIT3_TMA */
   void* arena;            /* caller-owned device memory, 256-byte aligned. Split into
                              max_ranks equal slices (Section 5: one memory object per
                              process, so data of different processes coexist safely) */

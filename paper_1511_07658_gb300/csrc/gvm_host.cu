@@ -158,7 +158,8 @@ bool cfg_valid(const gvm_config* c) {
   if (c->mode != GVM_MODE_BARRIER && c->mode != GVM_MODE_CONTINUOUS && c->mode != GVM_MODE_PS1 &&
       c->mode != GVM_MODE_PS2)
     return false;
-  if (c->sgemm_path != GVM_SGEMM_FMA && c->sgemm_path != GVM_SGEMM_SPLIT3 && c->sgemm_path != GVM_SGEMM_SPLIT3_WIDE)
+  if (c->sgemm_path != GVM_SGEMM_FMA && c->sgemm_path != GVM_SGEMM_SPLIT3 && c->sgemm_path != GVM_SGEMM_SPLIT3_WIDE &&
+      c->sgemm_path != GVM_SGEMM_SPLIT3_TMA)
     return false;
   return true;
 }
@@ -393,9 +394,9 @@ int ps_issue_comp(gvm_rank* r, uint64_t s) {
   } else {
     // The fused split3 form needs no scratch and computes the same tiles as
     // the scheduler's split3 path.
-    const int path = ctx->path == kPathSplit3       ? GVM_SGEMM_SPLIT3_FUSED
-                     : ctx->path == kPathSplit3Wide ? GVM_SGEMM_SPLIT3_WIDE
-                                                    : GVM_SGEMM_FMA;
+    const int path = (ctx->path == kPathSplit3 || ctx->path == kPathSplit3Tma) ? GVM_SGEMM_SPLIT3_FUSED
+                     : ctx->path == kPathSplit3Wide                             ? GVM_SGEMM_SPLIT3_WIDE
+                                                                                : GVM_SGEMM_FMA;
     rc = gvm_sgemm_f32(A, B, C, b.m, (int32_t)b.n, b.k, path, nullptr, 0, r->in_stream);
   }
   if (rc == GVM_OK) ctx->launches.fetch_add(1);
@@ -531,6 +532,7 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   ctx->L = L;
   ctx->path = cfg.sgemm_path == GVM_SGEMM_SPLIT3        ? kPathSplit3
               : cfg.sgemm_path == GVM_SGEMM_SPLIT3_WIDE ? kPathSplit3Wide
+              : cfg.sgemm_path == GVM_SGEMM_SPLIT3_TMA  ? kPathSplit3Tma
                                                         : kPathFma;
   ctx->slice_bytes = slice;
   ctx->device = dev;
@@ -786,13 +788,19 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
     body->n = t->n;
     // Split3: fused tiles (the bf16 split happens in the tile itself),
     // 128 x 256 or, in the wide form, 256 x 256.
-    const int tm = ctx->path == kPathSplit3 ? kTcM : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
-    const int tn = ctx->path == kPathSplit3 ? kTcN : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
+    const bool tiles128 = ctx->path == kPathSplit3 || ctx->path == kPathSplit3Tma;
+    const int tm = tiles128 ? kTcM : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
+    const int tn = tiles128 ? kTcN : ctx->path == kPathSplit3Wide ? 256 : kFmaTile;
     if (ctx->path != kPathFma) body->flags |= kFlagSplit3;
     // Wide tiles land A by TMA: the task's own map of A at its device address.
     if (ctx->path == kPathSplit3Wide &&
         encode_wide_a_map(reinterpret_cast<const float*>(da), t->m, t->k, &body->tmA) == CUDA_SUCCESS)
       body->flags |= kFlagTmA;
+    // The TMA form lands A and B by TMA: the task's own maps of both.
+    if (ctx->path == kPathSplit3Tma &&
+        encode_tma_maps(reinterpret_cast<const float*>(da), reinterpret_cast<const float*>(db), t->m, t->n, t->k,
+                        &body->tmA, &body->tmB) == CUDA_SUCCESS)
+      body->flags |= kFlagTmA | kFlagTmB;
     body->tiles_m = (uint32_t)((t->m + tm - 1) / tm);
     body->tiles_n = (uint32_t)((t->n + tn - 1) / tn);
     body->ntiles = body->tiles_m * body->tiles_n;

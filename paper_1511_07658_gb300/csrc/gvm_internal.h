@@ -31,7 +31,8 @@ enum : uint32_t {
   kFlagNeedsD2H = 2u,     // host-mode output: the output stream copies and completes
   kFlagSplit3 = 4u,       // SGEMM on the split-bf16 tensor-core path
   kFlagDirectOut = 8u,    // host-mode output written by the kernel into host memory
-  kFlagTmA = 16u,         // wide split3: tmA maps A in 256-row x 32-value boxes (ingest copies it)
+  kFlagTmA = 16u,         // wide / TMA split3: tmA maps A (ingest copies it)
+  kFlagTmB = 32u,         // TMA split3: tmB maps B in 32-row x 32-value boxes (ingest copies it)
 };
 
 // Device status words (written to HostShared::status with the place in `where`).
@@ -56,8 +57,8 @@ constexpr uint32_t kClaimLocked = 0x40000000u;  // claim counter while a slot is
 // ---- task body: written by the host into its ring, copied by the device ----
 // 384 bytes; the two tensor maps must stay 64-byte aligned (they are at 0, 128).
 struct alignas(128) TaskBody {
-  CUtensorMap tmA;  // wide split3 with kFlagTmA: binary32 A (m x k), box {kTcBK, 256}
-  CUtensorMap tmB;  // split3: bf16 planes [2][n][kp] of B^T, box {kTcBK, kTcN, 1}
+  CUtensorMap tmA;  // kFlagTmA: binary32 A (m x k), box {kTcBK, 256} (wide) or {kTcBK, 128} (TMA form)
+  CUtensorMap tmB;  // kFlagTmB: binary32 B (k x n), box {32, kTcBK}
   uint32_t type;
   uint32_t flags;
   uint32_t rank;

@@ -10,7 +10,7 @@
 
 namespace gvm {
 
-enum : int { kPathFma = 0, kPathSplit3 = 1, kPathSplit3Wide = 2 };
+enum : int { kPathFma = 0, kPathSplit3 = 1, kPathSplit3Wide = 2, kPathSplit3Tma = 3 };
 
 // Driver entry points, resolved once through the runtime (no link-time libcuda).
 struct DriverApi {
@@ -39,6 +39,13 @@ CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUten
 // landing buffers; an error where TMA cannot address A (k not a multiple of
 // 4, A not 16-byte aligned).
 CUresult encode_wide_a_map(const float* A, int32_t m, int32_t k, CUtensorMap* tm);
+
+// Tensor maps of a row-major binary32 A (m x k) in boxes of 128 rows x 32
+// values and B (k x n) in boxes of 32 rows x 32 values, for the TMA-fed
+// split3 form; an error where TMA cannot address them (pitch not a multiple
+// of 16 bytes, base not 16-byte aligned).
+CUresult encode_tma_maps(const float* A, const float* B, int32_t m, int64_t n, int32_t k, CUtensorMap* tmA,
+                         CUtensorMap* tmB);
 
 // Scheduler kernel: occupancy-derived grid for `path`, dynamic smem bytes,
 // and an asynchronous launch on `stream`.

@@ -36,6 +36,7 @@
 
 #include "gvm_fused.cuh"
 #include "gvm_runtime.h"
+#include "gvm_tma.cuh"
 #include "gvm_wide.cuh"
 
 namespace gvm {
@@ -185,12 +186,14 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
         uint4* dst = reinterpret_cast<uint4*>(&dt->body) + kFieldsAt;
 #pragma unroll
         for (int j = 0; j < 8; ++j) st_cg_v4(dst + j, v[j]);
-        if (flags & kFlagTmA) {  // the A tensor map (the descriptor's first 128 bytes)
-          static_assert(offsetof(TaskBody, tmA) == 0 && sizeof(CUtensorMap) == 128, "TaskBody tmA");
+        if (flags & (kFlagTmA | kFlagTmB)) {  // the tensor maps (the descriptor's first 128 or 256 bytes)
+          static_assert(offsetof(TaskBody, tmA) == 0 && offsetof(TaskBody, tmB) == 128 &&
+                            sizeof(CUtensorMap) == 128, "TaskBody maps");
           const uint4* m_src = reinterpret_cast<const uint4*>(&p.host_desc[idx]);
           uint4* m_dst = reinterpret_cast<uint4*>(&dt->body);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) st_cg_v4(m_dst + j, ld_volatile_v4(m_src + j));
+          const int nv = (flags & kFlagTmB) ? 16 : 8;
+#pragma unroll 1
+          for (int j = 0; j < nv; ++j) st_cg_v4(m_dst + j, ld_volatile_v4(m_src + j));
         }
         const uint32_t tag = v[1].x;
         const uint32_t ntiles = v[1].y;
@@ -724,9 +727,14 @@ __device__ void conv_item_done(const SchedParams& p, Sh& sh, uint32_t seq, uint3
 }
 
 // The split3 scheduler CTA for either tile form (kWide: 256 x 256 tiles).
-template <bool kWide>
+enum : int { kFormFused = 0, kFormWide = 1, kFormTma = 2 };
+
+template <int kForm>
 __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
-  using Pipe = typename std::conditional<kWide, WdShared, FzShared>::type;
+  constexpr bool kWide = kForm == kFormWide;
+  constexpr bool kTma = kForm == kFormTma;
+  using Pipe = typename std::conditional<kWide, WdShared,
+                                         typename std::conditional<kTma, TmShared, FzShared>::type>::type;
   __shared__ TensorSchedShared<Pipe> sh;
   extern __shared__ uint8_t dyn_smem[];
   uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
@@ -739,7 +747,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
     for (int i = 0; i < kFinSlots; ++i) sh.fin[i] = 0;
     for (int i = 0; i < kFzItems; ++i) {
       mbar_init(&sh.item_full[i], 1);
-      mbar_init(&sh.item_empty[i], kFzConvWarps + 1);
+      mbar_init(&sh.item_empty[i], kFzConvWarps + (kTma ? 2 : 1));  // converters, MMA (and producer)
     }
     cl->has_resv = 0;
     cl->stall_since = 0;
@@ -749,6 +757,8 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
   // initialises the pipeline barriers, fences all inits, allocates TMEM
   if constexpr (kWide)
     wd_init(&sh.fz);
+  else if constexpr (kTma)
+    tm_init(&sh.fz);
   else
     fz_init(&sh.fz);
 
@@ -821,6 +831,11 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
                       &sh.prof[kProfMmaWait])
                    ? 1u
                    : 0u;
+        else if constexpr (kTma)
+          ok = tm_mma(t, stages, &sh.fz, it_k, tile_no, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+                      &sh.prof[kProfMmaWait])
+                   ? 1u
+                   : 0u;
         else
           ok = fz_mma(t, stages, &sh.fz, it_k, tile_no, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
                       &sh.prof[kProfMmaWait])
@@ -833,6 +848,51 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
       }
       it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
       ++tile_no;
+    }
+  } else if (kTma && warp == kTmProducerWarp) {
+    // ---- producer (TMA form): every GEMM item's k-steps, in order, get
+    // their stage once the MMAs release it, with the tensor copies of A and
+    // B when the task has maps.
+    if constexpr (kTma) {
+      uint32_t it_k = 0, pend[kTcStages] = {0, 0, 0, 0};
+      for (uint32_t seq = 0;; ++seq) {
+        const uint32_t slot = seq % kFzItems, ph = (seq / kFzItems) & 1u;
+        if (!mbar_wait(&sh.item_full[slot], ph, p.wait_timeout_ns, &sh.abort)) {
+          if (lane == 0 && !sh.abort) cta_fail(p, sh, kWhereItemWait, seq);
+          break;
+        }
+        const FzItem& item = sh.items[slot];
+        const uint32_t kind = item.kind;
+        const FzTile t{reinterpret_cast<const float*>(item.a), reinterpret_cast<const float*>(item.b),
+                       reinterpret_cast<float*>(item.c), item.n, item.m, item.k,
+                       (int)(kind == kTaskSgemm ? item.tile / item.tiles_n : 0),
+                       (int)(kind == kTaskSgemm ? item.tile % item.tiles_n : 0)};
+        const bool maps = (item.flags & (kFlagTmA | kFlagTmB)) == (kFlagTmA | kFlagTmB);
+        const CUtensorMap* tmA = maps ? reinterpret_cast<const CUtensorMap*>(item.tma) : nullptr;
+        const CUtensorMap* tmB = maps ? reinterpret_cast<const CUtensorMap*>(item.tma + sizeof(CUtensorMap)) : nullptr;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
+        if (kind == kItemExit) break;
+        if (kind != kTaskSgemm) continue;
+        uint32_t ok = 1;
+        if (lane == 0) {
+          if (tmA != nullptr) {
+            // The maps were written by the ingest's generic stores.
+            fence_tensormap_acquire(tmA);
+            fence_tensormap_acquire(tmB);
+          }
+          ok = tm_produce(t, stages, &sh.fz, it_k, tmA, tmB, p.wait_timeout_ns, &sh.abort, &sh.fail_where, pend)
+                   ? 1u
+                   : 0u;
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          if (lane == 0) report_error(p, kStatusTimeout, sh.fail_where, seq);
+          break;
+        }
+        it_k += (uint32_t)((t.k + kTcBK - 1) / kTcBK);
+      }
+      if (lane == 0) tm_quiesce(&sh.fz, pend, p.wait_timeout_ns);
+      __syncwarp();
     }
   } else if (warp < kFzConvWarps) {
     // ---- converters: stage GEMM tiles; after staging tile T, count tile
@@ -868,6 +928,8 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
       bool drained;
       if constexpr (kWide)
         drained = wd_epilogue(pt, &sh.fz, no, p.wait_timeout_ns, &sh.abort, &sh.fail_where);
+      else if constexpr (kTma)
+        drained = fz_epilogue(pt, &sh.fz.fz, no, p.wait_timeout_ns, &sh.abort, &sh.fail_where);
       else
         drained = fz_epilogue(pt, &sh.fz, no, p.wait_timeout_ns, &sh.abort, &sh.fail_where);
       if (!drained) return false;
@@ -909,6 +971,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
       if (kind == kTaskSgemm) {
         const FzTile t = tile_of(item);
         const CUtensorMap* tma = kWide ? reinterpret_cast<const CUtensorMap*>(item.tma) : nullptr;
+        const uint32_t item_flags = item.flags;
         __syncwarp();
         if (lane == 0) {
           // The item's sequence number names its finish counter.
@@ -928,6 +991,14 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
                           land_n, land_iss, tma);
           if (ok) ok = drain();  // the group had no k-step of T
           if (ok) count_done();
+        } else if constexpr (kTma) {
+          const bool landed = (item_flags & (kFlagTmA | kFlagTmB)) == (kFlagTmA | kFlagTmB);
+          ok = tm_convert(t, stages, &sh.fz, it_k, landed, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
+                          tid == 0 ? &sh.prof[kProfStageWait] : nullptr);
+          if (ok) {
+            count_done();
+            ok = drain();
+          }
         } else {
           ok = fz_convert<true>(t, stages, &sh.fz, it_k, p.wait_timeout_ns, &sh.abort, &sh.fail_where,
                                 tid == 0 ? &sh.prof[kProfStageWait] : nullptr);
@@ -967,21 +1038,27 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
   }
   if constexpr (kWide)
     wd_teardown(&sh.fz);
+  else if constexpr (kTma)
+    fz_teardown(&sh.fz.fz);
   else
     fz_teardown(&sh.fz);
   if (tid == 0) sched_exit(p, sh.prof);
 }
 
 __global__ void __launch_bounds__(kFzThreads, 1) sched_fused_kernel(const SchedParams p) {
-  sched_tc_body<false>(p);
+  sched_tc_body<kFormFused>(p);
 }
 
 __global__ void __launch_bounds__(kFzThreads, 1) sched_wide_kernel(const SchedParams p) {
-  sched_tc_body<true>(p);
+  sched_tc_body<kFormWide>(p);
+}
+
+__global__ void __launch_bounds__(kTmThreads, 1) sched_tma_kernel(const SchedParams p) {
+  sched_tc_body<kFormTma>(p);
 }
 
 static size_t dyn_smem_bytes(int path) {
-  if (path == kPathSplit3) return (size_t)kTcStages * kTcStageBytes + 1024;
+  if (path == kPathSplit3 || path == kPathSplit3Tma) return (size_t)kTcStages * kTcStageBytes + 1024;
   if (path == kPathSplit3Wide) return (size_t)kWdSmemBytes + 1024;
   return sizeof(FmaSmem) + 1024;
 }
@@ -989,10 +1066,13 @@ static size_t dyn_smem_bytes(int path) {
 static const void* sched_fn(int path) {
   if (path == kPathSplit3) return (const void*)sched_fused_kernel;
   if (path == kPathSplit3Wide) return (const void*)sched_wide_kernel;
+  if (path == kPathSplit3Tma) return (const void*)sched_tma_kernel;
   return (const void*)sched_fma_kernel;
 }
 
-static int sched_threads(int path) { return path == kPathFma ? kThreads : kFzThreads; }
+static int sched_threads(int path) {
+  return path == kPathFma ? kThreads : path == kPathSplit3Tma ? kTmThreads : kFzThreads;
+}
 
 cudaError_t scheduler_setup(int path, int* blocks_per_sm, size_t* smem_bytes) {
   const size_t smem = dyn_smem_bytes(path);
@@ -1012,6 +1092,8 @@ cudaError_t launch_scheduler(int path, const SchedParams& p, int grid, size_t sm
     sched_fused_kernel<<<grid, kFzThreads, smem, stream>>>(p);
   } else if (path == kPathSplit3Wide) {
     sched_wide_kernel<<<grid, kFzThreads, smem, stream>>>(p);
+  } else if (path == kPathSplit3Tma) {
+    sched_tma_kernel<<<grid, kTmThreads, smem, stream>>>(p);
   } else {
     sched_fma_kernel<<<grid, kThreads, smem, stream>>>(p);
   }

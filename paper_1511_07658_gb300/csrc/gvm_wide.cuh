@@ -100,11 +100,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
-  uint4 v;
-  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
-  return v;
-}
 
 // Thread (w, lane) of a group stages k-step kb of a wide tile:
 //   A item j (j = 0..7): row 8 w + (lane >> 2) + 32 j, 8 values from k = 32 kb + 8 (lane & 3);

@@ -25,6 +25,7 @@ from ._abi import (
     GVM_SGEMM_SPLIT3,
     GVM_SGEMM_SPLIT3_FUSED,
     GVM_SGEMM_SPLIT3_PAIR,
+    GVM_SGEMM_SPLIT3_TMA,
     GVM_SGEMM_SPLIT3_WIDE,
     GVM_TASK_RESIDENT,
     GVM_TASK_SGEMM,
@@ -43,6 +44,7 @@ _PATHS = {
     "split3_fused": GVM_SGEMM_SPLIT3_FUSED,
     "split3_pair": GVM_SGEMM_SPLIT3_PAIR,
     "split3_wide": GVM_SGEMM_SPLIT3_WIDE,
+    "split3_tma": GVM_SGEMM_SPLIT3_TMA,
 }
 _MODES = {"barrier": GVM_MODE_BARRIER, "continuous": GVM_MODE_CONTINUOUS, "ps1": GVM_MODE_PS1, "ps2": GVM_MODE_PS2}
 

@@ -94,14 +94,14 @@ def test_vadd_tiny_config_bitexact(gvm, mode):
     run_workload(gvm, synth.vadd_tiny(), mode=mode)
 
 
-@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide", "split3_tma"])
 def test_sgemm_shared_subset(gvm, path):
     """16 ranks sharing the GPU, SGEMM 512^3 (two tasks per rank here; the
     full 64-per-rank configuration runs in test_gpu_sizes)."""
     run_workload(gvm, synth.sgemm_square(ranks=16, per_rank=2), path=path, slice_mb=64)
 
 
-@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide", "split3_tma"])
 def test_mixed_ragged_tasks(gvm, path):
     w = synth.Workload("mixed", 3)
     shapes = [(1, 1, 1), (64, 64, 64), (130, 257, 65), (5, 300, 17)]
@@ -118,7 +118,7 @@ def test_mixed_ragged_tasks(gvm, path):
 
 
 @pytest.mark.parametrize("mode", ["barrier", "continuous"])
-@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide", "split3_tma"])
 def test_vmul_tasks_in_mix(gvm, mode, path):
     """Vector-multiply tasks (the paper's VecMult, 15 products) shared with
     vector adds and matrix multiplies, ragged lengths, host mode."""
@@ -175,7 +175,7 @@ def _ps_mix():
 
 
 @pytest.mark.parametrize("mode", ["ps1", "ps2"])
-@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide", "split3_tma"])
 def test_paper_stream_modes(gvm, mode, path):
     """PS-1 / PS-2 (the host issues each task's copies and kernel at the
     request barrier): oracle parity, and bitwise the same results as the
@@ -281,7 +281,7 @@ def test_paper_stream_modes_barrier_rules(gvm, mode):
     assert np.array_equal(bits(out2.numpy()), bits(oracle.vmul(a, b, 15)))
 
 
-@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide"])
+@pytest.mark.parametrize("path", ["fma", "split3", "split3_wide", "split3_tma"])
 def test_solo_equals_mix_bitwise(gvm, path):
     """A task's result alone on the GPU equals its result in the mix, bit for
     bit (the tile shape is a function of the task's shape only)."""
@@ -643,7 +643,8 @@ def test_batch_from_contiguous_host_blocks(gvm, slice_mb):
 
 
 @pytest.mark.parametrize("mode,path", [("barrier", "split3"), ("continuous", "split3"), ("barrier", "fma"),
-                                       ("barrier", "split3_wide"), ("continuous", "split3_wide")])
+                                       ("barrier", "split3_wide"), ("continuous", "split3_wide"),
+                                       ("barrier", "split3_tma"), ("continuous", "split3_tma")])
 def test_stress_mix_ragged_sizes(gvm, mode, path):
     # The stress config's shape mix (70% vector adds with lognormal lengths,
     # 30% square SGEMMs with lognormal sides; most sizes odd, none aligned)
@@ -708,3 +709,23 @@ def test_continuous_solo_equals_mix_bitwise(gvm):
         inputs = (synth.vadd_inputs(spec.seed, spec.n) if spec.kind == synth.TASK_VADD
                   else synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k))
         check_result(spec, inputs, mix_out[(spec.rank, spec.index)])
+
+
+@pytest.mark.parametrize("mode", ["barrier", "continuous"])
+def test_tma_form_equals_fused_bitwise(gvm, mode):
+    """The TMA form (binary32 A and B landed by tensor copies, split in place;
+    tasks without maps staged by the converting warps' own loads) computes
+    every element as the fused form does: equal bit for bit, on interior and
+    ragged tiles, k below one k-step, k and n not multiples of 4 (no maps),
+    several tiles per CTA, and within the SGEMM rule against the oracle."""
+    shapes = [(512, 512, 512), (128, 256, 32), (130, 260, 100), (300, 1000, 160), (257, 384, 200),
+              (64, 700, 33), (1, 257, 31), (200, 192, 96), (1000, 520, 2052), (129, 257, 513), (256, 128, 4),
+              (384, 640, 44), (640, 768, 1024)]
+    w = synth.Workload("tma", 2)
+    for i, (m, n, k) in enumerate(shapes):
+        w.tasks.append(synth.TaskSpec(i % 2, i // 2, synth.TASK_SGEMM, m=m, n=n, k=k, seed=synth.task_seed(21, i)))
+    fused = run_workload(gvm, w, mode=mode, path="split3", slice_mb=256)
+    tma = run_workload(gvm, w, mode=mode, path="split3_tma", slice_mb=256)
+    for spec in w.tasks:
+        key = (spec.rank, spec.index)
+        assert np.array_equal(bits(tma[key].numpy()), bits(fused[key].numpy())), spec
