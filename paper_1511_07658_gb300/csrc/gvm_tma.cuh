@@ -42,6 +42,8 @@ constexpr uint32_t kTmBOff = kTcM * kTcBK * 4;           // B's eight boxes star
 constexpr uint32_t kTmBBox = kTcBK * 32 * 4;             // one B box: 32 k-rows x 32 columns
 constexpr uint32_t kTmAtoms = (kTcM + kTcN) * kTcBK * 4 / kTmAtom;  // 48 atoms a k-step
 constexpr uint32_t kTmStageTx = (kTcM + kTcN) * kTcBK * 4;          // 48 KB of boxes a k-step
+constexpr int kTmBatch = 4;  // atoms a converter warp reads before it writes (12 = 3 batches a k-step)
+static_assert(kTmAtoms % (kFzGroupWarps * kTmBatch) == 0, "whole batches");
 static_assert(kTmStageTx == kTcStageBytes, "TMA form stage = fused stage");
 
 struct TmShared {
@@ -133,25 +135,35 @@ __device__ __forceinline__ bool tm_convert(const FzTile& t, uint8_t* stages, TmS
     }
     if (t0) *wait_acc += globaltimer() - t0;
     const uint32_t st = base0 + s * kTcStageBytes;
+    // A warp's 12 atoms in batches of kTmBatch: all the batch's reads go out
+    // together (their latencies overlap), then its splits and writes.
 #pragma unroll 1
-    for (int a = w; a < (int)kTmAtoms; a += kFzGroupWarps) {
-      const uint32_t atom = st + tm_atom_off(a);
-      float v[8];
-      if (landed) {
-        const uint4 x0 = ld_shared_v4(atom + rd + sw), x1 = ld_shared_v4(atom + rd + (sw ^ 16u));
-        const uint4 lo4 = sw ? x1 : x0, hi4 = sw ? x0 : x1;
-        v[0] = __uint_as_float(lo4.x); v[1] = __uint_as_float(lo4.y);
-        v[2] = __uint_as_float(lo4.z); v[3] = __uint_as_float(lo4.w);
-        v[4] = __uint_as_float(hi4.x); v[5] = __uint_as_float(hi4.y);
-        v[6] = __uint_as_float(hi4.z); v[7] = __uint_as_float(hi4.w);
-      } else {
-        tm_atom_load(t, kb, a, lane, v);
+    for (int a0 = w; a0 < (int)kTmAtoms; a0 += kFzGroupWarps * kTmBatch) {
+      float v[kTmBatch][8];
+#pragma unroll
+      for (int i = 0; i < kTmBatch; ++i) {
+        const int a = a0 + i * kFzGroupWarps;
+        const uint32_t atom = st + tm_atom_off(a);
+        if (landed) {
+          const uint4 x0 = ld_shared_v4(atom + rd + sw), x1 = ld_shared_v4(atom + rd + (sw ^ 16u));
+          const uint4 lo4 = sw ? x1 : x0, hi4 = sw ? x0 : x1;
+          v[i][0] = __uint_as_float(lo4.x); v[i][1] = __uint_as_float(lo4.y);
+          v[i][2] = __uint_as_float(lo4.z); v[i][3] = __uint_as_float(lo4.w);
+          v[i][4] = __uint_as_float(hi4.x); v[i][5] = __uint_as_float(hi4.y);
+          v[i][6] = __uint_as_float(hi4.z); v[i][7] = __uint_as_float(hi4.w);
+        } else {
+          tm_atom_load(t, kb, a, lane, v[i]);
+        }
       }
-      uint4 hi, lo;
-      split8_x2(v, hi, lo);
-      __syncwarp();  // every lane has read the atom's binary32 before any lane overwrites it
-      st_shared_v4(atom + wr, hi);
-      st_shared_v4(atom + 512u + wr, lo);
+      __syncwarp();  // every lane has read the batch's binary32 before any lane overwrites it
+#pragma unroll
+      for (int i = 0; i < kTmBatch; ++i) {
+        const uint32_t atom = st + tm_atom_off(a0 + i * kFzGroupWarps);
+        uint4 hi, lo;
+        split8_x2(v[i], hi, lo);
+        st_shared_v4(atom + wr, hi);
+        st_shared_v4(atom + 512u + wr, lo);
+      }
     }
     fence_proxy_async_shared();
     __syncwarp();
