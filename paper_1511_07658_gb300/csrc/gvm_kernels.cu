@@ -333,8 +333,8 @@ CUresult encode_wide_a_map(const float* A, int32_t m, int32_t k, CUtensorMap* tm
 CUresult encode_tma_maps(const float* A, const float* B, int32_t m, int64_t n, int32_t k, CUtensorMap* tmA,
                          CUtensorMap* tmB) {
   // A: boxes of 128 rows x 32 values; B: boxes of 32 rows (k) x 32 columns.
-  // Each lands densely (128-byte rows) in shared memory; elements beyond the
-  // matrix read as zero.
+  // Each lands as 128-byte rows with the 128-byte swizzle (16-byte chunk j of
+  // row r at chunk j ^ (r % 8)); elements beyond the matrix read as zero.
   if ((k % 4) != 0 || (n % 4) != 0 || ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) != 0)
     return CUDA_ERROR_INVALID_VALUE;
   const DriverApi* api = driver_api();
@@ -345,7 +345,7 @@ CUresult encode_tma_maps(const float* A, const float* B, int32_t m, int64_t n, i
     const cuuint64_t strides[1] = {(cuuint64_t)k * 4};
     const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcM};
     CUresult r = api->encode_tiled(tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box,
-                                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return r;
   }
@@ -353,7 +353,7 @@ CUresult encode_tma_maps(const float* A, const float* B, int32_t m, int64_t n, i
   const cuuint64_t strides[1] = {(cuuint64_t)n * 4};
   const cuuint32_t box[2] = {32, (cuuint32_t)kTcBK};
   return api->encode_tiled(tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(B), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 

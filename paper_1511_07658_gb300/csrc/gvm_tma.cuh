@@ -9,12 +9,14 @@
 // landed where it lies.
 //
 // Stage layout (48 KB, four stages, the fused form's size): a k-step of A
-// is one TMA box of 128 rows x 32 binary32 values, landing densely (row r at
-// 128 r); a k-step of B is eight boxes of 32 k-rows x 32 columns, box c at
-// 16 KB + 4 KB c (k-row kr at 128 kr inside it). So every 8 rows of A and
+// is one TMA box of 128 rows x 32 binary32 values, landing as 128-byte rows
+// (row r at 128 r, its 16-byte chunks swizzled: chunk j at j ^ (r % 8)); a
+// k-step of B is eight boxes of 32 k-rows x 32 columns, box c at
+// 16 KB + 4 KB c (k-row kr at 128 kr inside it, swizzled alike). So every 8 rows of A and
 // every 8 k-rows x 32 columns of B occupy 1 KB of their own: an atom. A warp
 // converts an atom in place: all lanes read its 1 KB of binary32 (lane: row
-// lane / 4, 8 values from column 8 (lane % 4)), then write the bf16 hi plane
+// lane / 4, 8 values from column 8 (lane % 4); the swizzle spreads a warp's
+// reads over all banks), then write the bf16 hi plane
 // into its first 512 bytes and the lo plane into its last 512, each in the
 // 64-byte-swizzled 8-row layout the MMA descriptors read. The descriptors
 // step 1 KB between 8-row groups (A K-major; B's k groups) and 4 KB between
@@ -109,8 +111,11 @@ __device__ __forceinline__ uint32_t tm_atom_off(int a) {
 // Converter warps: stage the k-steps of tile t that belong to this warp's
 // group (k-step q of the pipeline goes to group q % 2; `it` counts the
 // k-steps before this tile). landed: the tile's boxes arrive by TMA and are
-// split in place; otherwise the warps load the values themselves. Returns
-// false when a wait ran out (*cta_abort set).
+// split in place; otherwise the warps load the values themselves. Warp w of
+// a group takes atoms w + 4 i of each third of the k-step (A's 16 atoms,
+// then B's boxes 0-3 and 4-7: atom w of box i + 4 (third - 1)), reading a
+// third's four atoms before writing them. Returns false when a wait ran out
+// (*cta_abort set).
 __device__ __forceinline__ bool tm_convert(const FzTile& t, uint8_t* stages, TmShared* ts, uint32_t it, bool landed,
                                            uint64_t timeout_ns, volatile uint32_t* cta_abort, uint32_t* fail_where,
                                            uint64_t* wait_acc) {
@@ -118,8 +123,10 @@ __device__ __forceinline__ bool tm_convert(const FzTile& t, uint8_t* stages, TmS
   const int par = warp / kFzGroupWarps, w = warp % kFzGroupWarps;
   const int nkb = (t.k + kTcBK - 1) / kTcBK;
   const int r = lane >> 2, c = lane & 3;
-  const uint32_t sw = (r & 1) ? 16u : 0u;  // odd rows read their second 16 bytes first (banks)
-  const uint32_t rd = (uint32_t)r * 128u + (uint32_t)c * 32u;
+  // The boxes land with the 128-byte swizzle: 16-byte chunk j of row r sits
+  // at chunk j ^ r. A lane's two chunks (values 8c .. 8c+7 of row r):
+  const uint32_t rd0 = (uint32_t)r * 128u + (((uint32_t)(2 * c) ^ (uint32_t)r) << 4);
+  const uint32_t rd1 = (uint32_t)r * 128u + (((uint32_t)(2 * c + 1) ^ (uint32_t)r) << 4);
   const uint32_t wr = swz64((uint32_t)r, (uint32_t)c);
   const uint32_t base0 = smem_u32(stages);
   for (int kb = (int)((it + (uint32_t)par) & 1u); kb < nkb; kb += 2) {
@@ -135,34 +142,41 @@ __device__ __forceinline__ bool tm_convert(const FzTile& t, uint8_t* stages, TmS
     }
     if (t0) *wait_acc += globaltimer() - t0;
     const uint32_t st = base0 + s * kTcStageBytes;
-    // A warp's 12 atoms in batches of kTmBatch: all the batch's reads go out
-    // together (their latencies overlap), then its splits and writes.
-#pragma unroll 1
-    for (int a0 = w; a0 < (int)kTmAtoms; a0 += kFzGroupWarps * kTmBatch) {
-      float v[kTmBatch][8];
+    if (landed) {
 #pragma unroll
-      for (int i = 0; i < kTmBatch; ++i) {
-        const int a = a0 + i * kFzGroupWarps;
-        const uint32_t atom = st + tm_atom_off(a);
-        if (landed) {
-          const uint4 x0 = ld_shared_v4(atom + rd + sw), x1 = ld_shared_v4(atom + rd + (sw ^ 16u));
-          const uint4 lo4 = sw ? x1 : x0, hi4 = sw ? x0 : x1;
-          v[i][0] = __uint_as_float(lo4.x); v[i][1] = __uint_as_float(lo4.y);
-          v[i][2] = __uint_as_float(lo4.z); v[i][3] = __uint_as_float(lo4.w);
-          v[i][4] = __uint_as_float(hi4.x); v[i][5] = __uint_as_float(hi4.y);
-          v[i][6] = __uint_as_float(hi4.z); v[i][7] = __uint_as_float(hi4.w);
-        } else {
-          tm_atom_load(t, kb, a, lane, v[i]);
+      for (int third = 0; third < 3; ++third) {
+        uint4 x[kTmBatch][2];
+#pragma unroll
+        for (int i = 0; i < kTmBatch; ++i) {
+          const uint32_t at = st + (third == 0 ? (uint32_t)(w + 4 * i) * kTmAtom
+                                               : kTmBOff + (uint32_t)(i + 4 * (third - 1)) * kTmBBox + (uint32_t)w * kTmAtom);
+          x[i][0] = ld_shared_v4(at + rd0);
+          x[i][1] = ld_shared_v4(at + rd1);
+        }
+        __syncwarp();  // every lane has read these atoms' binary32 before any lane overwrites them
+#pragma unroll
+        for (int i = 0; i < kTmBatch; ++i) {
+          const uint32_t at = st + (third == 0 ? (uint32_t)(w + 4 * i) * kTmAtom
+                                               : kTmBOff + (uint32_t)(i + 4 * (third - 1)) * kTmBBox + (uint32_t)w * kTmAtom);
+          const float v[8] = {__uint_as_float(x[i][0].x), __uint_as_float(x[i][0].y), __uint_as_float(x[i][0].z),
+                              __uint_as_float(x[i][0].w), __uint_as_float(x[i][1].x), __uint_as_float(x[i][1].y),
+                              __uint_as_float(x[i][1].z), __uint_as_float(x[i][1].w)};
+          uint4 hi, lo;
+          split8_x2(v, hi, lo);
+          st_shared_v4(at + wr, hi);
+          st_shared_v4(at + 512u + wr, lo);
         }
       }
-      __syncwarp();  // every lane has read the batch's binary32 before any lane overwrites it
-#pragma unroll
-      for (int i = 0; i < kTmBatch; ++i) {
-        const uint32_t atom = st + tm_atom_off(a0 + i * kFzGroupWarps);
+    } else {
+      for (int j = 0; j < (int)(kTmAtoms / kFzGroupWarps); ++j) {
+        const int a = j < 4 ? w + 4 * j : 16 + 4 * (j - 4) + w;
+        float v[8];
+        tm_atom_load(t, kb, a, lane, v);
         uint4 hi, lo;
-        split8_x2(v[i], hi, lo);
-        st_shared_v4(atom + wr, hi);
-        st_shared_v4(atom + 512u + wr, lo);
+        split8_x2(v, hi, lo);
+        const uint32_t at = st + tm_atom_off(a);
+        st_shared_v4(at + wr, hi);
+        st_shared_v4(at + 512u + wr, lo);
       }
     }
     fence_proxy_async_shared();
