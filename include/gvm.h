@@ -75,9 +75,7 @@ extern "C" {
 #define GVM_SGEMM_SPLIT3_FUSED 2 /* gvm_sgemm_f32 only: the manager's form of split3 (split
                               during staging, no scratch); bit-identical to
                               GVM_SGEMM_SPLIT3 */
-#define GVM_SGEMM_SPLIT3_PAIR 3 /* gvm_sgemm_f32 only: split during staging on CTA pairs
-                              (two-SM tcgen05 MMAs, 256 x 256 tiles); the same products
-                              in the same order, bit-identical to GVM_SGEMM_SPLIT3 */
+/* 3 is not used (it named a removed form); gvm_sgemm_f32 refuses it. */
 #define GVM_SGEMM_SPLIT3_WIDE 4 /* split during staging on 256 x 256 tiles of one CTA (the
                               two 128-row halves share each B stage; one accumulator);
                               bit-identical to GVM_SGEMM_SPLIT3. Also a manager path */

@@ -27,7 +27,6 @@ GVM_TASK_RESIDENT = 1
 GVM_SGEMM_FMA = 0
 GVM_SGEMM_SPLIT3 = 1
 GVM_SGEMM_SPLIT3_FUSED = 2
-GVM_SGEMM_SPLIT3_PAIR = 3
 GVM_SGEMM_SPLIT3_WIDE = 4
 GVM_SGEMM_SPLIT3_TMA = 5
 GVM_MODE_BARRIER = 0

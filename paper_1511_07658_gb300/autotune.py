@@ -11,14 +11,16 @@ and keeps the fastest:
   one pinned block (8 steps);
 * ``vadd_tile`` (elements per vector-add tile; 0 = per task, n / CTAs): 16
   ranks x 8 resident vector adds of n = 2^22 (10 steps);
-* ``sgemm_form`` (the split3 SGEMM tile shape): fused 128 x 256 tiles
-  against wide 256 x 256 tiles of one CTA (A by TMA), per workload class:
+* ``sgemm_form`` (the split3 SGEMM tile form): fused 128 x 256 tiles
+  (operands loaded by the staging warps), the same tiles with A and B landed
+  by TMA and split in place, and wide 256 x 256 tiles of one CTA (A by TMA),
+  per workload class:
   square 512^3 (16 x 64 tasks, the headline shape), 512 x 768 x 512
   (16 x 16), 2048^3 (16 x 1) and a grouped mix of shapes drawn from
   {128, ..., 2048} (16 ranks x 16 tasks). ``sgemm_form_by_class`` keeps the
-  faster form of each class; ``sgemm_form``, the manager's default, is the
-  512^3 class's. A tile shape per task inside one launch would need both
-  forms in one kernel, whose converters then spill (measured); so the shape
+  fastest form of each class; ``sgemm_form``, the manager's default, is the
+  512^3 class's. A tile form per task inside one launch would need several
+  forms in one kernel, whose converters then spill (measured); so the form
   is chosen per manager (per workload), and a task's result is the same
   alone and in any mix (every form computes each element the same way);
 * ``l2_prefetch`` (split3: the next queued tile's operands prefetched into
@@ -40,6 +42,7 @@ from . import manager as _m
 from .manager import GVM_TASK_RESIDENT, GVM_TASK_SGEMM, GVM_TASK_VADD, GvmTask, Manager
 
 COPY_RUNS = (4 << 20, 16 << 20, 64 << 20)
+SGEMM_FORMS = ("split3", "split3_tma", "split3_wide")
 VADD_TILES = (0, 1 << 16, 1 << 18, 1 << 20)
 
 
@@ -197,9 +200,9 @@ def run(path: str = _m.TUNING_FILE) -> dict:
     form_t, pf_t = {}, {}
     for m, n, k, per in SGEMM_SHAPES:
         key = _shape_key(m, n, k)
-        form_t[key] = {f: time_sgemm(m, n, k, per_rank=per, path=f) for f in ("split3", "split3_wide")}
+        form_t[key] = {f: time_sgemm(m, n, k, per_rank=per, path=f) for f in SGEMM_FORMS}
         pf_t[key] = {str(int(on)): time_sgemm(m, n, k, per_rank=per, prefetch=on) for on in (False, True)}
-    form_t[GROUPED_CLASS] = {f: time_grouped(f) for f in ("split3", "split3_wide")}
+    form_t[GROUPED_CLASS] = {f: time_grouped(f) for f in SGEMM_FORMS}
     choice = {
         "copy_run_bytes": int(min(copy_t, key=copy_t.get)),
         "vadd_tile": int(min(vadd_t, key=vadd_t.get)),
@@ -213,7 +216,8 @@ def run(path: str = _m.TUNING_FILE) -> dict:
             "copy_run_bytes": "end-to-end leg, 16 ranks x 16 SGEMM 512^3, operands in one pinned block per rank",
             "vadd_tile": "16 ranks x 8 resident vector adds, n = 2^22",
             "sgemm_form": "resident SGEMM, 16 ranks x (64 of 512^3, 16 of 512 x 768 x 512, 1 of 2048^3, "
-                          "16 of the grouped mix): fused 128 x 256 tiles against wide 256 x 256 tiles",
+                          "16 of the grouped mix): fused 128 x 256 tiles, the same tiles landed by TMA, "
+                          "wide 256 x 256 tiles",
             "l2_prefetch": "the same SGEMM workloads, fused tiles, next-tile L2 prefetch off (0) and on (1)",
         },
     }

@@ -10,7 +10,6 @@
 #include "gvm.h"
 #include "gvm_device.cuh"
 #include "gvm_fused.cuh"
-#include "gvm_pair.cuh"
 #include "gvm_wide.cuh"
 #include "gvm_runtime.h"
 
@@ -174,65 +173,6 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     __syncwarp();
   }
   wd_teardown(&ws);
-  if (threadIdx.x == 0 && abort_flag) atomicExch(&g_kernel_status, kStatusTimeout | (fail_where << 8));
-}
-
-// Pair form: clusters of two CTAs, each pair takes 256 x 256 tiles i, i +
-// pairs, ... (row-major over the tile grid); the even CTA issues the
-// two-SM MMAs.
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFzThreads, 1)
-    pr_sgemm_kernel(const float* A, const float* B, float* C, int m, int n, int k, uint32_t nstages,
-                    uint64_t timeout_ns) {
-  __shared__ PrShared ps;
-  __shared__ uint32_t abort_flag, fail_where;
-  extern __shared__ uint8_t dyn_smem[];
-  uint8_t* big = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
-  if (threadIdx.x == 0) {
-    abort_flag = 0;
-    fail_where = 0;
-  }
-  pr_init(&ps, nstages);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
-  const int tiles_n = (n + kPrN - 1) / kPrN;
-  const int ntiles = ((m + kPrM - 1) / kPrM) * tiles_n;
-  const uint32_t nkb = (uint32_t)((k + kTcBK - 1) / kTcBK);
-  uint32_t it = 0, tile_no = 0;
-  if (warp < kFzConvWarps) {
-    uint64_t* arrive_to = ps.cta == 0 ? ps.full : ps.pfull;
-    FzTile prev{};
-    bool have_prev = false, ok = true;
-    for (int tile = pair; ok && tile < ntiles; tile += npairs) {
-      const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
-      ok = pr_convert(t, big, &ps, arrive_to, it, timeout_ns, &abort_flag, &fail_where, nullptr);
-      if (ok && have_prev) ok = pr_epilogue(prev, &ps, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
-      prev = t;
-      have_prev = true;
-      it += nkb;
-      ++tile_no;
-    }
-    if (ok && have_prev) pr_epilogue(prev, &ps, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
-  } else if (warp == kFzMmaWarp) {
-    if (lane == 0 && ps.cta == 0) {
-      for (int tile = pair; tile < ntiles; tile += npairs) {
-        const FzTile t{A, B, C, n, m, k, tile / tiles_n, tile % tiles_n};
-        if (!pr_mma(t, big, &ps, it, tile_no, timeout_ns, &abort_flag, &fail_where, nullptr)) break;
-        it += nkb;
-        ++tile_no;
-      }
-    } else if (lane == 0) {
-      bool ok = true;
-      for (int tile = pair; ok && tile < ntiles; tile += npairs) {
-        ok = pr_relay_tile(&ps, it, (int)nkb, tile_no, timeout_ns, &abort_flag, &fail_where);
-        if (ok && tile_no > 0) ok = pr_relay_drain(&ps, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
-        it += nkb;
-        ++tile_no;
-      }
-      if (ok && tile_no > 0) pr_relay_drain(&ps, tile_no - 1, timeout_ns, &abort_flag, &fail_where);
-    }
-    __syncwarp();
-  }
-  pr_teardown(&ps);
   if (threadIdx.x == 0 && abort_flag) atomicExch(&g_kernel_status, kStatusTimeout | (fail_where << 8));
 }
 
@@ -449,19 +389,6 @@ extern "C" int gvm_sgemm_f32(const float* A, const float* B, float* C, int32_t m
     const int a_tma = encode_wide_a_map(A, m, k, &tmA) == CUDA_SUCCESS ? 1 : 0;
     if (!a_tma) memset(&tmA, 0, sizeof(tmA));
     wd_sgemm_kernel<<<grid, kFzThreads, smem, s>>>(tmA, a_tma, A, B, C, m, n, k, kStandaloneTimeoutNs);
-    return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
-  }
-  if (path == GVM_SGEMM_SPLIT3_PAIR) {
-    const uint32_t nstages = kPrDefaultStages;
-    const size_t smem = (size_t)nstages * kPrStageBytes + 1024;
-    if (cudaFuncSetAttribute(pr_sgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)kPrMaxStages * kPrStageBytes + 1024)) != cudaSuccess)
-      return GVM_EDEVICE;
-    const int sms = sm_count();
-    if (sms <= 0) return GVM_ENODEV;
-    const int64_t ntiles = (int64_t)((m + kPrM - 1) / kPrM) * ((n + kPrN - 1) / kPrN);
-    const int pairs = (int)(ntiles < sms / 2 ? ntiles : sms / 2);
-    pr_sgemm_kernel<<<2 * pairs, kFzThreads, smem, s>>>(A, B, C, m, n, k, nstages, kStandaloneTimeoutNs);
     return cudaGetLastError() == cudaSuccess ? GVM_OK : GVM_EDEVICE;
   }
   if (path != GVM_SGEMM_SPLIT3) return GVM_EINVAL;

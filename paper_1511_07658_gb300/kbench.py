@@ -32,7 +32,7 @@ def _time(fn, reps=10):
     return e0.elapsed_time(e1) / reps / 1e3
 
 
-def sgemm(side: int, paths=("split3", "split3_fused", "split3_pair", "fma")) -> None:
+def sgemm(side: int, paths=("split3", "split3_fused", "split3_wide", "fma")) -> None:
     A = torch.randn(side, side, device="cuda")
     B = torch.randn(side, side, device="cuda")
     C = torch.empty(side, side, device="cuda")
@@ -117,7 +117,7 @@ def main(argv) -> None:
     elif what == "link":
         link()
     elif what.isdigit():
-        sgemm(int(what), paths=("split3", "split3_fused", "split3_pair", "split3_wide"))
+        sgemm(int(what), paths=("split3", "split3_fused", "split3_wide"))
     else:
         for side in (512, 2048, 4096):
             sgemm(side)

@@ -24,7 +24,6 @@ from ._abi import (
     GVM_SGEMM_FMA,
     GVM_SGEMM_SPLIT3,
     GVM_SGEMM_SPLIT3_FUSED,
-    GVM_SGEMM_SPLIT3_PAIR,
     GVM_SGEMM_SPLIT3_TMA,
     GVM_SGEMM_SPLIT3_WIDE,
     GVM_TASK_RESIDENT,
@@ -42,7 +41,6 @@ _PATHS = {
     "fma": GVM_SGEMM_FMA,
     "split3": GVM_SGEMM_SPLIT3,
     "split3_fused": GVM_SGEMM_SPLIT3_FUSED,
-    "split3_pair": GVM_SGEMM_SPLIT3_PAIR,
     "split3_wide": GVM_SGEMM_SPLIT3_WIDE,
     "split3_tma": GVM_SGEMM_SPLIT3_TMA,
 }
