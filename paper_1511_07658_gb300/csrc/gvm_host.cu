@@ -797,10 +797,11 @@ void fill_body(gvm_ctx* ctx, gvm_rank* r, const Prep& p, uint64_t seq, uint64_t 
         encode_wide_a_map(reinterpret_cast<const float*>(da), t->m, t->k, &body->tmA) == CUDA_SUCCESS)
       body->flags |= kFlagTmA;
     // The TMA form lands A and B by TMA: the task's own maps of both.
+    int b3 = 0;
     if (ctx->path == kPathSplit3Tma &&
         encode_tma_maps(reinterpret_cast<const float*>(da), reinterpret_cast<const float*>(db), t->m, t->n, t->k,
-                        &body->tmA, &body->tmB) == CUDA_SUCCESS)
-      body->flags |= kFlagTmA | kFlagTmB;
+                        &body->tmA, &body->tmB, &b3) == CUDA_SUCCESS)
+      body->flags |= kFlagTmA | kFlagTmB | (b3 ? kFlagTmB3 : 0u);
     body->tiles_m = (uint32_t)((t->m + tm - 1) / tm);
     body->tiles_n = (uint32_t)((t->n + tn - 1) / tn);
     body->ntiles = body->tiles_m * body->tiles_n;

@@ -33,6 +33,7 @@ enum : uint32_t {
   kFlagDirectOut = 8u,    // host-mode output written by the kernel into host memory
   kFlagTmA = 16u,         // wide / TMA split3: tmA maps A (ingest copies it)
   kFlagTmB = 32u,         // TMA split3: tmB maps B in 32-row x 32-value boxes (ingest copies it)
+  kFlagTmB3 = 64u,        // with kFlagTmB: tmB is 3D, one box lands a k-step's eight 32-column slabs
 };
 
 // Device status words (written to HostShared::status with the place in `where`).
@@ -58,7 +59,7 @@ constexpr uint32_t kClaimLocked = 0x40000000u;  // claim counter while a slot is
 // 384 bytes; the two tensor maps must stay 64-byte aligned (they are at 0, 128).
 struct alignas(128) TaskBody {
   CUtensorMap tmA;  // kFlagTmA: binary32 A (m x k), box {kTcBK, 256} (wide) or {kTcBK, 128} (TMA form)
-  CUtensorMap tmB;  // kFlagTmB: binary32 B (k x n), box {32, kTcBK}
+  CUtensorMap tmB;  // kFlagTmB: binary32 B (k x n), box {32, kTcBK}; kFlagTmB3: (32, k, n / 32), box {32, kTcBK, 8}
   uint32_t type;
   uint32_t flags;
   uint32_t rank;

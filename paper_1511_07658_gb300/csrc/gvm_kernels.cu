@@ -271,7 +271,7 @@ CUresult encode_wide_a_map(const float* A, int32_t m, int32_t k, CUtensorMap* tm
 }
 
 CUresult encode_tma_maps(const float* A, const float* B, int32_t m, int64_t n, int32_t k, CUtensorMap* tmA,
-                         CUtensorMap* tmB) {
+                         CUtensorMap* tmB, int* b3) {
   // A: boxes of 128 rows x 32 values; B: boxes of 32 rows (k) x 32 columns.
   // Each lands as 128-byte rows with the 128-byte swizzle (16-byte chunk j of
   // row r at chunk j ^ (r % 8)); elements beyond the matrix read as zero.
@@ -288,6 +288,22 @@ CUresult encode_tma_maps(const float* A, const float* B, int32_t m, int64_t n, i
                                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return r;
+  }
+  *b3 = 0;
+  if (n % 32 == 0) {
+    // B as (column within its 32-column slab, k, slab): a box of {32, kTcBK,
+    // 8} lands the eight slabs of a tile's k-step one after another, each as
+    // kTcBK rows of 128 bytes: the layout of eight 2D boxes, in one copy.
+    const cuuint64_t dims3[3] = {32, (cuuint64_t)k, (cuuint64_t)(n / 32)};
+    const cuuint64_t strides3[2] = {(cuuint64_t)n * 4, 128};
+    const cuuint32_t box3[3] = {32, (cuuint32_t)kTcBK, (cuuint32_t)(kTcN / 32)};
+    const cuuint32_t estr3[3] = {1, 1, 1};
+    if (api->encode_tiled(tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(B), dims3, strides3, box3,
+                          estr3, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+      *b3 = 1;
+      return CUDA_SUCCESS;
+    }
   }
   const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
   const cuuint64_t strides[1] = {(cuuint64_t)n * 4};

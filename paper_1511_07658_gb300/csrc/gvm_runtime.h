@@ -41,11 +41,13 @@ CUresult encode_split_maps(void* scratch, int32_t m, int64_t n, int32_t k, CUten
 CUresult encode_wide_a_map(const float* A, int32_t m, int32_t k, CUtensorMap* tm);
 
 // Tensor maps of a row-major binary32 A (m x k) in boxes of 128 rows x 32
-// values and B (k x n) in boxes of 32 rows x 32 values, for the TMA-fed
-// split3 form; an error where TMA cannot address them (pitch not a multiple
-// of 16 bytes, base not 16-byte aligned).
+// values and of B (k x n): when n is a multiple of 32, a 3D map (columns
+// within a 32-column slab, k, slabs) whose one box is a k-step's eight slabs
+// (*b3 = 1); otherwise boxes of 32 rows x 32 values (*b3 = 0). For the
+// TMA-fed split3 form; an error where TMA cannot address them (pitch not a
+// multiple of 16 bytes, base not 16-byte aligned).
 CUresult encode_tma_maps(const float* A, const float* B, int32_t m, int64_t n, int32_t k, CUtensorMap* tmA,
-                         CUtensorMap* tmB);
+                         CUtensorMap* tmB, int* b3);
 
 // Scheduler kernel: occupancy-derived grid for `path`, dynamic smem bytes,
 // and an asynchronous launch on `stream`.

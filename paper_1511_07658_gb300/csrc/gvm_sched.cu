@@ -870,6 +870,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
         const bool maps = (item.flags & (kFlagTmA | kFlagTmB)) == (kFlagTmA | kFlagTmB);
         const CUtensorMap* tmA = maps ? reinterpret_cast<const CUtensorMap*>(item.tma) : nullptr;
         const CUtensorMap* tmB = maps ? reinterpret_cast<const CUtensorMap*>(item.tma + sizeof(CUtensorMap)) : nullptr;
+        const bool b3 = (item.flags & kFlagTmB3) != 0;
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
         if (kind == kItemExit) break;
@@ -881,7 +882,8 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
             fence_tensormap_acquire(tmA);
             fence_tensormap_acquire(tmB);
           }
-          ok = tm_produce(t, stages, &sh.fz, it_k, tmA, tmB, p.wait_timeout_ns, &sh.abort, &sh.fail_where, pend)
+          ok = tm_produce(t, stages, &sh.fz, it_k, tmA, tmB, b3, p.wait_timeout_ns,
+                          &sh.abort, &sh.fail_where, pend)
                    ? 1u
                    : 0u;
         }

@@ -11,8 +11,9 @@
 // Stage layout (48 KB, four stages, the fused form's size): a k-step of A
 // is one TMA box of 128 rows x 32 binary32 values, landing as 128-byte rows
 // (row r at 128 r, its 16-byte chunks swizzled: chunk j at j ^ (r % 8)); a
-// k-step of B is eight boxes of 32 k-rows x 32 columns, box c at
-// 16 KB + 4 KB c (k-row kr at 128 kr inside it, swizzled alike). So every 8 rows of A and
+// k-step of B is eight slabs of 32 k-rows x 32 columns, slab c at
+// 16 KB + 4 KB c (k-row kr at 128 kr inside it, swizzled alike), landed by
+// one 3D box when n is a multiple of 32 and by eight 2D boxes otherwise. So every 8 rows of A and
 // every 8 k-rows x 32 columns of B occupy 1 KB of their own: an atom. A warp
 // converts an atom in place: all lanes read its 1 KB of binary32 (lane: row
 // lane / 4, 8 values from column 8 (lane % 4); the swizzle spreads a warp's
@@ -188,11 +189,12 @@ __device__ __forceinline__ bool tm_convert(const FzTile& t, uint8_t* stages, TmS
 
 // Producer warp, one lane: hand every k-step of tile t its stage once the
 // MMAs have released it -- with the TMA boxes of A and B when the task has
-// maps (tmA, tmB non-null), else as a free stage for the converters to fill.
+// maps (tmA, tmB non-null; b3: tmB lands all eight B slabs in one 3D box),
+// else as a free stage for the converters to fill.
 // pend[s] records the parity of a landing still possibly in flight in stage s
 // (bit 1 set), for tm_quiesce. Returns false when a wait ran out.
 __device__ __forceinline__ bool tm_produce(const FzTile& t, uint8_t* stages, TmShared* ts, uint32_t it,
-                                           const CUtensorMap* tmA, const CUtensorMap* tmB, uint64_t timeout_ns,
+                                           const CUtensorMap* tmA, const CUtensorMap* tmB, bool b3, uint64_t timeout_ns,
                                            volatile uint32_t* cta_abort, uint32_t* fail_where, uint32_t* pend) {
   const int nkb = (t.k + kTcBK - 1) / kTcBK;
   const uint32_t base0 = smem_u32(stages);
@@ -207,9 +209,13 @@ __device__ __forceinline__ bool tm_produce(const FzTile& t, uint8_t* stages, TmS
       const uint32_t st = base0 + s * kTcStageBytes;
       mbar_expect_tx(&ts->landed[s], kTmStageTx);
       tma_load_2d(st, tmA, kb * kTcBK, t.tm * kTcM, &ts->landed[s]);
+      if (b3) {
+        tma_load_3d(stages + s * kTcStageBytes + kTmBOff, tmB, 0, kb * kTcBK, t.tn * (kTcN / 32), &ts->landed[s]);
+      } else {
 #pragma unroll
-      for (int b = 0; b < kTcN / 32; ++b)
-        tma_load_2d(st + kTmBOff + (uint32_t)b * kTmBBox, tmB, t.tn * kTcN + 32 * b, kb * kTcBK, &ts->landed[s]);
+        for (int b = 0; b < kTcN / 32; ++b)
+          tma_load_2d(st + kTmBOff + (uint32_t)b * kTmBBox, tmB, t.tn * kTcN + 32 * b, kb * kTcBK, &ts->landed[s]);
+      }
       pend[s] = 2u | ph;
     } else {
       mbar_arrive(&ts->landed[s]);

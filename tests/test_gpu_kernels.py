@@ -183,3 +183,28 @@ def test_split3_fused_equals_prepass(gvm, shape):
     assert kernel_status() == 0
 
 
+@pytest.mark.parametrize(
+    "shape",
+    [(256, 256, 32), (257, 130, 67), (512, 512, 512), (129, 257, 513), (300, 1001, 77),
+     (130, 260, 100), (1000, 520, 2052), (4096, 2048, 96), (2500, 3000, 40), (256, 256, 1),
+     (768, 1024, 512), (1024, 512, 2048), (512, 768, 64), (520, 512, 256), (200, 300, 96), (384, 640, 44)],
+)
+def test_split3_wide_equals_prepass(gvm, shape):
+    # 256 x 256 tiles of one CTA (two 128-row MMA halves sharing each B stage,
+    # one accumulator drained after the next tile's first k-step): the same
+    # products in the same order per element, so the pre-pass result bit for
+    # bit. k = 1 and k = 32 leave one group without a k-step of a tile.
+    # Where k is a multiple of 4, A arrives by TMA boxes into the landing
+    # buffers, rows and k beyond A zero-filled (m = 200: a box taller than A;
+    # k = 44: a partial last k-step); several tiles per CTA check that the
+    # landings of consecutive tiles alternate correctly.
+    m, n, k = shape
+    A, B = synth.sgemm_inputs(synth.task_seed(11, m % 1000), m, n, k)
+    C1 = run_sgemm(gvm, A, B, "split3")
+    C2 = run_sgemm(gvm, A, B, "split3_wide")
+    assert np.array_equal(bits(C1), bits(C2)), shape
+    from paper_1511_07658_gb300.manager import kernel_status
+
+    assert kernel_status() == 0
+
+

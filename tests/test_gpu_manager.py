@@ -716,8 +716,10 @@ def test_tma_form_equals_fused_bitwise(gvm, mode):
     """The TMA form (binary32 A and B landed by tensor copies, split in place;
     tasks without maps staged by the converting warps' own loads) computes
     every element as the fused form does: equal bit for bit, on interior and
-    ragged tiles, k below one k-step, k and n not multiples of 4 (no maps),
-    several tiles per CTA, and within the SGEMM rule against the oracle."""
+    ragged tiles, k below one k-step, n a multiple of 32 (B in one 3D box per
+    k-step, slabs beyond n zero-filled: n = 384, 640), n a multiple of 4 only
+    (eight 2D boxes), k and n not multiples of 4 (no maps), several tiles per
+    CTA, and within the SGEMM rule against the oracle."""
     shapes = [(512, 512, 512), (128, 256, 32), (130, 260, 100), (300, 1000, 160), (257, 384, 200),
               (64, 700, 33), (1, 257, 31), (200, 192, 96), (1000, 520, 2052), (129, 257, 513), (256, 128, 4),
               (384, 640, 44), (640, 768, 1024)]
