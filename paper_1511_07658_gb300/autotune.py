@@ -14,10 +14,10 @@ and keeps the fastest:
 * ``sgemm_form`` (the split3 SGEMM tile form): fused 128 x 256 tiles
   (operands loaded by the staging warps), the same tiles with A and B landed
   by TMA and split in place, and wide 256 x 256 tiles of one CTA (A by TMA),
-  per workload class:
-  square 512^3 (16 x 64 tasks, the headline shape), 512 x 768 x 512
-  (16 x 16), 2048^3 (16 x 1) and a grouped mix of shapes drawn from
-  {128, ..., 2048} (16 ranks x 16 tasks). ``sgemm_form_by_class`` keeps the
+  per workload class: square 512^3 (16 x 64 tasks, the headline shape),
+  512 x 768 x 512 (16 x 16), 2048^3 (16 x 1) and a grouped mix of shapes
+  drawn from {128, ..., 2048} (64 ranks x 64 tasks, a quarter of the
+  grouped benchmark's tasks per rank). ``sgemm_form_by_class`` keeps the
   fastest form of each class; ``sgemm_form``, the manager's default, is the
   512^3 class's. A tile form per task inside one launch would need several
   forms in one kernel, whose converters then spill (measured); so the form
@@ -142,7 +142,7 @@ SGEMM_SHAPES = ((512, 512, 512, 64), (512, 768, 512, 16), (2048, 2048, 2048, 1))
 GROUPED_CLASS = "grouped"
 
 
-def time_grouped(path: str, ranks: int = 16, per_rank: int = 16, steps: int = 4) -> float:
+def time_grouped(path: str, ranks: int = 64, per_rank: int = 64, steps: int = 4) -> float:
     """Median step time (s) of resident SGEMMs with M, N, K drawn from
     {128, ..., 2048} (the grouped recipe), operands drawn on the device."""
     import synth
@@ -215,8 +215,8 @@ def run(path: str = _m.TUNING_FILE) -> dict:
         "workloads": {
             "copy_run_bytes": "end-to-end leg, 16 ranks x 16 SGEMM 512^3, operands in one pinned block per rank",
             "vadd_tile": "16 ranks x 8 resident vector adds, n = 2^22",
-            "sgemm_form": "resident SGEMM, 16 ranks x (64 of 512^3, 16 of 512 x 768 x 512, 1 of 2048^3, "
-                          "16 of the grouped mix): fused 128 x 256 tiles, the same tiles landed by TMA, "
+            "sgemm_form": "resident SGEMM, 16 ranks x (64 of 512^3, 16 of 512 x 768 x 512, 1 of 2048^3), "
+                          "64 ranks x 64 of the grouped mix: fused 128 x 256 tiles, the same tiles landed by TMA, "
                           "wide 256 x 256 tiles",
             "l2_prefetch": "the same SGEMM workloads, fused tiles, next-tile L2 prefetch off (0) and on (1)",
         },
