@@ -70,7 +70,7 @@ bool debug_on() {
 
 // gvm_sync gives the device this long beyond its own wait limit to report.
 constexpr uint64_t kStreamQueryNs = 2000000;  // gvm_sync: driver status check period (2 ms)
-constexpr uint64_t kSyncSpinNs = 200000;      // gvm_sync: spin this long, then sleep between polls
+constexpr uint64_t kSyncSpinNs = 5000000;     // gvm_sync: spin this long, then sleep between polls
 constexpr uint64_t kSyncSleepNs = 10000;      // gvm_sync: poll period once sleeping
 // Copies of one batch are merged when both sides are adjacent, by default up
 // to this many bytes per copy (gvm_config.copy_run_bytes): the link serves
@@ -1097,9 +1097,11 @@ int gvm_sync(gvm_rank* r, uint64_t seq) {
     if ((++spins & 63) == 0) {
       g.unlock();
       // Spin (yielding) for the first kSyncSpinNs, then poll every
-      // kSyncSleepNs: many ranks waiting on one GPU then leave the host's
-      // cores to the threads that have work (a rank preempted while it
-      // submits delays the whole request barrier by a scheduler slice).
+      // kSyncSleepNs: waits that outlast a whole launch leave the host's
+      // cores to the threads that have work. Shorter waits spin, because a
+      // sleeping waiter sees its completion late (measured: sleeping from
+      // 200 us on made each 1 ms step of 16 ranks x 64 SGEMM 512^3 17 us
+      // longer).
       if (now - t_wait > kSyncSpinNs)
         short_sleep(kSyncSleepNs);
       else

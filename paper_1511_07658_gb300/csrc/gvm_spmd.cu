@@ -31,9 +31,9 @@ class SpinBarrier {
     const auto t0 = std::chrono::steady_clock::now();
     while (gen_.load(std::memory_order_acquire) == gen) {
       if (++spins <= 64) continue;
-      // After 200 us, sleep between checks: waiting threads free the cores
-      // for the threads the barrier waits for.
-      if ((spins & 63) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200)) {
+      // After 5 ms (longer than a step's launch), sleep between checks:
+      // waiting threads free the cores for the threads the barrier waits for.
+      if ((spins & 63) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(5)) {
         thread_local bool slack_set = false;  // 1 us timer slack for this thread's short sleeps
         if (!slack_set) {
           prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
