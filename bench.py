@@ -78,8 +78,8 @@ def parse():
     p.add_argument("--skip-extra", action="store_true",
                    help="skip the FMA, vector-add and plain-form legs of the default workload")
     p.add_argument("--model", action="store_true", help="also check timings against Eqs. 1, 2 and 7")
-    p.add_argument("--e2e-overlap", type=int, choices=[1, 2], default=2,
-                   help="end-to-end leg: steps in flight per rank (2: gvm_spmd_run_overlapped, own manager)")
+    p.add_argument("--e2e-overlap", type=int, choices=[1, 2, 3, 4], default=2,
+                   help="end-to-end leg: steps in flight per rank (>= 2: gvm_spmd_run_pipelined, own manager)")
     p.add_argument("--direct-output", type=int, choices=[0, 1], default=None,
                    help="host-mode results written by the scheduler into the host buffers (default: tuning)")
     p.add_argument("--cross-process", action="store_true",
@@ -502,9 +502,9 @@ def gpu_arm(args, w, desc, rank, world):
         res_need[spec.rank] = off + (la + lb + lc + 255) // 256 * 256
         sizes[(spec.rank, spec.index)] = (la, lb, lc)
     resident = max(res_need)
-    # Two steps in flight on the end-to-end leg (its own manager, whose ring
-    # and staging hold two batches).
-    overlap = 2 if (args.e2e_overlap == 2 and args.harness == "native" and args.mode != "continuous") else 1
+    # Several steps in flight on the end-to-end leg (its own manager, whose
+    # ring and staging hold that many batches).
+    overlap = args.e2e_overlap if (args.harness == "native" and args.mode != "continuous") else 1
     host_stage = max(sum(sizes[(s.rank, s.index)]) for s in w.tasks) * per_rank
     slice_bytes = resident + host_stage + (64 << 20)
     slice_bytes = (slice_bytes + (1 << 20) - 1) // (1 << 20) * (1 << 20)
@@ -535,15 +535,17 @@ def gpu_arm(args, w, desc, rank, world):
         out_need[spec.rank] += al256(lc)
     in_blocks = [torch.empty(max(n, 256), dtype=torch.uint8).pin_memory() for n in in_need]
     out_blocks = [torch.empty(max(n, 256), dtype=torch.uint8).pin_memory() for n in out_need]
-    # odd steps of the overlapped end-to-end leg write here (a step's results
-    # stay until its rank has collected them)
-    out_blocks2 = [torch.empty(max(n, 256), dtype=torch.uint8).pin_memory() for n in out_need] if overlap == 2 else None
+    # steps of the pipelined end-to-end leg write to the output blocks of
+    # their phase (step i: phase i % overlap), so that a step's results stay
+    # until its rank has collected them
+    out_blocks_ph = [out_blocks] + [[torch.empty(max(n, 256), dtype=torch.uint8).pin_memory() for n in out_need]
+                                    for _ in range(overlap - 1)]
 
     def view(block, off, nbytes):
         return block[off:off + nbytes].view(torch.float32)
 
     host = {}
-    host2 = {}
+    host_ph = [host] + [{} for _ in range(overlap - 1)]
     for spec, inp in zip(w.tasks, inputs):
         a, b = inp
         la, lb, lc = sizes[(spec.rank, spec.index)]
@@ -554,15 +556,17 @@ def gpu_arm(args, w, desc, rank, world):
         tb.copy_(torch.from_numpy(np.ascontiguousarray(b)).reshape(-1))
         tc = view(out_blocks[spec.rank], out_off[(spec.rank, spec.index)], lc)
         host[(spec.rank, spec.index)] = (ta, tb, tc)
-        if out_blocks2 is not None:
-            host2[(spec.rank, spec.index)] = (ta, tb, view(out_blocks2[spec.rank], out_off[(spec.rank, spec.index)], lc))
+        for ph in range(1, overlap):
+            host_ph[ph][(spec.rank, spec.index)] = (
+                ta, tb, view(out_blocks_ph[ph][spec.rank], out_off[(spec.rank, spec.index)], lc))
         oa, ob, _ = res_offs[(spec.rank, spec.index)]
         ranks[spec.rank].write(oa, ta)
         ranks[spec.rank].write(ob, tb)
     bufs = {"res_offs": res_offs, "host": host}
     res_arrays = build_tasks(w, inputs, True, bufs)
     host_arrays = build_tasks(w, inputs, False, bufs)
-    host_arrays_odd = build_tasks(w, inputs, False, {"res_offs": res_offs, "host": host2}) if overlap == 2 else None
+    host_arrays_ph = [host_arrays] + [build_tasks(w, inputs, False, {"res_offs": res_offs, "host": host_ph[ph]})
+                                      for ph in range(1, overlap)]
     pool = ThreadPoolExecutor(max_workers=R)
     sampler = ClockSampler(dev)
 
@@ -692,25 +696,25 @@ def gpu_arm(args, w, desc, rank, world):
 
     # ---- end to end (host buffers, copies inside the timed region)
     e2e = None
-    if not args.skip_e2e and overlap == 2:
-        # Two steps in flight per rank: step i + 1 is submitted (and flushed)
-        # before step i's results are collected; even and odd steps write to
-        # separate host output blocks.
+    if not args.skip_e2e and overlap >= 2:
+        # `overlap` steps in flight per rank: step i + overlap - 1 is
+        # submitted (and flushed) before step i's results are collected; the
+        # phases write to separate host output blocks.
         mgr2 = g.Manager(
-            R, ring_depth=max(2, 1 << (2 * per_rank - 1).bit_length()), mode=args.mode, sgemm_path=args.path,
-            slice_bytes=2 * host_stage + (64 << 20), ingest_quantum=args.quantum,
+            R, ring_depth=max(2, 1 << (overlap * per_rank - 1).bit_length()), mode=args.mode, sgemm_path=args.path,
+            slice_bytes=overlap * host_stage + (64 << 20), ingest_quantum=args.quantum,
             direct_output=None if args.direct_output is None else bool(args.direct_output),
             l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
             copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
             copy_streams_max=args.copy_streams_max,
         )
         ranks2 = [mgr2.attach(r) for r in range(R)]
-        mgr2.spmd_run_overlapped(ranks2, host_arrays, host_arrays_odd, max(1, args.warmup))
+        mgr2.spmd_run_pipelined(ranks2, host_arrays_ph, max(1, args.warmup))
         device_sync()
         if world > 1:
             torch.distributed.barrier()
         e_steps = max(3, args.steps // 2)
-        total_ms, _ = mgr2.spmd_run_overlapped(ranks2, host_arrays, host_arrays_odd, e_steps)
+        total_ms, _ = mgr2.spmd_run_pipelined(ranks2, host_arrays_ph, e_steps)
         mgr2.shutdown()
         h_s = total_ms / 1e3
         if world > 1:
@@ -724,7 +728,7 @@ def gpu_arm(args, w, desc, rank, world):
             "d2h_bytes_per_step": d2h,
             "host_link_gbs": (h2d + d2h) * e_steps / h_s / 1e9,
             "ms_per_step": 1e3 * h_s / e_steps,
-            "steps_in_flight": 2,
+            "steps_in_flight": overlap,
             "host_memcpy_gbs": host_memcpy_gbs(),
         }
     elif not args.skip_e2e:
@@ -763,12 +767,12 @@ def gpu_arm(args, w, desc, rank, world):
 
     spot = []
     if e2e is not None and w.tasks[0].kind == synth.TASK_SGEMM:
-        # end-to-end outputs (both parities when two steps were in flight)
+        # end-to-end outputs (every phase's when several steps were in flight)
         spec = [s for s in w.tasks if s.rank == R - 1][-1]
         inp = inputs[w.tasks.index(spec)]
         rows = np.arange(0, spec.m, 37)
         ref = oracle.sgemm64(inp[0][rows], inp[1])
-        for hb in ([host, host2] if overlap == 2 else [host]):
+        for hb in host_ph:
             C = hb[(R - 1, spec.index)][2].reshape(spec.m, spec.n).numpy()
             spot.append(oracle.rel_fro_err(C[rows], ref))
     for r in (0, R - 1):

@@ -353,6 +353,18 @@ GVM_API int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, const 
                                     const gvm_task* const* tasks_odd, const uint32_t* counts, int32_t nranks,
                                     int32_t steps, double* total_ms_host, double* done_ms_host);
 
+/* The same with nphases steps in flight per rank (nphases >= 1; 2 is
+   gvm_spmd_run_overlapped, 1 collects each step before the next): step i
+   uses phases[i % nphases][r], and a rank collects step i after it has
+   submitted step i + nphases - 1, so up to nphases steps' copies and
+   launches are queued at once. Give each phase its own output buffers. A
+   rank's ring and staging space must hold nphases batches. Timings and
+   errors as gvm_spmd_run_overlapped; GVM_EINVAL for nphases < 1 or a NULL
+   phase. */
+GVM_API int gvm_spmd_run_pipelined(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* const* phases,
+                                   int32_t nphases, const uint32_t* counts, int32_t nranks, int32_t steps,
+                                   double* total_ms_host, double* done_ms_host);
+
 /* Open-loop serving harness (continuous mode): one native thread per rank
    submits tasks[r][i] at its scheduled arrival arrival_ns[r][i] (nanoseconds
    after a common start, non-decreasing per rank), keeping at most

@@ -153,6 +153,11 @@ PROTOTYPES = {
         [c_void_p, POINTER(c_void_p), POINTER(POINTER(GvmTask)), POINTER(POINTER(GvmTask)), POINTER(c_uint32),
          c_int32, c_int32, POINTER(c_double), POINTER(c_double)],
     ),
+    "gvm_spmd_run_pipelined": (
+        c_int,
+        [c_void_p, POINTER(c_void_p), POINTER(POINTER(POINTER(GvmTask))), c_int32, POINTER(c_uint32), c_int32,
+         c_int32, POINTER(c_double), POINTER(c_double)],
+    ),
     "gvm_open_loop_run": (
         c_int,
         [c_void_p, POINTER(c_void_p), POINTER(POINTER(GvmTask)), POINTER(POINTER(c_uint64)), POINTER(c_uint32),

@@ -185,12 +185,18 @@ extern "C" int gvm_spmd_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task
   return rc;
 }
 
-extern "C" int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks_even,
-                                       const gvm_task* const* tasks_odd, const uint32_t* counts, int32_t nranks,
-                                       int32_t steps, double* total_ms_host, double* done_ms_host) {
-  if (!ctx || !ranks || !tasks_even || !counts || nranks <= 0 || steps < 0 || !total_ms_host) return GVM_EINVAL;
-  for (int r = 0; r < nranks; ++r)
-    if (!ranks[r] || (counts[r] && (!tasks_even[r] || (tasks_odd && !tasks_odd[r])))) return GVM_EINVAL;
+extern "C" int gvm_spmd_run_pipelined(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* const* phases,
+                                      int32_t nphases, const uint32_t* counts, int32_t nranks, int32_t steps,
+                                      double* total_ms_host, double* done_ms_host) {
+  if (!ctx || !ranks || !phases || nphases < 1 || !counts || nranks <= 0 || steps < 0 || !total_ms_host)
+    return GVM_EINVAL;
+  for (int p = 0; p < nphases; ++p)
+    if (!phases[p]) return GVM_EINVAL;
+  for (int r = 0; r < nranks; ++r) {
+    if (!ranks[r]) return GVM_EINVAL;
+    for (int p = 0; p < nphases; ++p)
+      if (counts[r] && !phases[p][r]) return GVM_EINVAL;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GVM_EINVAL;
   SpinBarrier bar(nranks);
@@ -199,15 +205,16 @@ extern "C" int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, con
     int ok = GVM_OK;
     err.compare_exchange_strong(ok, rc);
   };
+  const int lag = nphases - 1;  // steps submitted ahead of the one collected
   const auto t0 = std::chrono::steady_clock::now();
   std::vector<std::chrono::steady_clock::time_point> t_done(steps);
   auto body = [&](int r) {
     cudaSetDevice(dev);
     std::vector<uint64_t> last(steps, 0);
-    for (int i = 0; i <= steps; ++i) {
+    for (int i = 0; i < steps + lag; ++i) {
       // Step i: submit (every rank), meet, flush (thread 0), meet.
       if (i < steps) {
-        const gvm_task* t = (tasks_odd && (i & 1)) ? tasks_odd[r] : tasks_even[r];
+        const gvm_task* t = phases[i % nphases][r];
         if (err.load() == GVM_OK && counts[r]) {
           const int rc = submit_batch(ranks[r], t, counts[r], &last[i]);
           if (rc != GVM_OK) fail(rc);
@@ -219,14 +226,15 @@ extern "C" int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, con
         }
         bar.wait();
       }
-      // Then the results of step i - 1.
-      if (i >= 1) {
+      // Then the results of step i - lag.
+      const int j = i - lag;
+      if (j >= 0) {
         if (err.load() == GVM_OK && counts[r]) {
-          const int rc = gvm_sync(ranks[r], last[i - 1]);
+          const int rc = gvm_sync(ranks[r], last[j]);
           if (rc != GVM_OK) fail(rc);
         }
         bar.wait();
-        if (r == 0) t_done[i - 1] = std::chrono::steady_clock::now();
+        if (r == 0) t_done[j] = std::chrono::steady_clock::now();
       }
     }
   };
@@ -240,6 +248,14 @@ extern "C" int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, con
   if (done_ms_host)
     for (int i = 0; i < steps; ++i) done_ms_host[i] = std::chrono::duration<double, std::milli>(t_done[i] - t0).count();
   return err.load();
+}
+
+extern "C" int gvm_spmd_run_overlapped(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks_even,
+                                       const gvm_task* const* tasks_odd, const uint32_t* counts, int32_t nranks,
+                                       int32_t steps, double* total_ms_host, double* done_ms_host) {
+  if (!tasks_even) return GVM_EINVAL;
+  const gvm_task* const* phases[2] = {tasks_even, tasks_odd ? tasks_odd : tasks_even};
+  return gvm_spmd_run_pipelined(ctx, ranks, phases, 2, counts, nranks, steps, total_ms_host, done_ms_host);
 }
 
 extern "C" int gvm_open_loop_run(gvm_ctx* ctx, gvm_rank* const* ranks, const gvm_task* const* tasks,

@@ -389,6 +389,26 @@ class Manager:
               "gvm_spmd_run_overlapped")
         return total.value, list(done)[:steps]
 
+    def spmd_run_pipelined(self, ranks, arrays_by_phase, steps: int) -> tuple[float, list[float]]:
+        """gvm_spmd_run_pipelined: like spmd_run_overlapped with
+        len(arrays_by_phase) steps in flight per rank; step i uses
+        arrays_by_phase[i % len(arrays_by_phase)] (one list of per-rank ctypes
+        task arrays per phase). Returns (total ms, per-step ms at which each
+        step's results were all collected)."""
+        n = len(ranks)
+        P = len(arrays_by_phase)
+        hs = (c_void_p * n)(*[r.handle for r in ranks])
+        per = [(ctypes.POINTER(GvmTask) * n)(*[ctypes.cast(a, ctypes.POINTER(GvmTask)) for a in arrs])
+               for arrs in arrays_by_phase]
+        ph = (ctypes.POINTER(ctypes.POINTER(GvmTask)) * P)(
+            *[ctypes.cast(x, ctypes.POINTER(ctypes.POINTER(GvmTask))) for x in per])
+        cnt = (ctypes.c_uint32 * n)(*[len(a) for a in arrays_by_phase[0]])
+        total = ctypes.c_double()
+        done = (ctypes.c_double * max(steps, 1))()
+        check(lib().gvm_spmd_run_pipelined(self.handle, hs, ph, P, cnt, n, steps, byref(total), done),
+              "gvm_spmd_run_pipelined")
+        return total.value, list(done)[:steps]
+
     def open_loop_run(self, ranks, task_arrays, arrival_ns, max_inflight: int = 0):
         """gvm_open_loop_run: rank i submits task_arrays[i][j] (ctypes arrays
         of GvmTask) at arrival_ns[i][j] ns after a common start (one native

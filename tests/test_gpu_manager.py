@@ -534,6 +534,49 @@ def test_spmd_overlapped_steps(gvm, mode):
             check_result(spec, (ins[0].numpy(), ins[1].numpy()), out)
 
 
+@pytest.mark.parametrize("nphases", [1, 3])
+def test_spmd_pipelined_steps(gvm, nphases):
+    """gvm_spmd_run_pipelined: with nphases steps in flight, step i uses phase
+    i % nphases and is collected after step i + nphases - 1 is submitted;
+    every phase's host outputs hold the oracle's results afterwards (7 steps:
+    each phase runs at least twice, the last ones collected after the final
+    submit)."""
+    R, per, steps = 3, 4, 7
+    specs = []
+    for r in range(R):
+        for i in range(per):
+            if i % 2 == 0:
+                specs.append(synth.TaskSpec(r, i, synth.TASK_SGEMM, m=100 + r, n=260, k=64, seed=synth.task_seed(r, i)))
+            else:
+                specs.append(synth.TaskSpec(r, i, synth.TASK_VADD, n=40003 + r, seed=synth.task_seed(r, i)))
+    with gvm.Manager(R, ring_depth=16, mode="barrier", sgemm_path="split3", slice_bytes=32 << 20) as mgr:
+        ranks = [mgr.attach(r) for r in range(R)]
+        phases = [[(gvm.GvmTask * per)() for _ in range(R)] for _ in range(nphases)]
+        keep = []
+        for spec in specs:
+            if spec.kind == synth.TASK_SGEMM:
+                A, B = synth.sgemm_inputs(spec.seed, spec.m, spec.n, spec.k)
+                ins, shape = (pinned(A), pinned(B)), (spec.m, spec.n)
+            else:
+                a, b = synth.vadd_inputs(spec.seed, spec.n)
+                ins, shape = (pinned(a), pinned(b)), (spec.n,)
+            outs = [torch.full(shape, float("nan")).pin_memory() for _ in range(nphases)]
+            for arr, out in zip(phases, outs):
+                t = arr[spec.rank][spec.index]
+                t.type = gvm.GVM_TASK_SGEMM if spec.kind == synth.TASK_SGEMM else gvm.GVM_TASK_VADD
+                t.flags = 0
+                t.m, t.n, t.k = spec.m, spec.n, spec.k
+                t.a, t.b, t.c = ins[0].data_ptr(), ins[1].data_ptr(), out.data_ptr()
+            keep.append((spec, ins, outs))
+        total, done = mgr.spmd_run_pipelined(ranks, phases, steps)
+        assert total > 0 and len(done) == steps and all(x > 0 for x in done)
+        assert done == sorted(done) and done[-1] <= total
+        assert mgr.stats()["device_status"] == 0
+    for spec, ins, outs in keep:
+        for out in outs:
+            check_result(spec, (ins[0].numpy(), ins[1].numpy()), out)
+
+
 @pytest.mark.parametrize("max_inflight", [1, 3])
 def test_open_loop_harness(gvm, max_inflight):
     """gvm_open_loop_run (continuous mode): paced arrivals, at most
