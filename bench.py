@@ -271,6 +271,39 @@ def host_memcpy_gbs(nbytes=256 << 20, reps=3):
     return 2 * nbytes / best / 1e9
 
 
+def block_link_gbs(blocks, to_device: bool):
+    """Copy rate of each page-locked host block on its own (one copy of the
+    whole block, best of 2, CUDA events): in a virtual machine each
+    allocation's placement relative to the GPU's host link is not visible,
+    so this shows whether a slow end-to-end leg had slow buffers. The blocks'
+    contents are left as they were. Returns min, median and max over the
+    blocks (GB/s)."""
+    import torch
+
+    rates = []
+    for hb in blocks:
+        # The device copy starts as the block's own bytes, so that timing the
+        # device-to-host direction writes back what the block already holds.
+        dev = hb.to("cuda")
+        best = None
+        for _ in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if to_device:
+                dev.copy_(hb, non_blocking=True)
+            else:
+                hb.copy_(dev, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        rates.append(hb.numel() / (best / 1e3) / 1e9)
+        del dev
+    rates.sort()
+    return {"min": rates[0], "median": rates[len(rates) // 2], "max": rates[-1], "blocks": len(rates)}
+
+
 def percentile(xs, q):
     if not xs:
         return None
@@ -730,6 +763,8 @@ def gpu_arm(args, w, desc, rank, world):
             "ms_per_step": 1e3 * h_s / e_steps,
             "steps_in_flight": overlap,
             "host_memcpy_gbs": host_memcpy_gbs(),
+            "block_h2d_gbs": block_link_gbs(in_blocks, True),
+            "block_d2h_gbs": block_link_gbs(out_blocks, False),
         }
     elif not args.skip_e2e:
         if native:
@@ -760,6 +795,8 @@ def gpu_arm(args, w, desc, rank, world):
             "host_link_gbs": (h2d + d2h) * e_steps / h_s / 1e9,
             "ms_per_step": 1e3 * h_s / e_steps,
             "host_memcpy_gbs": host_memcpy_gbs(),
+            "block_h2d_gbs": block_link_gbs(in_blocks, True),
+            "block_d2h_gbs": block_link_gbs(out_blocks, False),
         }
 
     # ---- parity spot check of the last step (resident outputs), sampled rows
