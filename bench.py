@@ -90,6 +90,8 @@ def parse():
     p.add_argument("--quantum", type=int, default=8)
     p.add_argument("--copy-streams-max", type=int, default=0,
                    help="copy streams the managers create (0: the library's default budget)")
+    p.add_argument("--vadd-tile", type=int, default=None,
+                   help="elements per vector-add tile (0: per task, n / CTAs; default: the tuned value)")
     p.add_argument("--copy-run-mb", type=int, default=None,
                    help="merge adjacent host-mode copies up to this many MiB (default: the tuned choice)")
     p.add_argument("--l2-prefetch", type=int, choices=[0, 1], default=None,
@@ -547,7 +549,7 @@ def gpu_arm(args, w, desc, rank, world):
         direct_output=None if args.direct_output is None else bool(args.direct_output),
         l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
         copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
-        copy_streams_max=args.copy_streams_max,
+        copy_streams_max=args.copy_streams_max, vadd_tile=args.vadd_tile,
     )
     direct_output_used = mgr.cfg.direct_output
     ranks = [mgr.attach(r) for r in range(R)]
@@ -739,7 +741,7 @@ def gpu_arm(args, w, desc, rank, world):
             direct_output=None if args.direct_output is None else bool(args.direct_output),
             l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
             copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
-            copy_streams_max=args.copy_streams_max,
+            copy_streams_max=args.copy_streams_max, vadd_tile=args.vadd_tile,
         )
         ranks2 = [mgr2.attach(r) for r in range(R)]
         mgr2.spmd_run_pipelined(ranks2, host_arrays_ph, max(1, args.warmup))

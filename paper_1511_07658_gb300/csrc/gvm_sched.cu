@@ -109,6 +109,7 @@ struct IngestOut {
 // Warp 0 of one CTA: move ready descriptors from the host rings into the
 // device table and append their queue entries, each covering a contiguous
 // range of the global tile space. All lanes call.
+template <bool kPrefetch>
 __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
   const int lane = threadIdx.x & 31;
   IngestOut out{0, 0, 0};
@@ -173,13 +174,36 @@ __device__ IngestOut ingest(const SchedParams& p, uint64_t* prof) {
       static_assert(offsetof(TaskBody, flags) == 260 && offsetof(TaskBody, tag) == 272 &&
                         offsetof(TaskBody, ntiles) == 276 && offsetof(TaskBody, nsplit) == 280,
                     "TaskBody header words");
+      // kPrefetch: descriptor s + 1 is read while s is processed, so that a
+      // lane's host round trips overlap instead of following one another
+      // (32 more registers; the FMA scheduler, which would spill, reads them
+      // one by one).
+      auto fields_of = [&](uint32_t s) {
+        return reinterpret_cast<const uint4*>(&p.host_desc[r * p.depth + (s & (p.depth - 1))]) + kFieldsAt;
+      };
+      uint4 vn[kPrefetch ? 8 : 1];
+      if (kPrefetch && lim > 0) {
+        const uint4* src = fields_of(t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) vn[kPrefetch ? j : 0] = ld_volatile_v4(src + j);
+      }
       for (; take < lim; ++take) {
         const uint32_t s = t + take;
         const uint32_t idx = r * p.depth + (s & (p.depth - 1));
-        const uint4* src = reinterpret_cast<const uint4*>(&p.host_desc[idx]) + kFieldsAt;
         uint4 v[8];
+        if constexpr (kPrefetch) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = ld_volatile_v4(src + j);
+          for (int j = 0; j < 8; ++j) v[j] = vn[j];
+          if (take + 1 < lim) {
+            const uint4* nsrc = fields_of(s + 1);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) vn[j] = ld_volatile_v4(nsrc + j);
+          }
+        } else {
+          const uint4* src = fields_of(s);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = ld_volatile_v4(src + j);
+        }
         const uint32_t flags = v[0].y;
         if ((flags & kFlagNeedsReady) && ld_acquire_gpu(&p.ready[idx]) != s + 1u) break;
         DevTask* dt = &p.tasks[idx];
@@ -310,6 +334,7 @@ struct Claim {
 // counter for all CTAs to contend on. A tile beyond published_tiles is a
 // reservation; tiles are published in increasing order, so it becomes valid
 // without further claims.
+template <bool kPrefetch>
 __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t& phase, uint32_t& tile,
                        uint64_t* prof, bool blocking, uint64_t idle_return_ns = 0) {
   const int lane = threadIdx.x & 31;
@@ -347,7 +372,7 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
     quiet = bcast64(quiet);
     if (x < pt) {
       // Keep the queue ahead of the CTAs.
-      if (pt - x <= kLookaheadTiles && now >= quiet) (void)ingest(p, prof);
+      if (pt - x <= kLookaheadTiles && now >= quiet) (void)ingest<kPrefetch>(p, prof);
       // Find the entry holding tile x: the last entry with base <= x. Entries
       // are published in tile order, and x only grows from one claim of a CTA
       // to the next, so the search starts at the entry of this CTA's previous
@@ -419,7 +444,7 @@ __device__ int acquire(const SchedParams& p, Claim* cl, uint32_t& task, uint32_t
       if (reserved_published()) continue;
       return 0;
     }
-    const IngestOut r = ingest(p, prof);
+    const IngestOut r = ingest<kPrefetch>(p, prof);
     if (r.published) {
       set_stall(0);
       continue;
@@ -535,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 2) sched_fma_kernel(const SchedParam
   auto claim = [&](int slot, bool blocking) {
     const uint64_t t_acq = globaltimer();
     uint32_t task = 0, phase = 0, tile = 0;
-    const int got = acquire(p, cl, task, phase, tile, sh.prof, blocking);
+    const int got = acquire<false>(p, cl, task, phase, tile, sh.prof, blocking);
     if (lane == 0) {
       sh.go[slot] = (uint32_t)got;
       sh.task[slot] = task;
@@ -776,7 +801,7 @@ __device__ __forceinline__ void sched_tc_body(const SchedParams& p) {
       uint32_t task = 0, phase = 0, tile = 0;
       // An idle control warp posts a no-op item now and then, so that the
       // other warps' waits for items stay bounded.
-      const int got = sh.abort ? 0 : acquire(p, cl, task, phase, tile, sh.prof, true, p.wait_timeout_ns / 4);
+      const int got = sh.abort ? 0 : acquire<true>(p, cl, task, phase, tile, sh.prof, true, p.wait_timeout_ns / 4);
       if (lane == 0) {
         FzItem& it = sh.items[slot];
         it.kind = got == 1 ? 0u : (got == 2 ? kItemNop : kItemExit);
