@@ -90,6 +90,8 @@ def parse():
     p.add_argument("--quantum", type=int, default=8)
     p.add_argument("--copy-streams-max", type=int, default=0,
                    help="copy streams the managers create (0: the library's default budget)")
+    p.add_argument("--idle-poll-ns", type=int, default=1000,
+                   help="sleep of an idle scheduler CTA between polls of the task rings")
     p.add_argument("--vadd-tile", type=int, default=None,
                    help="elements per vector-add tile (0: per task, n / CTAs; default: the tuned value)")
     p.add_argument("--copy-run-mb", type=int, default=None,
@@ -550,6 +552,7 @@ def gpu_arm(args, w, desc, rank, world):
         l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
         copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
         copy_streams_max=args.copy_streams_max, vadd_tile=args.vadd_tile,
+        idle_poll_ns=args.idle_poll_ns,
     )
     direct_output_used = mgr.cfg.direct_output
     ranks = [mgr.attach(r) for r in range(R)]
@@ -742,6 +745,7 @@ def gpu_arm(args, w, desc, rank, world):
             l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
             copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
             copy_streams_max=args.copy_streams_max, vadd_tile=args.vadd_tile,
+        idle_poll_ns=args.idle_poll_ns,
         )
         ranks2 = [mgr2.attach(r) for r in range(R)]
         mgr2.spmd_run_pipelined(ranks2, host_arrays_ph, max(1, args.warmup))
