@@ -155,7 +155,7 @@ def test_vadd_4x8_bench_layout_bitexact(gvm):
         assert np.array_equal(bits(c_host), ref), s
 
 
-@pytest.mark.parametrize("path", ["split3", "fma"])
+@pytest.mark.parametrize("path", ["split3", "split3_wide", "split3_tma", "fma"])
 def test_sgemm512_16x64_bench_layout_sampled(gvm, path):
     w = synth.sgemm_square()
     out = run_bench_layout(gvm, w, path)
@@ -170,7 +170,10 @@ def test_sgemm512_16x64_bench_layout_sampled(gvm, path):
     assert chk.finish() < 1e-5
 
 
-def test_grouped_64x256_sampled(gvm):
+@pytest.mark.parametrize("path", ["split3", "split3_wide", "split3_tma"])
+def test_grouped_64x256_sampled(gvm, path):
+    # Every split3 tile form at the grouped benchmark's full size: the bench
+    # runs whichever form the tuning table picks for this class.
     g = gvm
     R, P, side = 64, 256, 2048
     w = synth.grouped_mixed(ranks=R, per_rank=P)
@@ -188,7 +191,7 @@ def test_grouped_64x256_sampled(gvm):
     for r in range(R):
         more = rng.choice(np.arange(1, P - 1), 4, replace=False)
         picks += [(r, int(i)) for i in sorted({0, P - 1, *more.tolist()})]
-    with g.Manager(R, ring_depth=max(2, 1 << (P - 1).bit_length()), mode="barrier", sgemm_path="split3",
+    with g.Manager(R, ring_depth=max(2, 1 << (P - 1).bit_length()), mode="barrier", sgemm_path=path,
                    slice_bytes=resident + (4 << 20), resident_bytes=resident, ingest_quantum=8) as mgr:
         ranks = [mgr.attach(r) for r in range(R)]
         pinned = [torch.from_numpy(x).pin_memory() for x in pools]
