@@ -351,12 +351,8 @@ __device__ __forceinline__ bool fz_epilogue(const FzTile& t, FzShared* fs, uint3
   const int row = t.tm * kTcM + q * 32 + lane;
   const uintptr_t ca = reinterpret_cast<uintptr_t>(t.C);
   const int vec = ((t.n & 7) == 0 && (ca & 31) == 0) ? 2 : ((t.n & 3) == 0 && (ca & 15) == 0) ? 1 : 0;
-#pragma unroll 1
-  for (int ch = 0; ch < 4; ++ch) {
-    const int chunk = cq * 4 + ch;
-    uint32_t r[32];
-    tmem_ld_32x32b_x32(fs->tmem_base + b * kTcN + ((uint32_t)(q * 32) << 16) + (uint32_t)(chunk * 32), r);
-    tmem_ld_wait();
+  // One row's 32 columns from chunk `chunk` into C.
+  auto store_chunk = [&](int chunk, const uint32_t (&r)[32]) {
     const int64_t c0 = (int64_t)t.tn * kTcN + chunk * 32;
     if (row < t.m && c0 < t.n) {
       float* dst = t.C + (int64_t)row * t.n + c0;
@@ -373,6 +369,19 @@ __device__ __forceinline__ bool fz_epilogue(const FzTile& t, FzShared* fs, uint3
           if (c0 + j < t.n) dst[j] = __uint_as_float(r[j]);
       }
     }
+  };
+  // Two 32-column chunks a TMEM round trip (the staging registers are free
+  // here), four chunks a warp.
+  const uint32_t taddr = fs->tmem_base + b * kTcN + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+  for (int ch = 0; ch < 4; ch += 2) {
+    const int chunk = cq * 4 + ch;
+    uint32_t r0[32], r1[32];
+    tmem_ld_32x32b_x32(taddr + (uint32_t)(chunk * 32), r0);
+    tmem_ld_32x32b_x32(taddr + (uint32_t)((chunk + 1) * 32), r1);
+    tmem_ld_wait();
+    store_chunk(chunk, r0);
+    store_chunk(chunk + 1, r1);
   }
   tc_fence_before();
   __syncwarp();
