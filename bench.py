@@ -90,6 +90,10 @@ def parse():
     p.add_argument("--quantum", type=int, default=8)
     p.add_argument("--copy-streams-max", type=int, default=0,
                    help="copy streams the managers create (0: the library's default budget)")
+    p.add_argument("--e2e-steps", type=int, default=0,
+                   help="timed steps of the end-to-end leg (0: half of --steps)")
+    p.add_argument("--copy-in-streams", type=int, default=0,
+                   help="input copy streams of the manager (0: half of the copy-stream limit)")
     p.add_argument("--idle-poll-ns", type=int, default=1000,
                    help="sleep of an idle scheduler CTA between polls of the task rings")
     p.add_argument("--vadd-tile", type=int, default=None,
@@ -552,7 +556,7 @@ def gpu_arm(args, w, desc, rank, world):
         l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
         copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
         copy_streams_max=args.copy_streams_max, vadd_tile=args.vadd_tile,
-        idle_poll_ns=args.idle_poll_ns,
+        idle_poll_ns=args.idle_poll_ns, copy_in_streams=args.copy_in_streams,
     )
     direct_output_used = mgr.cfg.direct_output
     ranks = [mgr.attach(r) for r in range(R)]
@@ -745,16 +749,19 @@ def gpu_arm(args, w, desc, rank, world):
             l2_prefetch=None if args.l2_prefetch is None else bool(args.l2_prefetch),
             copy_run_bytes=None if args.copy_run_mb is None else args.copy_run_mb << 20,
             copy_streams_max=args.copy_streams_max, vadd_tile=args.vadd_tile,
-        idle_poll_ns=args.idle_poll_ns,
+        idle_poll_ns=args.idle_poll_ns, copy_in_streams=args.copy_in_streams,
         )
         ranks2 = [mgr2.attach(r) for r in range(R)]
         mgr2.spmd_run_pipelined(ranks2, host_arrays_ph, max(1, args.warmup))
         device_sync()
         if world > 1:
             torch.distributed.barrier()
-        e_steps = max(3, args.steps // 2)
-        total_ms, _ = mgr2.spmd_run_pipelined(ranks2, host_arrays_ph, e_steps)
+        e_steps = max(3, args.e2e_steps or args.steps // 2)
+        total_ms, done_ms = mgr2.spmd_run_pipelined(ranks2, host_arrays_ph, e_steps)
         mgr2.shutdown()
+        # per step: time between consecutive steps' results all collected
+        gaps_in_order = [b - a for a, b in zip([0.0] + done_ms[:-1], done_ms)]
+        gaps = sorted(gaps_in_order)
         h_s = total_ms / 1e3
         if world > 1:
             h_s = max_over_ranks(h_s, world)
@@ -771,6 +778,8 @@ def gpu_arm(args, w, desc, rank, world):
             "host_memcpy_gbs": host_memcpy_gbs(),
             "block_h2d_gbs": block_link_gbs(in_blocks, True),
             "block_d2h_gbs": block_link_gbs(out_blocks, False),
+            "step_ms": {"min": gaps[0], "median": gaps[len(gaps) // 2], "max": gaps[-1], "first": gaps_in_order[0],
+                        "kind": "host clock, between consecutive steps' results collected (the first from the start)"},
         }
     elif not args.skip_e2e:
         if native:

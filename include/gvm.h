@@ -158,7 +158,11 @@ typedef struct gvm_config {
                                hardware queues of CUDA_DEVICE_MAX_CONNECTIONS=32); while
                                2 x max_ranks exceeds it, ranks share input streams (r % n_in)
                                and output streams (r % n_out), n_in + n_out <= the limit */
-  int32_t reserved0;        /* 0 */
+  int32_t copy_in_streams;  /* copy_streams NULL: input copy streams to create (ranks share
+                               them round robin, r % n), the rest of copy_streams_max going
+                               to output streams; 0 = split the limit evenly. One input
+                               stream lands a step's inputs in submission order, all of a
+                               step before the next step's */
 } gvm_config;
 
 typedef struct gvm_task {

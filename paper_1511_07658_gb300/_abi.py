@@ -58,7 +58,7 @@ class GvmConfig(ctypes.Structure):
         ("direct_output", c_int32),
         ("l2_prefetch", c_int32),
         ("copy_streams_max", c_int32),
-        ("reserved0", c_int32),
+        ("copy_in_streams", c_int32),
     ]
 
 

@@ -512,7 +512,7 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   if (cfg.copy_run_bytes == 0) cfg.copy_run_bytes = kDefaultCopyRun;
   if (cfg.vadd_tile < 0) return GVM_EINVAL;
   if (cfg.direct_output < 0 || cfg.direct_output > 1 || cfg.l2_prefetch < 0 || cfg.l2_prefetch > 1 ||
-      cfg.copy_streams_max < 0 || cfg.reserved0 != 0)
+      cfg.copy_streams_max < 0 || cfg.copy_in_streams < 0)
     return GVM_EINVAL;
   if (cfg.vadd_tile > 0) cfg.vadd_tile = std::max<int64_t>(1024, cfg.vadd_tile / 1024 * 1024);
   if (cfg.ingest_quantum <= 0) cfg.ingest_quantum = 4;
@@ -606,7 +606,10 @@ int gvm_init(const gvm_config* cfg_in, gvm_ctx** out) {
   // otherwise at most half of the budget each.
   const uint32_t budget = cfg.copy_streams_max > 0 ? (uint32_t)cfg.copy_streams_max : 31u;
   uint32_t n_in = R, n_out = R;
-  if (2 * R > budget) {
+  if (cfg.copy_in_streams > 0) {
+    n_in = std::min<uint32_t>(R, std::min<uint32_t>((uint32_t)cfg.copy_in_streams, budget > 1 ? budget - 1 : 1u));
+    n_out = std::min<uint32_t>(R, std::max<uint32_t>(1u, budget - n_in));
+  } else if (2 * R > budget) {
     n_in = std::min<uint32_t>(R, std::max<uint32_t>(1u, (budget + 1) / 2));
     n_out = std::min<uint32_t>(R, std::max<uint32_t>(1u, budget - n_in));
   }

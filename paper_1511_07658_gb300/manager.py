@@ -262,6 +262,7 @@ class Manager:
         direct_output: bool | None = None,
         l2_prefetch: bool | None = None,
         copy_streams_max: int = 0,
+        copy_in_streams: int = 0,
         device: int | None = None,
     ):
         if not torch.cuda.is_available():
@@ -308,6 +309,7 @@ class Manager:
         cfg.direct_output = int(bool(tuned.get("direct_output", 0) if direct_output is None else direct_output))
         cfg.l2_prefetch = int(bool(tuned.get("l2_prefetch", 0) if l2_prefetch is None else l2_prefetch))
         cfg.copy_streams_max = int(copy_streams_max)
+        cfg.copy_in_streams = int(copy_in_streams)
         self.cfg = cfg
         h = c_void_p()
         with torch.cuda.device(self.device):
