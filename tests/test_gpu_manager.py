@@ -534,13 +534,14 @@ def test_spmd_overlapped_steps(gvm, mode):
             check_result(spec, (ins[0].numpy(), ins[1].numpy()), out)
 
 
-@pytest.mark.parametrize("nphases", [1, 3])
-def test_spmd_pipelined_steps(gvm, nphases):
+@pytest.mark.parametrize("nphases,in_streams", [(1, 0), (3, 0), (3, 1)])
+def test_spmd_pipelined_steps(gvm, nphases, in_streams):
     """gvm_spmd_run_pipelined: with nphases steps in flight, step i uses phase
     i % nphases and is collected after step i + nphases - 1 is submitted;
     every phase's host outputs hold the oracle's results afterwards (7 steps:
     each phase runs at least twice, the last ones collected after the final
-    submit)."""
+    submit). in_streams = 1: every rank's input copies share one stream
+    (gvm_config.copy_in_streams)."""
     R, per, steps = 3, 4, 7
     specs = []
     for r in range(R):
@@ -549,7 +550,8 @@ def test_spmd_pipelined_steps(gvm, nphases):
                 specs.append(synth.TaskSpec(r, i, synth.TASK_SGEMM, m=100 + r, n=260, k=64, seed=synth.task_seed(r, i)))
             else:
                 specs.append(synth.TaskSpec(r, i, synth.TASK_VADD, n=40003 + r, seed=synth.task_seed(r, i)))
-    with gvm.Manager(R, ring_depth=16, mode="barrier", sgemm_path="split3", slice_bytes=32 << 20) as mgr:
+    with gvm.Manager(R, ring_depth=16, mode="barrier", sgemm_path="split3", slice_bytes=32 << 20,
+                     copy_in_streams=in_streams) as mgr:
         ranks = [mgr.attach(r) for r in range(R)]
         phases = [[(gvm.GvmTask * per)() for _ in range(R)] for _ in range(nphases)]
         keep = []
