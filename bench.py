@@ -14,10 +14,12 @@ scheduler), every rank syncs (gvm_sync).
          copies, the kernel and the output copies are inside the timed
          region (host wall clock).
   roofline     the scheduler kernel (the dominant kernel: it runs every tile)
+         against its compute roof (SGEMM: bf16 / 3 or FFMA), with HBM under
+         `other` and the roof with the longer time floor named in `binding`
   cpu_baseline the CPU oracle (binary64) on the host cores, bounded sample
-  plain_per_rank  (--plain) each rank in its own process and context, default
-         stream, synchronous copies, the same FMA kernel (Section 4.1's
-         conventional sharing, Eq. 1)
+  plain_per_rank  each rank in its own process and context, default stream,
+         the same task kernels (Section 4.1's conventional sharing, Eq. 1):
+         operands resident, with copies, and with T_init
 
 ``--impl reference`` runs the reference arm: the CPU oracle as it stands on
 the host cores, one rank per thread, a bounded sample per step.
@@ -277,6 +279,32 @@ def host_memcpy_gbs(nbytes=256 << 20, reps=3):
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return 2 * nbytes / best / 1e9
+
+
+def sgemm_roofline(tasks, launch_s, path, pk, pk_kind):
+    """Roofline of an SGEMM launch against both of its roofs: the compute
+    roof of its path (split3: the measured bf16 burst / 3 products; FMA: the
+    FP32 lanes at the maximum clock), reported as the bound, and HBM (A, B
+    and C once per task, 4 (mk + kn + mn) bytes) under `other`, with
+    `binding` naming the roof whose time floor (work / peak) is longer."""
+    flops = sum(s.flops for s in tasks)
+    byts = sum(4 * (s.m * s.k + s.k * s.n + s.m * s.n) for s in tasks)
+    if path == "fma":
+        cpeak = GB300_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        compute = {"bound": "alu", "unit": "TFLOP/s", "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    else:
+        cpeak = pk["bf16_tflops"] / 3.0
+        compute = {"bound": "tensor", "unit": "TFLOP/s",
+                   "peak_basis": f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"}
+    compute.update({"achieved": flops / launch_s / 1e12, "peak": cpeak, "algorithmic_flops": flops})
+    compute["frac"] = compute["achieved"] / cpeak
+    hbm = {"bound": "hbm", "unit": "GB/s", "peak_basis": f"HBM copy {pk['hbm_gbs']} GB/s ({pk_kind})",
+           "achieved": byts / launch_s / 1e9, "peak": pk["hbm_gbs"], "bytes_per_launch": byts}
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    main = dict(compute)
+    main["other"] = {k: hbm[k] for k in ("bound", "unit", "achieved", "peak", "frac", "bytes_per_launch")}
+    main["binding"] = "hbm" if hbm["frac"] > compute["frac"] else compute["bound"]
+    return main
 
 
 def block_link_gbs(blocks, to_device: bool):
@@ -851,16 +879,8 @@ def gpu_arm(args, w, desc, rank, world):
     pk, pk_kind = peaks()
     kmean = statistics.mean(t_kernel)
     if w.tasks[0].kind == synth.TASK_SGEMM:
-        flops = sum(s.flops for s in w.tasks)
-        if args.path in ("split3", "split3_wide", "split3_tma"):
-            peak = pk["bf16_tflops"] / 3.0
-            roof = {"bound": "tensor", "unit": "TFLOP/s",
-                    "peak_basis": f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"}
-        else:
-            peak = GB300_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            roof = {"bound": "alu", "unit": "TFLOP/s",
-                    "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
-        achieved = flops / kmean / 1e12
+        roof = sgemm_roofline(w.tasks, kmean, args.path, pk, pk_kind)
+        achieved, peak = roof["achieved"], roof["peak"]
     else:
         byts = sum(12 * s.n for s in w.tasks)
         peak = pk["hbm_gbs"]
@@ -990,15 +1010,8 @@ def resident_leg(args, w, inputs, path, steps, warmup, label):
     kmean = statistics.mean(launch) / 1e3
     pk, pk_kind = peaks()
     if w.tasks[0].kind == synth.TASK_SGEMM:
-        flops = sum(s.flops for s in w.tasks)
-        if path == "fma":
-            peak = GB300_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            roof = {"bound": "alu", "unit": "TFLOP/s", "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
-        else:
-            peak = pk["bf16_tflops"] / 3.0
-            roof = {"bound": "tensor", "unit": "TFLOP/s",
-                    "peak_basis": f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"}
-        achieved = flops / kmean / 1e12
+        roof = sgemm_roofline(w.tasks, kmean, path, pk, pk_kind)
+        achieved, peak = roof["achieved"], roof["peak"]
     else:
         byts = sum(12 * s.n for s in w.tasks)
         peak = pk["hbm_gbs"]
