@@ -1899,10 +1899,17 @@ def grouped_arm(args):
         errs.append(float(oracle.rel_fro_err(C[rows], oracle.sgemm64(A[rows], B))))
     mgr.shutdown()
     pk, pk_kind = peaks()
+    # A launch this long runs back to back under the power cap: the measured
+    # sustained bf16 rate is its peak (the burst one for short launches),
+    # with the burst fraction kept beside it.
+    sustained = kmean >= 0.05 and "bf16_tflops_sustained" in pk
+    burst_frac = None
     if args.path != "fma":
-        peak = pk["bf16_tflops"] / 3.0
-        basis = f"bf16 dense {pk['bf16_tflops']} TFLOP/s ({pk_kind}, burst) / 3 products"
+        tf = pk["bf16_tflops_sustained"] if sustained else pk["bf16_tflops"]
+        peak = tf / 3.0
+        basis = f"bf16 dense {tf} TFLOP/s ({pk_kind}, {'sustained' if sustained else 'burst'}) / 3 products"
         bound = "tensor"
+        burst_frac = flops / kmean / 1e12 / (pk["bf16_tflops"] / 3.0)
     else:
         peak = GB300_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         basis = "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
@@ -1923,7 +1930,7 @@ def grouped_arm(args):
                                "standard-normal operands drawn on the device, resident",
                    "sgemm_path": args.path, "mode": "barrier", "tflop_per_step": flops / 1e12},
         "roofline": {"bound": bound, "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                     "peak_basis": basis,
+                     "peak_basis": basis, "frac_of_burst_peak": burst_frac,
                      "kernel": "gvm::" + {"split3": "sched_fused_kernel",
                                           "split3_wide": "sched_wide_kernel",
                                           "split3_tma": "sched_tma_kernel"}.get(args.path, "sched_fma_kernel"),
